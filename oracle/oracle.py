@@ -1,0 +1,213 @@
+"""Python access to the serial FP64 CPU oracle in ``rhd_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The library never imports
+this module and shares no code with it.
+
+The oracle is compiled with ``-O2 -ffp-contract=off`` so that x86-64 and
+aarch64 hosts evaluate the same expressions in the same way.
+
+Problem descriptions are plain dicts (see ``paper_2404_08247_gb300.inputs``);
+this module maps them onto the oracle's own ``orc_params`` struct.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "rhd_oracle.c")
+HDR = os.path.join(HERE, "rhd_oracle.h")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD_DIR, "liborc.so")
+
+NFIELD = 10
+FIELDS = ("rho", "mx", "my", "mz", "egas", "erad", "fx", "fy", "fz", "kappa")
+STATUS = {0: "ok", 1: "arg", 3: "newton", 4: "outer", 5: "nonphysical"}
+
+_BC = {"periodic": 0, "reflect": 1}
+_CLOSURE = {"m1": 0, "eddington": 1}
+_HLL = {"tau": 0, "none": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``_build/liborc.so`` (if missing or stale)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    stale = force or not os.path.exists(LIB)
+    if not stale:
+        t = os.path.getmtime(LIB)
+        stale = any(os.path.getmtime(f) > t for f in (SRC, HDR))
+    if stale:
+        tmp = LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_longlong * 3),
+        ("dx", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("gamma", ctypes.c_double),
+        ("c", ctypes.c_double),
+        ("chat", ctypes.c_double),
+        ("a_rad", ctypes.c_double),
+        ("kB_over_mu", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("closure", ctypes.c_int),
+        ("vc_order", ctypes.c_int),
+        ("hll_mode", ctypes.c_int),
+        ("newton_rtol", ctypes.c_double),
+        ("outer_rtol", ctypes.c_double),
+        ("newton_max_iter", ctypes.c_int),
+        ("outer_max_iter", ctypes.c_int),
+    ]
+
+
+class OrcInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("fail_cell", ctypes.c_longlong),
+        ("max_newton", ctypes.c_int),
+        ("max_outer", ctypes.c_int),
+        ("sum_newton", ctypes.c_longlong),
+        ("n_solves", ctypes.c_longlong),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        P = ctypes.POINTER(OrcParams)
+        L.orc_dt.argtypes = [P]
+        L.orc_dt.restype = ctypes.c_double
+        L.orc_eddington_tensor.argtypes = [P, ctypes.c_double, dp, dp]
+        L.orc_eddington_tensor.restype = None
+        L.orc_transport.argtypes = [P, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_transport.restype = ctypes.c_int
+        L.orc_local_solve.argtypes = [P, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, dp,
+                                      ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
+        L.orc_local_solve.restype = ctypes.c_int
+        L.orc_step.argtypes = [P, dp, ctypes.c_double, ctypes.POINTER(OrcInfo)]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_totals.argtypes = [P, dp, dp]
+        L.orc_totals.restype = None
+        _lib = L
+    return _lib
+
+
+def make_params(prob: dict) -> OrcParams:
+    """Map a problem dict onto ``orc_params``."""
+    p = OrcParams()
+    p.ndim = int(prob["ndim"])
+    n = list(prob["n"]) + [1] * (3 - len(prob["n"]))
+    dx = list(prob["dx"]) + [1.0] * (3 - len(prob["dx"]))
+    for d in range(3):
+        p.n[d] = int(n[d])
+        p.dx[d] = float(dx[d])
+    bc = prob.get("bc", "periodic")
+    for d in range(3):
+        for s in range(2):
+            kind = bc if isinstance(bc, str) else (
+                bc[d][s] if d < len(bc) else "periodic")
+            p.bc[d][s] = _BC[kind]
+    p.gamma = float(prob["gamma"])
+    p.c = float(prob["c"])
+    p.chat = float(prob["chat"])
+    p.a_rad = float(prob.get("a_rad", 1.0))
+    p.kB_over_mu = float(prob.get("kB_over_mu", 1.0))
+    p.cfl = float(prob.get("cfl", 0.4))
+    p.closure = _CLOSURE[prob.get("closure", "m1")]
+    p.vc_order = int(prob.get("vc_order", 2))
+    p.hll_mode = _HLL[prob.get("hll_mode", "tau")]
+    p.newton_rtol = float(prob.get("newton_rtol", 1e-13))
+    p.outer_rtol = float(prob.get("outer_rtol", 1e-13))
+    p.newton_max_iter = int(prob.get("newton_max_iter", 64))
+    p.outer_max_iter = int(prob.get("outer_max_iter", 32))
+    return p
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def dt(prob: dict) -> float:
+    p = make_params(prob)
+    return lib().orc_dt(ctypes.byref(p))
+
+
+def step(prob: dict, U: np.ndarray, nsteps: int = 1, dt: float = 0.0,
+         raise_on_error: bool = True):
+    """Advance U (shape (10, nz, ny, nx) float64, modified in place) by nsteps.
+
+    Returns a list with one info dict per step taken."""
+    p = make_params(prob)
+    infos = []
+    for _ in range(nsteps):
+        info = OrcInfo()
+        st = lib().orc_step(ctypes.byref(p), _dptr(U), float(dt), ctypes.byref(info))
+        d = {k: getattr(info, k) for k, _ in OrcInfo._fields_}
+        infos.append(d)
+        if st != 0:
+            if raise_on_error:
+                raise RuntimeError("oracle step failed: %s at cell %d"
+                                   % (STATUS.get(st, st), info.fail_cell))
+            break
+    return infos
+
+
+def transport(prob: dict, U: np.ndarray) -> np.ndarray:
+    """Rates (dE/dt, dFx/dt, dFy/dt, dFz/dt) of s(y), shape (4, nz, ny, nx)."""
+    p = make_params(prob)
+    rate = np.zeros((4,) + U.shape[1:], dtype=np.float64)
+    fc = ctypes.c_longlong(-1)
+    st = lib().orc_transport(ctypes.byref(p), _dptr(U), _dptr(rate), ctypes.byref(fc))
+    if st != 0:
+        raise RuntimeError("oracle transport failed at cell %d" % fc.value)
+    return rate
+
+
+def local_solve(prob: dict, theta: float, dt: float, rho: float, chi: float,
+                y) -> tuple:
+    """One cell's implicit solve.  y = (Egas, mx, my, mz, E, Fx, Fy, Fz).
+
+    Returns (status, y_out, n_newton, n_outer)."""
+    p = make_params(prob)
+    yy = np.ascontiguousarray(np.asarray(y, dtype=np.float64).copy())
+    nn = ctypes.c_int(0)
+    no = ctypes.c_int(0)
+    st = lib().orc_local_solve(ctypes.byref(p), float(theta), float(dt), float(rho),
+                               float(chi), _dptr(yy), ctypes.byref(nn),
+                               ctypes.byref(no))
+    return st, yy, nn.value, no.value
+
+
+def eddington_tensor(prob: dict, E: float, F) -> np.ndarray:
+    p = make_params(prob)
+    FF = np.ascontiguousarray(np.asarray(F, dtype=np.float64))
+    D = np.zeros((3, 3), dtype=np.float64)
+    lib().orc_eddington_tensor(ctypes.byref(p), float(E), _dptr(FF), _dptr(D))
+    return D
+
+
+def totals(prob: dict, U: np.ndarray) -> np.ndarray:
+    p = make_params(prob)
+    out = np.zeros(4, dtype=np.float64)
+    lib().orc_totals(ctypes.byref(p), _dptr(U), _dptr(out))
+    return out

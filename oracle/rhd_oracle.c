@@ -1,0 +1,487 @@
+/*
+ * rhd_oracle.c -- serial FP64 CPU oracle of one grey IMEX PD-ARS radiation
+ * step (He, Wibking & Krumholz 2024).
+ *
+ * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+ * CPU baseline are its only users.  It is deliberately plain: no blocking, no
+ * fusion, loops over cells and faces in the order the paper describes them.
+ *
+ * Readings of passages the paper leaves open are marked "reading:" below.
+ */
+#include "rhd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static long long ncell_of(const orc_params* p) {
+  return p->n[0] * p->n[1] * p->n[2];
+}
+
+/* ---------------------------------------------------------------- time step */
+
+/* Sec. 4.3: the radiation wave speed never exceeds the (reduced) speed of
+ * light, so the explicit CFL step is fixed by chat and the cell widths.
+ * reading: multi-dimensional CFL = CFL / (chat * sum_d 1/dx_d). */
+double orc_dt(const orc_params* p) {
+  double s = 0.0;
+  for (int d = 0; d < p->ndim; ++d) s += 1.0 / p->dx[d];
+  return p->cfl / (p->chat * s);
+}
+
+/* ------------------------------------------------------------- the closure */
+
+/* The paper leaves the closure free (Sec. 2.1).  reading: Levermore's M1
+ * closure, P = D E with D = (1-xi)/2 I + (3 xi - 1)/2 n n, reduced flux
+ * f = |F| / (c E) clipped to [0, 1], xi = (3 + 4 f^2) / (5 + 2 sqrt(4 - 3 f^2)).
+ * Zero flux gives the isotropic D = I/3.  The Eddington option is D = I/3. */
+void orc_eddington_tensor(const orc_params* p, double E, const double F[3],
+                          double D[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) D[i][j] = (i == j) ? 1.0 / 3.0 : 0.0;
+  if (p->closure == ORC_CLOSURE_EDDINGTON) return;
+  double Fmag = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+  if (Fmag == 0.0) return;
+  double f = Fmag / (p->c * E);
+  if (f > 1.0) f = 1.0;
+  if (f < 0.0) f = 0.0;
+  double xi = (3.0 + 4.0 * f * f) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f * f));
+  double nhat[3] = {F[0] / Fmag, F[1] / Fmag, F[2] / Fmag};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      D[i][j] = 0.5 * (1.0 - xi) * (i == j ? 1.0 : 0.0) +
+                0.5 * (3.0 * xi - 1.0) * nhat[i] * nhat[j];
+}
+
+/* ---------------------------------------------------------- reconstruction */
+
+/* reading: PLM with the monotonised-central limiter,
+ * slope = minmod(2 d-, (d- + d+)/2, 2 d+), minmod of mixed signs = 0. */
+static double minmod3(double a, double b, double c) {
+  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+  return 0.0;
+}
+
+static double mc_slope(double um, double u0, double up) {
+  double dm = u0 - um;
+  double dp = up - u0;
+  return minmod3(2.0 * dm, 0.5 * (dm + dp), 2.0 * dp);
+}
+
+/* One cell's radiation variables as the transport sees them. */
+typedef struct {
+  double E;
+  double F[3];
+  double chi;
+} rad_cell;
+
+/* Fetch the cell at coordinate (i0,i1,i2) shifted by off along axis d, with
+ * ghost cells made by the boundary condition.  reading: periodic wrap, or a
+ * reflecting wall that mirrors the cell and negates the normal flux. */
+static rad_cell fetch(const orc_params* p, const double* U, const long long ic[3],
+                      int d, int off) {
+  long long q[3] = {ic[0], ic[1], ic[2]};
+  long long nd = p->n[d];
+  long long x = q[d] + off;
+  int flip = 0;
+  if (x < 0) {
+    if (p->bc[d][0] == ORC_BC_PERIODIC) {
+      x = ((x % nd) + nd) % nd;
+    } else {
+      x = -1 - x;
+      flip = 1;
+    }
+  } else if (x >= nd) {
+    if (p->bc[d][1] == ORC_BC_PERIODIC) {
+      x = x % nd;
+    } else {
+      x = 2 * nd - 1 - x;
+      flip = 1;
+    }
+  }
+  q[d] = x;
+  long long N = ncell_of(p);
+  long long idx = q[0] + p->n[0] * (q[1] + p->n[1] * q[2]);
+  rad_cell r;
+  r.E = U[ORC_ERAD * N + idx];
+  r.F[0] = U[ORC_FX * N + idx];
+  r.F[1] = U[ORC_FY * N + idx];
+  r.F[2] = U[ORC_FZ * N + idx];
+  if (flip) r.F[d] = -r.F[d];
+  r.chi = U[ORC_KAPPA * N + idx] * U[ORC_RHO * N + idx];
+  return r;
+}
+
+/* HLL flux through the face between cells a and b along axis d, for the RSLA
+ * transport system of eq. (yrsla): conserved (E, F/(c chat)) with fluxes
+ * ((chat/c) F_d, P_d.).  Face states: PLM from the 4-cell stencil
+ * (am, a | b, bp).  out[0] = energy flux, out[1..3] = flux of F/(c chat). */
+static int hll_face(const orc_params* p, int d, const rad_cell* am,
+                    const rad_cell* a, const rad_cell* b, const rad_cell* bp,
+                    double out[4]) {
+  const double c = p->c, chat = p->chat;
+  /* left state: cell a + half its slope; right state: cell b - half its slope */
+  double EL = a->E + 0.5 * mc_slope(am->E, a->E, b->E);
+  double ER = b->E - 0.5 * mc_slope(a->E, b->E, bp->E);
+  double FL[3], FR[3];
+  for (int j = 0; j < 3; ++j) {
+    FL[j] = a->F[j] + 0.5 * mc_slope(am->F[j], a->F[j], b->F[j]);
+    FR[j] = b->F[j] - 0.5 * mc_slope(a->F[j], b->F[j], bp->F[j]);
+  }
+  if (!(EL > 0.0) || !(ER > 0.0)) return ORC_ERR_NONPHYSICAL;
+  /* reading: a reconstructed face flux above the free-streaming limit
+   * |F| <= c E is scaled back onto that limit. */
+  double nL = sqrt(FL[0] * FL[0] + FL[1] * FL[1] + FL[2] * FL[2]);
+  double nR = sqrt(FR[0] * FR[0] + FR[1] * FR[1] + FR[2] * FR[2]);
+  if (nL > c * EL)
+    for (int j = 0; j < 3; ++j) FL[j] *= c * EL / nL;
+  if (nR > c * ER)
+    for (int j = 0; j < 3; ++j) FR[j] *= c * ER / nR;
+
+  double DL[3][3], DR[3][3];
+  orc_eddington_tensor(p, EL, FL, DL);
+  orc_eddington_tensor(p, ER, FR, DR);
+
+  /* Sec. 4.3: S = +-sqrt(f) c with f the Eddington-tensor component along the
+   * face normal; under the RSLA the speed is chat.  reading: the larger of the
+   * two sides, never below the diffusion-limit value 1/sqrt(3). */
+  double sf = fmax(sqrt(DL[d][d]), sqrt(DR[d][d]));
+  sf = fmax(sf, 1.0 / sqrt(3.0));
+  double SR = chat * sf;
+  double SL = -SR;
+
+  /* Sec. 4.3 HLL energy flux with the factor epsilon on the diffusive term.
+   * NONE (the paper's IMEX method): epsilon = 1.  TAU: reading,
+   * epsilon = (1 - exp(-tau)) / tau with tau the optical depth of one cell
+   * width at the face, which is 1 when thin and 1/tau when thick. */
+  double eps = 1.0;
+  if (p->hll_mode == ORC_HLL_TAU) {
+    double tau = 0.5 * (a->chi + b->chi) * p->dx[d];
+    if (tau > 0.0) eps = -expm1(-tau) / tau;
+  }
+  double phiL = (chat / c) * FL[d];
+  double phiR = (chat / c) * FR[d];
+  out[0] = (SR * phiL - SL * phiR + eps * SR * SL * (ER - EL)) / (SR - SL);
+  for (int j = 0; j < 3; ++j) {
+    double PL = DL[d][j] * EL;
+    double PR = DR[d][j] * ER;
+    double uL = FL[j] / (c * chat);
+    double uR = FR[j] / (c * chat);
+    out[1 + j] = (SR * PL - SL * PR + SR * SL * (uR - uL)) / (SR - SL);
+  }
+  return ORC_OK;
+}
+
+/* s(y) of eq. (yrsla): dE/dt = -div((chat/c) F), d(F/(c chat))/dt = -div P.
+ * The rate of the physical flux F is c chat times the latter. */
+int orc_transport(const orc_params* p, const double* U, double* rate,
+                  long long* fail_cell) {
+  const long long N = ncell_of(p);
+  memset(rate, 0, sizeof(double) * 4 * (size_t)N);
+  if (fail_cell) *fail_cell = -1;
+  for (int d = 0; d < p->ndim; ++d) {
+    for (long long i2 = 0; i2 < p->n[2]; ++i2)
+      for (long long i1 = 0; i1 < p->n[1]; ++i1)
+        for (long long i0 = 0; i0 < p->n[0]; ++i0) {
+          long long ic[3] = {i0, i1, i2};
+          long long idx = i0 + p->n[0] * (i1 + p->n[1] * i2);
+          rad_cell s[5];
+          for (int o = -2; o <= 2; ++o) s[o + 2] = fetch(p, U, ic, d, o);
+          double lo[4], hi[4];
+          /* face i-1/2: cells (i-2, i-1 | i, i+1); face i+1/2: (i-1, i | i+1, i+2) */
+          if (hll_face(p, d, &s[0], &s[1], &s[2], &s[3], lo) != ORC_OK ||
+              hll_face(p, d, &s[1], &s[2], &s[3], &s[4], hi) != ORC_OK) {
+            if (fail_cell) *fail_cell = idx;
+            return ORC_ERR_NONPHYSICAL;
+          }
+          rate[0 * N + idx] -= (hi[0] - lo[0]) / p->dx[d];
+          for (int j = 0; j < 3; ++j)
+            rate[(1 + j) * N + idx] -=
+                p->c * p->chat * (hi[1 + j] - lo[1 + j]) / p->dx[d];
+        }
+  }
+  return ORC_OK;
+}
+
+/* -------------------------------------------------------- the local solve */
+
+/* Implicit stage of one cell, Sec. 3.3, grey material: chi_0P = chi_0E =
+ * chi_0F = chi, so every (chi_0F - chi_0E) term of eq. (G0), (G1), (Rnew) and
+ * (numF1) vanishes and (2 chi_0E - chi_0F) = chi.
+ *
+ * Inner stage: Newton-Raphson on x = (Egas, R) for eq. (FGFR),
+ *   F_G = Egas - Egas^(t) + (c/chat) R,   F_R = E - E^(t) - R,
+ * where E(Egas, R) follows from eq. (Rnew) with v and F frozen:
+ *   R = theta dt [chat chi (aT^4 - E)(1 + beta^2/2) + chi (chat/c) v.F/c],
+ * with the paper's Jacobian (beta^2 terms dropped).  Outer stage: eq. (numF1)
+ * or (numF2) for F, the momentum update, then a repeat of the inner stage with
+ * the new v and F until the v- and F-terms of R settle. */
+int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
+                    double chi, double y[8], int* n_newton, int* n_outer) {
+  const double c = p->c, chat = p->chat, a = p->a_rad;
+  const double Cv = rho * p->kB_over_mu / (p->gamma - 1.0); /* C_v = rho c_v */
+  const double Eg0 = y[0];
+  const double m0[3] = {y[1], y[2], y[3]};
+  const double E0 = y[4];
+  const double F0[3] = {y[5], y[6], y[7]};
+  *n_newton = 0;
+  *n_outer = 0;
+
+  /* With chi = 0 every exchange term of eq. (egupdate)-(fupdate) vanishes. */
+  if (chi == 0.0) return ORC_OK;
+
+  /* reading: E_tot = Egas^(t) + (c/chat) E^(t), the energy the source terms
+   * conserve (the printed chat/c factor is read as a typo; both agree when
+   * chat = c). */
+  const double Etot = Eg0 + (c / chat) * E0;
+  const double eps = p->newton_rtol;
+  const double tdt = theta * dt;
+
+  double Eg = Eg0, R = 0.0; /* reading: Newton starts from (Egas^(t), 0) */
+  double m[3] = {m0[0], m0[1], m0[2]};
+  double F[3] = {F0[0], F0[1], F0[2]};
+  double E = E0;
+
+  for (int outer = 0; outer < p->outer_max_iter; ++outer) {
+    *n_outer = outer + 1;
+    /* v and F frozen for the inner stage */
+    double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+    double beta2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / (c * c);
+    double g = (p->vc_order == 2) ? 1.0 + 0.5 * beta2 : 1.0;
+    double vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
+    double Ekin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+
+    /* ---- inner Newton-Raphson on (Egas, R) ---- */
+    int converged = 0;
+    for (int it = 0;; ++it) {
+      double T = (Eg - Ekin) / Cv;
+      if (!(T > 0.0) || !isfinite(T) || !isfinite(R)) return ORC_ERR_NONPHYSICAL;
+      double aT4 = a * T * T * T * T; /* 4 pi B / c */
+      /* E as a function of (Egas, R): eq. (Rnew) solved for E */
+      double Ex = aT4 + (vF / (c * c)) / g - R / (chat * chi * tdt * g);
+      double FG = Eg - Eg0 + (c / chat) * R;
+      double FR = Ex - E0 - R;
+      if (fabs(FG / Etot) < eps && fabs((c / chat) * FR / Etot) < eps) {
+        converged = 1;
+        break;
+      }
+      if (it >= p->newton_max_iter) break;
+      /* Jacobian of eq. (linear) */
+      double J00 = 1.0;
+      double J01 = c / chat;
+      double J10 = 4.0 * a * T * T * T / Cv; /* (1/C_v) d(aT^4)/dT */
+      double J11 = -1.0 / (chat * chi * tdt) - 1.0;
+      double det = J00 * J11 - J01 * J10;
+      double dEg = (-FG * J11 + FR * J01) / det;
+      double dR = (-FR * J00 + FG * J10) / det;
+      Eg += dEg;
+      R += dR;
+      *n_newton += 1;
+    }
+    if (!converged) return ORC_ERR_NEWTON;
+
+    /* Energy closure: F_G = F_R = 0 give E - E^(t) = R = -(chat/c)(Egas -
+     * Egas^(t)).  reading: the printed c/chat factor is read as chat/c, the
+     * form consistent with eq. (FGFR) (they agree when chat = c). */
+    E = E0 - (chat / c) * (Eg - Eg0);
+
+    /* ---- outer stage: flux and momentum ---- */
+    double T = (Eg - Ekin) / Cv;
+    double aT4 = a * T * T * T * T;
+    double D[3][3];
+    orc_eddington_tensor(p, E, F, D); /* reading: P from the new E and the
+                                         flux of the previous outer pass */
+    double Fn[3], mn[3];
+    for (int i = 0; i < 3; ++i) {
+      double vP = 0.0;
+      for (int j = 0; j < 3; ++j) vP += v[j] * D[j][i] * E; /* v_j P_ji */
+      double num = F0[i] + chat * tdt * (chi * aT4 * v[i] + chi * vP);
+      double den = (p->vc_order == 2)
+                       ? 1.0 + chat * chi * (1.0 + beta2 / 2.0) * tdt /* (numF2) */
+                       : 1.0 + chat * chi * tdt;                      /* (numF1) */
+      Fn[i] = num / den;
+      mn[i] = m0[i] - (Fn[i] - F0[i]) / (c * chat); /* momentum update */
+    }
+
+    /* reading: the "terms proportional to v and F in R" are
+     * Q = theta dt chat chi [(g - 1)(aT^4 - E) + v.F/c^2]; compare the Q the
+     * inner stage used with the Q of the updated v and F. */
+    double Q_old = chat * chi * tdt * ((g - 1.0) * (aT4 - E) + vF / (c * c));
+    double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
+    double beta2n = (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]) / (c * c);
+    double gn = (p->vc_order == 2) ? 1.0 + 0.5 * beta2n : 1.0;
+    double vFn = vn[0] * Fn[0] + vn[1] * Fn[1] + vn[2] * Fn[2];
+    double Q_new = chat * chi * tdt * ((gn - 1.0) * (aT4 - E) + vFn / (c * c));
+
+    for (int i = 0; i < 3; ++i) {
+      F[i] = Fn[i];
+      m[i] = mn[i];
+    }
+    double dQ = fabs(Q_new - Q_old);
+    if (dQ <= p->outer_rtol * fabs(Q_old) || dQ <= p->outer_rtol * fabs(R)) {
+      y[0] = Eg;
+      y[1] = m[0];
+      y[2] = m[1];
+      y[3] = m[2];
+      y[4] = E;
+      y[5] = F[0];
+      y[6] = F[1];
+      y[7] = F[2];
+      if (!(E > 0.0) || !isfinite(E) || !isfinite(F[0]) || !isfinite(F[1]) ||
+          !isfinite(F[2]))
+        return ORC_ERR_NONPHYSICAL;
+      return ORC_OK;
+    }
+  }
+  return ORC_ERR_OUTER;
+}
+
+/* ---------------------------------------------------------- the IMEX step */
+
+static void record(orc_info* info, int st, long long cell) {
+  if (info && st != ORC_OK && info->status == ORC_OK) {
+    info->status = st;
+    info->fail_cell = cell;
+  }
+}
+
+/* Implicit part of one stage over all cells: U holds the explicit state on
+ * input and the solution on output. */
+static int implicit_all(const orc_params* p, double* U, double theta, double dt,
+                        orc_info* info) {
+  const long long N = ncell_of(p);
+  for (long long i = 0; i < N; ++i) {
+    double rho = U[ORC_RHO * N + i];
+    double chi = U[ORC_KAPPA * N + i] * rho;
+    /* y order: Egas, m, E, F */
+    double yy[8] = {U[ORC_EGAS * N + i], U[ORC_MX * N + i], U[ORC_MY * N + i],
+                    U[ORC_MZ * N + i],   U[ORC_ERAD * N + i], U[ORC_FX * N + i],
+                    U[ORC_FY * N + i],   U[ORC_FZ * N + i]};
+    int nn = 0, no = 0;
+    int st = orc_local_solve(p, theta, dt, rho, chi, yy, &nn, &no);
+    if (info) {
+      if (nn > info->max_newton) info->max_newton = nn;
+      if (no > info->max_outer) info->max_outer = no;
+      info->sum_newton += nn;
+      info->n_solves += 1;
+    }
+    if (st != ORC_OK) {
+      record(info, st, i);
+      return st;
+    }
+    U[ORC_EGAS * N + i] = yy[0];
+    U[ORC_MX * N + i] = yy[1];
+    U[ORC_MY * N + i] = yy[2];
+    U[ORC_MZ * N + i] = yy[3];
+    U[ORC_ERAD * N + i] = yy[4];
+    U[ORC_FX * N + i] = yy[5];
+    U[ORC_FY * N + i] = yy[6];
+    U[ORC_FZ * N + i] = yy[7];
+  }
+  return ORC_OK;
+}
+
+static const int RAD_FIELD[4] = {ORC_ERAD, ORC_FX, ORC_FY, ORC_FZ};
+
+/* eq. (imex1) and (imex2) with epsilon = 0 in the PD-ARS tableau:
+ *   y(n+1/2) = y(n) + dt s(y(n)) + dt f(y(n+1/2))
+ *   y(n+1)   = y(n) + dt [s(y(n)) + s(y(n+1/2))]/2
+ *                   + dt [f(y(n+1/2)) + f(y(n+1))]/2
+ * The stage-1 relation fixes dt f(y(n+1/2)) = y(n+1/2) - y*, y* the explicit
+ * state of stage 1; stage 2 uses it as such.  On failure U is left at y(n). */
+int orc_step(const orc_params* p, double* U, double dt, orc_info* info) {
+  const long long N = ncell_of(p);
+  const size_t bytes = sizeof(double) * ORC_NFIELD * (size_t)N;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->fail_cell = -1;
+  }
+  if (dt <= 0.0) dt = orc_dt(p);
+
+  double* Un = (double*)malloc(bytes);     /* y(n) */
+  double* Uh = (double*)malloc(bytes);     /* y*, then y(n+1/2) */
+  double* Ystar = (double*)malloc(bytes);  /* copy of y* */
+  double* s0 = (double*)malloc(sizeof(double) * 4 * (size_t)N);
+  double* s1 = (double*)malloc(sizeof(double) * 4 * (size_t)N);
+  int st = ORC_OK;
+  long long fc = -1;
+  if (!Un || !Uh || !Ystar || !s0 || !s1) {
+    st = ORC_ERR_ARG;
+    goto done;
+  }
+  memcpy(Un, U, bytes);
+
+  /* ---- stage 1: explicit s(y(n)), then implicit with theta = 1 ---- */
+  st = orc_transport(p, Un, s0, &fc);
+  if (st != ORC_OK) {
+    record(info, st, fc);
+    goto done;
+  }
+  memcpy(Uh, Un, bytes);
+  for (int r = 0; r < 4; ++r)
+    for (long long i = 0; i < N; ++i)
+      Uh[RAD_FIELD[r] * N + i] = Un[RAD_FIELD[r] * N + i] + dt * s0[r * N + i];
+  memcpy(Ystar, Uh, bytes);
+  st = implicit_all(p, Uh, 1.0, dt, info);
+  if (st != ORC_OK) goto done;
+
+  /* ---- stage 2: explicit part of eq. (imex2), then implicit, theta = 1/2 ---- */
+  st = orc_transport(p, Uh, s1, &fc);
+  if (st != ORC_OK) {
+    record(info, st, fc);
+    goto done;
+  }
+  {
+    double* U2 = Ystar; /* reuse: becomes the stage-2 explicit state */
+    /* evolved fields: y(n) + dt/2 [s(y(n)) + s(y(n+1/2))] + (1/2) dt f(y(n+1/2)) */
+    static const int EVOLVED[8] = {ORC_EGAS, ORC_MX, ORC_MY, ORC_MZ,
+                                   ORC_ERAD, ORC_FX, ORC_FY, ORC_FZ};
+    for (int e = 0; e < 8; ++e) {
+      int f = EVOLVED[e];
+      int r = -1;
+      for (int q = 0; q < 4; ++q)
+        if (RAD_FIELD[q] == f) r = q;
+      for (long long i = 0; i < N; ++i) {
+        double yn = Un[f * N + i];
+        double sn = (r >= 0) ? s0[r * N + i] : 0.0;
+        double sh = (r >= 0) ? s1[r * N + i] : 0.0;
+        double dtf_half = Uh[f * N + i] - U2[f * N + i]; /* y(n+1/2) - y* */
+        U2[f * N + i] = yn + dt * (0.5 * sn + 0.5 * sh) + 0.5 * dtf_half;
+      }
+    }
+    /* static fields stay those of y(n) */
+    for (long long i = 0; i < N; ++i) {
+      U2[ORC_RHO * N + i] = Un[ORC_RHO * N + i];
+      U2[ORC_KAPPA * N + i] = Un[ORC_KAPPA * N + i];
+    }
+    st = implicit_all(p, U2, 0.5, dt, info);
+    if (st != ORC_OK) goto done;
+    memcpy(U, U2, bytes);
+  }
+
+done:
+  free(Un);
+  free(Uh);
+  free(Ystar);
+  free(s0);
+  free(s1);
+  return st;
+}
+
+/* ---------------------------------------------------------- the totals */
+
+/* Sec. 3.3: with the energy closure the scheme conserves Egas + (c/chat) E,
+ * and with the momentum update m + F/(c chat), cell by cell up to rounding. */
+void orc_totals(const orc_params* p, const double* U, double out[4]) {
+  const long long N = ncell_of(p);
+  double V = 1.0;
+  for (int d = 0; d < p->ndim; ++d) V *= p->dx[d];
+  for (int q = 0; q < 4; ++q) out[q] = 0.0;
+  for (long long i = 0; i < N; ++i) {
+    out[0] += (U[ORC_EGAS * N + i] + (p->c / p->chat) * U[ORC_ERAD * N + i]) * V;
+    out[1] += (U[ORC_MX * N + i] + U[ORC_FX * N + i] / (p->c * p->chat)) * V;
+    out[2] += (U[ORC_MY * N + i] + U[ORC_FY * N + i] / (p->c * p->chat)) * V;
+    out[3] += (U[ORC_MZ * N + i] + U[ORC_FZ * N + i] / (p->c * p->chat)) * V;
+  }
+}
