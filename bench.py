@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the grey IMEX PD-ARS radiation step on the 256^3 turbulent box.
+
+Metric: Mcell-updates/s, one cell-update = one cell advanced through both
+stages of one step.  Default run: one GPU, FP64, HLL TAU mode.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                  [--hll tau|none] [--n 256] [--impl ours|reference]
+
+* value: K steps enqueued back to back on the library stream, timed with CUDA
+  events after W warm-up steps; the state (1.34 GB at 256^3 FP64) is larger
+  than L2, so no flush is needed between steps.
+* e2e: the same metric through the public API with host buffers: every step
+  copies the full input state from pinned host memory, runs one step and
+  reads the full state back (wall clock, synchronised).
+* roofline: the dominant kernel's algorithmic HBM bytes per launch divided by
+  its mean event-timed duration inside the timed region, against the measured
+  copy bandwidth.
+* cpu_baseline: the CPU oracle (serial C, one core) on a bounded sample: a
+  periodic sub-box of the same initial state with the same dt.
+* --impl reference: the CPU oracle is the reference arm; each step is one
+  oracle step on a sub-box of the workload.
+* Several GPUs (torchrun): every rank advances its own independent box (weak
+  scaling, no data-path collective); value = all ranks' cell-updates / the
+  slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-updates/s per IMEX RHD step at 256^3, FP64 vs mixed; % HBM peak; adj/fwd"
+UNIT = "Mcell-updates/s"
+# algorithmic HBM bytes per cell of one launch of each stage kernel:
+# stage 1 reads y(n) (8 fields) + rho + kappa and writes y(n+1/2) (8 fields);
+# stage 2 reads y(n), y(n+1/2), rho, kappa and writes y(n+1).
+ALG_BYTES = {0: 8 * (8 + 2 + 8), 1: 8 * (8 + 8 + 2 + 8)}
+KERNEL_NAMES = {0: "stage1", 1: "stage2"}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__,
+                                 formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--hll", default="tau", choices=["tau", "none"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=96,
+                    help="edge of the oracle's sub-box for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=48,
+                    help="edge of the oracle's sub-box per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(prob, U, edge, nsteps, dt):
+    """Time the CPU oracle on a periodic edge^3 sub-box of U (Mcell-updates/s)."""
+    from oracle import oracle as O
+    O.build()
+    sub = dict(prob)
+    sub["n"] = [edge, edge, edge]
+    box = np.ascontiguousarray(U[:, :edge, :edge, :edge])
+    t0 = time.perf_counter()
+    O.step(sub, box, nsteps=nsteps, dt=dt)
+    t1 = time.perf_counter()
+    return edge ** 3 * nsteps / (t1 - t0) / 1e6, t1 - t0
+
+
+def workload(args, rank=0):
+    from paper_2404_08247_gb300 import inputs as I
+    prob, U, _ = I.turbulent_box_3d(n=args.n, seed_rho=3 + 100 * rank,
+                                    seed_v=4 + 100 * rank, seed_T=5 + 100 * rank,
+                                    hll_mode=args.hll)
+    return prob, U
+
+
+def config_of(args, prob):
+    return {
+        "workload": "turbulent_box_3d %d^3 periodic: log-normal rho (k^-4 GRF, "
+                    "sigma_ln=1), kappa~rho with tau_cell in [1e-3,1e3], log-uniform "
+                    "T over 1 decade, rms Mach 1, chat=30 max|v|, c=10 chat"
+                    % args.n,
+        "cells": int(args.n ** 3),
+        "precision": args.precision,
+        "hll_mode": args.hll,
+        "closure": "m1",
+        "vc_order": 2,
+        "cfl": prob["cfl"],
+        "l2_policy": "inputs larger than L2 (state %.2f GB)" % (args.n ** 3 * 80 / 1e9),
+    }
+
+
+# ------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    prob, U = workload(args)
+    dt = O.dt(prob)
+    edge = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_rate(prob, U, edge, 1, dt)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dtime = oracle_rate(prob, U, edge, 1, dt)
+        t += dtime
+    cells = edge ** 3 * args.steps
+    value = cells / t / 1e6
+    sample = "each step: one oracle step on a periodic %d^3 sub-box of the %d^3 state" % (
+        edge, args.n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, prob),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    from paper_2404_08247_gb300 import rhd
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    rhd.load()
+    prob, U = workload(args, rank)
+    N = U[0].size
+    stream = torch.cuda.current_stream()
+    ctx = rhd.RHDContext(prob, args.precision, stream=stream)
+    Ud = torch.from_numpy(U).cuda()
+    ctx.set_state(Ud)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    ctx.step(args.warmup)
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    l0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step_async(args.steps)
+    e1.record(stream)
+    info = ctx.sync()
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    klaunch, kms = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N * args.steps / (ms * 1e-3) / 1e6
+
+    # dominant kernel roofline (HBM view)
+    peaks, peak_src = measured_peaks()
+    dom = max((0, 1), key=lambda k: kms[k])
+    avg_ms = kms[dom] / max(klaunch[dom], 1)
+    achieved = ALG_BYTES[dom] * N / (avg_ms * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    roofline = {
+        "bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
+        "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+        if peak_src == "measured" else "fallback",
+        "alg_bytes_per_cell": ALG_BYTES[dom],
+        "avg_launch_ms": avg_ms,
+        "kernel_ms": {KERNEL_NAMES[k]: kms[k] / max(klaunch[k], 1) for k in (0, 1)},
+        "step_alg_bytes_per_cell_min": 144,
+    }
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(U).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        ctx.set_state(hin)
+        ctx.step(1)
+        ctx.get_state(hout)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.set_state(hin)
+            ctx.step(1)
+            ctx.get_state(hout)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        tt = t1 - t0
+        if dist is not None:
+            t = torch.tensor([tt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tt = float(t.item())
+        e2e = {"value": ws * N * args.e2e_steps / tt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(hin.numel() * 8),
+               "d2h_bytes_per_step": int(hout.numel() * 8),
+               "steps": args.e2e_steps}
+    ctx.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        rate, secs = oracle_rate(prob, U, args.cpu_sample, 2, O.dt(prob))
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "2 oracle steps of a periodic %d^3 sub-box of the %d^3 initial "
+                         "state, same dt (%.1f s)" % (args.cpu_sample, args.n, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic", "config": config_of(args, prob),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
+            "iterations": {"max_newton": info["max_newton"],
+                           "max_outer": info["max_outer"],
+                           "mean_newton": info["sum_newton"] / max(info["n_solves"], 1),
+                           "mean_outer": info["sum_outer"] / max(info["n_solves"], 1)},
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

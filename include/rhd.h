@@ -1,0 +1,207 @@
+/*
+ * rhd.h -- C ABI of the GB300 library for one grey, M1-closure IMEX PD-ARS
+ * radiation step (He, Wibking & Krumholz 2024, "An asymptotically-correct
+ * implicit-explicit time integration scheme for finite volume
+ * radiation-hydrodynamics").
+ *
+ * What one step computes (Sec. 3.2, eq. imex1 / imex2 with epsilon = 0):
+ *   y(n+1/2) = y(n) + dt s(y(n)) + dt f(y(n+1/2))
+ *   y(n+1)   = y(n) + dt [s(y(n)) + s(y(n+1/2))]/2
+ *                   + dt [f(y(n+1/2)) + f(y(n+1))]/2
+ * on a uniform Cartesian grid, with y = (rho v, Egas, E, F/(c chat)) and the
+ * reduced-speed-of-light split of eq. (yrsla):
+ *   s(y) = -div(0, 0, (chat/c) F, P)         explicit transport (Sec. 3.3:
+ *          piecewise-linear faces, HLL fluxes, Sec. 4.3 wave speeds and the
+ *          optional optical-depth factor on the energy flux),
+ *   f(y) = (G, c G0, -chat G0, -G)           local implicit exchange (Sec. 3.3:
+ *          eq. egupdate-fupdate, inner Newton on (Egas, R) of eq. FGFR/Rnew,
+ *          energy closure, eq. numF1/numF2, momentum update, outer iteration).
+ * Grey material: chi_P = chi_E = chi_F = chi = kappa rho.
+ *
+ * Units are the caller's: a_rad is the radiation constant (4 pi B / c =
+ * a_rad T^4) and T = (Egas - |m|^2 / (2 rho)) / (rho kB_over_mu / (gamma - 1)).
+ *
+ * Conventions for every call:
+ *  - Errors: every call returns an rhd_status; nothing is thrown across the
+ *    ABI.  rhd_last_error() describes the most recent failure of a context.
+ *  - Ownership: the library owns all device memory of a context (allocated in
+ *    rhd_init, released in rhd_destroy).  Caller buffers passed to get/set are
+ *    only read/written during the call (host buffers) or by work enqueued on
+ *    the context's stream before the call returns (device buffers); the caller
+ *    keeps ownership.
+ *  - Layout of every field array: ncell = n[0]*n[1]*n[2] doubles, cell
+ *    (i, j, k) at index i + n[0]*(j + n[1]*k) (x fastest).
+ *  - Threads: a context must not be used by two host threads at once.
+ */
+#ifndef RHD_H
+#define RHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rhd_ctx rhd_ctx; /* opaque; library-owned device state */
+
+typedef enum {
+  RHD_OK = 0,
+  RHD_ERR_ARG = 1,          /* invalid argument or rejected input values */
+  RHD_ERR_CUDA = 2,         /* a CUDA runtime call failed (see rhd_last_error) */
+  RHD_ERR_NEWTON = 3,       /* inner Newton iteration did not converge (Sec. 3.3) */
+  RHD_ERR_OUTER = 4,        /* outer iteration did not converge (Sec. 3.3) */
+  RHD_ERR_NONPHYSICAL = 5,  /* T <= 0, E <= 0 or a non-finite value */
+  RHD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  RHD_ERR_STATE = 7         /* call out of order (e.g. step before all fields set) */
+} rhd_status;
+
+typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_REFLECT = 1 } rhd_bc;
+typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_EDDINGTON = 1 } rhd_closure;
+/* HLL energy-flux dissipation (Sec. 4.3): TAU scales it by
+ * (1 - exp(-tau))/tau, tau = chi dx of the face; NONE is the paper's own
+ * uncorrected IMEX choice. */
+typedef enum { RHD_HLL_TAU = 0, RHD_HLL_NONE = 1 } rhd_hll_mode;
+/* FP64: everything in double.  MIXED: reconstruction, closure and HLL fluxes
+ * in single precision from double-precision differences; state, Newton solve,
+ * exchange terms and all updates in double. */
+typedef enum { RHD_PREC_FP64 = 0, RHD_PREC_MIXED = 1 } rhd_precision;
+
+/* Fields of the state.  F is the physical lab-frame radiation flux; KAPPA is
+ * the specific absorption opacity (chi = kappa rho).  RHO and KAPPA are
+ * static; the other eight are evolved. */
+typedef enum {
+  RHD_F_RHO = 0, RHD_F_MX, RHD_F_MY, RHD_F_MZ, RHD_F_EGAS, RHD_F_ERAD,
+  RHD_F_FX, RHD_F_FY, RHD_F_FZ, RHD_F_KAPPA, RHD_NFIELDS
+} rhd_field;
+
+typedef struct {
+  int ndim;            /* 1, 2 or 3 */
+  int64_t n[3];        /* cells per axis; axes >= ndim must be 1 */
+  double dx[3];        /* cell widths (> 0 on the active axes) */
+  int bc[3][2];        /* rhd_bc of the low/high face of each axis; a
+                          reflecting axis needs n >= 2 */
+  double gamma;        /* adiabatic index (> 1) */
+  double c;            /* speed of light (> 0) */
+  double chat;         /* reduced speed of light, 0 < chat <= c (Sec. 3.2) */
+  double a_rad;        /* radiation constant (> 0) */
+  double kB_over_mu;   /* k_B/mu: c_v = kB_over_mu/(gamma-1) per unit mass */
+  double cfl;          /* CFL number of the default step (> 0) */
+  int closure;         /* rhd_closure */
+  int vc_order;        /* 1: eq. numF1; 2: eq. numF2 and the (1+beta^2/2) terms */
+  int hll_mode;        /* rhd_hll_mode */
+  int precision;       /* rhd_precision */
+  double newton_rtol;  /* inner convergence tolerance (Sec. 3.3: 1e-13) */
+  double outer_rtol;   /* outer convergence tolerance (Sec. 3.3: 1e-13) */
+  int newton_max_iter; /* bound on Newton updates per inner solve */
+  int outer_max_iter;  /* bound on outer passes per local solve */
+} rhd_params;
+
+typedef struct {
+  int status;          /* rhd_status of this call */
+  int steps_done;      /* steps completed by this call */
+  int64_t fail_cell;   /* smallest failing cell index, -1 if none */
+  int fail_step;       /* step (within the call) that failed, -1 if none */
+  int fail_stage;      /* 1 or 2, 0 if none */
+  int max_newton;      /* most Newton updates of any local solve */
+  int max_outer;       /* most outer passes of any local solve */
+  int64_t sum_newton;  /* total Newton updates */
+  int64_t n_solves;    /* local solves performed */
+  double t;            /* simulated time of the context after the call */
+  double dt;           /* step size used */
+  int64_t sum_outer;   /* total outer passes */
+} rhd_step_info;
+
+/* Fill p with the library defaults: periodic, gamma 5/3, c = chat = 1,
+ * a_rad = kB_over_mu = 1, CFL 0.4, M1, v/c order 2, HLL TAU, FP64,
+ * tolerances 1e-13, 64 Newton updates, 32 outer passes.  The grid fields are
+ * zeroed; the caller sets ndim, n and dx. */
+void rhd_params_default(rhd_params* p);
+
+/* Check p without touching the GPU.  Returns RHD_OK or RHD_ERR_ARG; on error
+ * writes a message into msg (msglen bytes, may be NULL/0). */
+rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen);
+
+/* Default step of Sec. 4.3's wave-speed bound: cfl / (chat * sum_d 1/dx_d),
+ * or a negative value if p is invalid. */
+double rhd_default_dt(const rhd_params* p);
+
+/* Create a context on the current CUDA device: validates p, allocates the
+ * device state (two ping-pong copies of the evolved fields, the stage buffer,
+ * rho, kappa) and a private non-blocking stream.  *out is NULL on error. */
+rhd_status rhd_init(const rhd_params* p, rhd_ctx** out);
+
+/* Use an external CUDA stream (cudaStream_t passed as void*, e.g. torch's
+ * current stream) for all later work of ctx.  The handle is taken literally:
+ * NULL is CUDA's legacy default stream.  The caller keeps ownership of the
+ * stream and must keep it alive; rhd_use_private_stream switches back. */
+rhd_status rhd_set_stream(rhd_ctx* ctx, void* cuda_stream);
+
+/* Switch ctx back to the private stream created by rhd_init. */
+rhd_status rhd_use_private_stream(rhd_ctx* ctx);
+
+/* Copy one field in (count must equal ncell).  src is a host pointer
+ * (src_on_device = 0; pinned memory makes the copy asynchronous-capable) or a
+ * device pointer on the context's device (src_on_device = 1).  Values are
+ * validated on the device: rho > 0, Erad > 0 and kappa >= 0, all finite.  A
+ * rejected field returns RHD_ERR_ARG and stays marked unset, so rhd_step
+ * returns RHD_ERR_STATE until it is set again.  Synchronises the stream. */
+rhd_status rhd_state_set(rhd_ctx* ctx, int field, const double* src,
+                         int64_t count, int src_on_device);
+
+/* All ten fields at once from one field-major array of RHD_NFIELDS*ncell
+ * doubles (field f at src + f*ncell); same rules as rhd_state_set. */
+rhd_status rhd_state_set_all(rhd_ctx* ctx, const double* src, int64_t count,
+                             int src_on_device);
+
+/* Copy one field out of the current state (count must equal ncell) to a host
+ * or device buffer.  Synchronises the stream before returning. */
+rhd_status rhd_state_get(rhd_ctx* ctx, int field, double* dst, int64_t count,
+                         int dst_on_device);
+
+/* All ten fields to one field-major array of RHD_NFIELDS*ncell doubles. */
+rhd_status rhd_state_get_all(rhd_ctx* ctx, double* dst, int64_t count,
+                             int dst_on_device);
+
+/* Advance nsteps IMEX PD-ARS steps of size dt (dt <= 0: rhd_default_dt).
+ * Enqueues 2 stage kernels per step, then waits once and reads the device
+ * status.  On a failed step the context stays at the last completed step
+ * (ping-pong buffers) and info (nullable) names the step, stage and smallest
+ * failing cell. */
+rhd_status rhd_step(rhd_ctx* ctx, int nsteps, double dt, rhd_step_info* info);
+
+/* Enqueue nsteps without waiting (same semantics as rhd_step once the
+ * matching rhd_sync returns).  At most one rhd_step_async batch may be
+ * pending; kernels of later steps skip their work once a step has failed. */
+rhd_status rhd_step_async(rhd_ctx* ctx, int nsteps, double dt);
+
+/* Wait for the pending rhd_step_async batch and report it like rhd_step. */
+rhd_status rhd_sync(rhd_ctx* ctx, rhd_step_info* info);
+
+/* Conserved totals of the current state (Sec. 3.3): out[0] = sum over cells
+ * of (Egas + (c/chat) E) V, out[1..3] = sum of (m + F/(c chat)) V, V the cell
+ * volume.  Deterministic (fixed reduction order).  Synchronises. */
+rhd_status rhd_totals(rhd_ctx* ctx, double out[4]);
+
+/* Kernel timing with CUDA events on the context stream.  enable = 1 starts
+ * recording (clears previous records), 0 stops.  rhd_profile_read returns, per
+ * kernel kind k (0: stage 1, 1: stage 2, 2: totals), the number of launches
+ * and the summed device time in milliseconds; synchronises. */
+rhd_status rhd_profile(rhd_ctx* ctx, int enable);
+rhd_status rhd_profile_read(rhd_ctx* ctx, int64_t launches[3], double ms[3]);
+
+/* Number of kernels this context has launched since rhd_init. */
+int64_t rhd_launch_count(const rhd_ctx* ctx);
+
+/* Simulated time of the context (sum of completed step sizes). */
+double rhd_time(const rhd_ctx* ctx);
+
+/* Message of the most recent failure of ctx (never NULL). */
+const char* rhd_last_error(const rhd_ctx* ctx);
+
+/* Release all device memory and the private stream.  NULL is ignored. */
+void rhd_destroy(rhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RHD_H */

@@ -1,0 +1,607 @@
+// rhd_api.cu -- the C ABI declared in include/rhd.h.
+//
+// A context owns the device state of one grid: two ping-pong copies of the
+// eight evolved fields (y(n) and y(n+1)), the stage buffer y(n+1/2), the static
+// rho and kappa, a status block and the totals scratch.  A step enqueues two
+// kernels; nothing waits on the host until rhd_sync/rhd_step reads the status
+// block once per batch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "rhd_internal.cuh"
+
+using namespace rhd;
+
+namespace {
+
+struct Rec {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+thread_local char g_err[512] = "";
+
+void set_msg(char* buf, const char* fmt, va_list ap) {
+  vsnprintf(buf, 512, fmt, ap);
+}
+
+}  // namespace
+
+struct rhd_ctx {
+  rhd_params p;
+  int device = 0;
+  int ncell = 0;
+  Geometry g;
+  Physics ph;
+  double* ybuf[2] = {nullptr, nullptr};
+  double* yhalf = nullptr;
+  double* rho = nullptr;
+  double* kappa = nullptr;
+  DevStatus* d_status = nullptr;
+  DevStatus* h_status = nullptr;
+  double* d_partials = nullptr;
+  double* d_tot = nullptr;
+  double* h_tot = nullptr;
+  int* d_flag = nullptr;
+  int* h_flag = nullptr;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  int cur = 0;
+  unsigned fields_set = 0;
+  double t = 0.0;
+  bool pending = false;
+  int pending_n = 0;
+  double pending_dt = 0.0;
+  int pending_cur0 = 0;
+  int64_t launches = 0;
+  char err[512] = "";
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+static rhd_status fail(rhd_ctx* c, rhd_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  set_msg(c ? c->err : g_err, fmt, ap);
+  va_end(ap);
+  if (c) memcpy(g_err, c->err, sizeof(g_err));
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                       \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return fail((ctx), RHD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static const unsigned kAllFields = (1u << RHD_NFIELDS) - 1u;
+
+// evolved-field slot of an ABI field, -1 for the static ones
+static int slot_of(int field) {
+  switch (field) {
+    case RHD_F_EGAS: return Y_EGAS;
+    case RHD_F_MX: return Y_MX;
+    case RHD_F_MY: return Y_MY;
+    case RHD_F_MZ: return Y_MZ;
+    case RHD_F_ERAD: return Y_ERAD;
+    case RHD_F_FX: return Y_FX;
+    case RHD_F_FY: return Y_FY;
+    case RHD_F_FZ: return Y_FZ;
+    default: return -1;
+  }
+}
+
+static double* field_ptr(rhd_ctx* c, int field) {
+  if (field == RHD_F_RHO) return c->rho;
+  if (field == RHD_F_KAPPA) return c->kappa;
+  return c->ybuf[c->cur] + (size_t)slot_of(field) * c->ncell;
+}
+
+extern "C" {
+
+void rhd_params_default(rhd_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->ndim = 1;
+  for (int d = 0; d < 3; ++d) {
+    p->n[d] = 1;
+    p->dx[d] = 1.0;
+    p->bc[d][0] = p->bc[d][1] = RHD_BC_PERIODIC;
+  }
+  p->gamma = 5.0 / 3.0;
+  p->c = 1.0;
+  p->chat = 1.0;
+  p->a_rad = 1.0;
+  p->kB_over_mu = 1.0;
+  p->cfl = 0.4;
+  p->closure = RHD_CLOSURE_M1;
+  p->vc_order = 2;
+  p->hll_mode = RHD_HLL_TAU;
+  p->precision = RHD_PREC_FP64;
+  p->newton_rtol = 1e-13;
+  p->outer_rtol = 1e-13;
+  p->newton_max_iter = 64;
+  p->outer_max_iter = 32;
+}
+
+static int bad(char* msg, int len, const char* fmt, ...) {
+  if (msg && len > 0) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, (size_t)len, fmt, ap);
+    va_end(ap);
+  }
+  return 1;
+}
+
+rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
+  if (msg && msglen > 0) msg[0] = 0;
+  if (!p) return bad(msg, msglen, "params is NULL"), RHD_ERR_ARG;
+  if (p->ndim < 1 || p->ndim > 3)
+    return bad(msg, msglen, "ndim must be 1, 2 or 3 (got %d)", p->ndim), RHD_ERR_ARG;
+  long double cells = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (d < p->ndim) {
+      if (p->n[d] < 1)
+        return bad(msg, msglen, "n[%d] must be >= 1", d), RHD_ERR_ARG;
+      if (!(p->dx[d] > 0.0) || !std::isfinite(p->dx[d]))
+        return bad(msg, msglen, "dx[%d] must be positive and finite", d), RHD_ERR_ARG;
+      for (int s = 0; s < 2; ++s) {
+        if (p->bc[d][s] != RHD_BC_PERIODIC && p->bc[d][s] != RHD_BC_REFLECT)
+          return bad(msg, msglen, "bc[%d][%d] is not an rhd_bc", d, s), RHD_ERR_ARG;
+        if (p->bc[d][s] == RHD_BC_REFLECT && p->n[d] < 2)
+          return bad(msg, msglen, "reflecting axis %d needs n >= 2", d), RHD_ERR_ARG;
+      }
+      if ((p->bc[d][0] == RHD_BC_PERIODIC) != (p->bc[d][1] == RHD_BC_PERIODIC))
+        return bad(msg, msglen, "axis %d: periodic must apply to both faces", d),
+               RHD_ERR_ARG;
+    } else if (p->n[d] != 1) {
+      return bad(msg, msglen, "n[%d] must be 1 for ndim = %d", d, p->ndim), RHD_ERR_ARG;
+    }
+    cells *= (long double)p->n[d];
+  }
+  if (cells > 2147483647.0L)
+    return bad(msg, msglen, "grid has more than 2^31-1 cells"), RHD_ERR_ARG;
+  if (!(p->gamma > 1.0) || !std::isfinite(p->gamma))
+    return bad(msg, msglen, "gamma must be > 1"), RHD_ERR_ARG;
+  if (!(p->c > 0.0) || !std::isfinite(p->c))
+    return bad(msg, msglen, "c must be positive and finite"), RHD_ERR_ARG;
+  if (!(p->chat > 0.0) || !(p->chat <= p->c))
+    return bad(msg, msglen, "chat must satisfy 0 < chat <= c"), RHD_ERR_ARG;
+  if (!(p->a_rad > 0.0) || !std::isfinite(p->a_rad))
+    return bad(msg, msglen, "a_rad must be positive"), RHD_ERR_ARG;
+  if (!(p->kB_over_mu > 0.0) || !std::isfinite(p->kB_over_mu))
+    return bad(msg, msglen, "kB_over_mu must be positive"), RHD_ERR_ARG;
+  if (!(p->cfl > 0.0) || !std::isfinite(p->cfl))
+    return bad(msg, msglen, "cfl must be positive"), RHD_ERR_ARG;
+  if (p->closure != RHD_CLOSURE_M1 && p->closure != RHD_CLOSURE_EDDINGTON)
+    return bad(msg, msglen, "closure is not an rhd_closure"), RHD_ERR_ARG;
+  if (p->vc_order != 1 && p->vc_order != 2)
+    return bad(msg, msglen, "vc_order must be 1 or 2"), RHD_ERR_ARG;
+  if (p->hll_mode != RHD_HLL_TAU && p->hll_mode != RHD_HLL_NONE)
+    return bad(msg, msglen, "hll_mode is not an rhd_hll_mode"), RHD_ERR_ARG;
+  if (p->precision != RHD_PREC_FP64 && p->precision != RHD_PREC_MIXED)
+    return bad(msg, msglen, "precision is not an rhd_precision"), RHD_ERR_ARG;
+  if (!(p->newton_rtol > 0.0) || !(p->outer_rtol >= 0.0))
+    return bad(msg, msglen, "tolerances must be positive"), RHD_ERR_ARG;
+  if (p->newton_max_iter < 1 || p->outer_max_iter < 1)
+    return bad(msg, msglen, "iteration bounds must be >= 1"), RHD_ERR_ARG;
+  return RHD_OK;
+}
+
+double rhd_default_dt(const rhd_params* p) {
+  if (rhd_params_validate(p, nullptr, 0) != RHD_OK) return -1.0;
+  double s = 0.0;
+  for (int d = 0; d < p->ndim; ++d) s += 1.0 / p->dx[d];
+  return p->cfl / (p->chat * s);
+}
+
+}  // extern "C"
+
+static void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
+  memset(&g, 0, sizeof(g));
+  g.ndim = p->ndim;
+  int stride = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = (int)p->n[d];
+    g.stride[d] = stride;
+    stride *= g.n[d];
+    g.dx[d] = p->dx[d];
+    g.inv_dx[d] = 1.0 / p->dx[d];
+    g.bc[d][0] = p->bc[d][0];
+    g.bc[d][1] = p->bc[d][1];
+  }
+  g.ncell = stride;
+  memset(&ph, 0, sizeof(ph));
+  ph.c = p->c;
+  ph.chat = p->chat;
+  ph.a_rad = p->a_rad;
+  ph.cv_spec = p->kB_over_mu / (p->gamma - 1.0);
+  ph.inv_c = 1.0 / p->c;
+  ph.c_over_chat = p->c / p->chat;
+  ph.chat_over_c = p->chat / p->c;
+  ph.inv_c2 = 1.0 / (p->c * p->c);
+  ph.inv_cchat = 1.0 / (p->c * p->chat);
+  ph.closure = p->closure;
+  ph.vc_order = p->vc_order;
+  ph.hll_mode = p->hll_mode;
+  ph.newton_rtol = p->newton_rtol;
+  ph.outer_rtol = p->outer_rtol;
+  ph.newton_max = p->newton_max_iter;
+  ph.outer_max = p->outer_max_iter;
+}
+
+static void release(rhd_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  cudaFree(c->ybuf[0]);
+  cudaFree(c->ybuf[1]);
+  cudaFree(c->yhalf);
+  cudaFree(c->rho);
+  cudaFree(c->kappa);
+  cudaFree(c->d_status);
+  cudaFree(c->d_partials);
+  cudaFree(c->d_tot);
+  cudaFree(c->d_flag);
+  cudaFreeHost(c->h_status);
+  cudaFreeHost(c->h_tot);
+  cudaFreeHost(c->h_flag);
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+static cudaEvent_t take_event(rhd_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void recycle_records(rhd_ctx* c) {
+  for (auto& r : c->recs) {
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+}
+
+extern "C" {
+
+rhd_status rhd_init(const rhd_params* p, rhd_ctx** out) {
+  if (!out) return fail(nullptr, RHD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  char msg[256];
+  if (rhd_params_validate(p, msg, sizeof(msg)) != RHD_OK)
+    return fail(nullptr, RHD_ERR_ARG, "invalid params: %s", msg);
+  rhd_ctx* c = new rhd_ctx();
+  c->p = *p;
+  fill_geometry(p, c->g, c->ph);
+  c->ncell = c->g.ncell;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    fail(nullptr, RHD_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    delete c;
+    return RHD_ERR_CUDA;
+  }
+  const size_t N = (size_t)c->ncell;
+  const size_t ybytes = sizeof(double) * NY * N;
+  e = cudaMalloc(&c->ybuf[0], ybytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->ybuf[1], ybytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->yhalf, ybytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->rho, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->kappa, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(DevStatus));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->d_partials, sizeof(double) * totals_partials_needed());
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_tot, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_tot, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    fail(nullptr, RHD_ERR_CUDA, "allocating %zu bytes of device state: %s",
+         3 * ybytes + 2 * sizeof(double) * N, cudaGetErrorString(e));
+    release(c);
+    return RHD_ERR_CUDA;
+  }
+  c->stream = c->own;
+  *out = c;
+  return RHD_OK;
+}
+
+rhd_status rhd_set_stream(rhd_ctx* c, void* s) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->stream = (cudaStream_t)s;
+  return RHD_OK;
+}
+
+rhd_status rhd_use_private_stream(rhd_ctx* c) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->stream = c->own;
+  return RHD_OK;
+}
+
+static rhd_status check_copy_args(rhd_ctx* c, int field, const void* ptr, int64_t count) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (field < 0 || field >= RHD_NFIELDS) return fail(c, RHD_ERR_ARG, "bad field %d", field);
+  if (!ptr) return fail(c, RHD_ERR_ARG, "buffer is NULL");
+  if (count != (int64_t)c->ncell)
+    return fail(c, RHD_ERR_ARG, "count %lld != ncell %d", (long long)count, c->ncell);
+  return RHD_OK;
+}
+
+static rhd_status copy_in(rhd_ctx* c, int field, const double* src, int on_dev) {
+  CUDA_TRY(c, cudaMemcpyAsync(field_ptr(c, field), src, sizeof(double) * c->ncell,
+                              on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, launch_check_field(field, field_ptr(c, field), c->ncell, c->d_flag, c->stream));
+  c->launches += 1;
+  return RHD_OK;
+}
+
+rhd_status rhd_state_set(rhd_ctx* c, int field, const double* src, int64_t count,
+                         int src_on_device) {
+  rhd_status s = check_copy_args(c, field, src, count);
+  if (s != RHD_OK) return s;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  s = copy_in(c, field, src, src_on_device);
+  if (s != RHD_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (*c->h_flag) {
+    c->fields_set &= ~(1u << field);
+    return fail(c, RHD_ERR_ARG, "field %d holds a non-finite or out-of-range value", field);
+  }
+  c->fields_set |= 1u << field;
+  return RHD_OK;
+}
+
+rhd_status rhd_state_set_all(rhd_ctx* c, const double* src, int64_t count,
+                             int src_on_device) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (count != (int64_t)RHD_NFIELDS * c->ncell)
+    return fail(c, RHD_ERR_ARG, "count must be RHD_NFIELDS * ncell");
+  rhd_status s = check_copy_args(c, 0, src, c->ncell);
+  if (s != RHD_OK) return s;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  for (int f = 0; f < RHD_NFIELDS; ++f) {
+    s = copy_in(c, f, src + (size_t)f * c->ncell, src_on_device);
+    if (s != RHD_OK) return s;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (*c->h_flag) {
+    c->fields_set = 0;
+    return fail(c, RHD_ERR_ARG, "state holds a non-finite or out-of-range value");
+  }
+  c->fields_set = kAllFields;
+  return RHD_OK;
+}
+
+rhd_status rhd_state_get(rhd_ctx* c, int field, double* dst, int64_t count,
+                         int dst_on_device) {
+  rhd_status s = check_copy_args(c, field, dst, count);
+  if (s != RHD_OK) return s;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaMemcpyAsync(dst, field_ptr(c, field), sizeof(double) * c->ncell,
+                              dst_on_device ? cudaMemcpyDeviceToDevice
+                                            : cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RHD_OK;
+}
+
+rhd_status rhd_state_get_all(rhd_ctx* c, double* dst, int64_t count, int dst_on_device) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (count != (int64_t)RHD_NFIELDS * c->ncell)
+    return fail(c, RHD_ERR_ARG, "count must be RHD_NFIELDS * ncell");
+  rhd_status s = check_copy_args(c, 0, dst, c->ncell);
+  if (s != RHD_OK) return s;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  for (int f = 0; f < RHD_NFIELDS; ++f)
+    CUDA_TRY(c, cudaMemcpyAsync(dst + (size_t)f * c->ncell, field_ptr(c, f),
+                                sizeof(double) * c->ncell,
+                                dst_on_device ? cudaMemcpyDeviceToDevice
+                                              : cudaMemcpyDeviceToHost,
+                                c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RHD_OK;
+}
+
+static cudaError_t launch_recorded(rhd_ctx* c, int kind, int stage, const StageArgs& A) {
+  if (!c->prof) return launch_stage(stage, c->p.precision, A, c->stream);
+  Rec r;
+  r.a = take_event(c);
+  r.b = take_event(c);
+  r.kind = kind;
+  cudaEventRecord(r.a, c->stream);
+  cudaError_t e = launch_stage(stage, c->p.precision, A, c->stream);
+  cudaEventRecord(r.b, c->stream);
+  c->recs.push_back(r);
+  return e;
+}
+
+rhd_status rhd_step_async(rhd_ctx* c, int nsteps, double dt) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is already pending");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
+  if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
+  if (!std::isfinite(dt)) return fail(c, RHD_ERR_ARG, "dt is not finite");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+  c->launches += 1;
+  StageArgs A;
+  A.g = c->g;
+  A.ph = c->ph;
+  A.dt = dt;
+  A.rho = c->rho;
+  A.kappa = c->kappa;
+  A.st = c->d_status;
+  int cur = c->cur;
+  const int N = c->ncell;
+  for (int s = 0; s < nsteps; ++s) {
+    A.step = s;
+    slots_of<const double*>(A.yt, c->ybuf[cur], N);
+    slots_of<const double*>(A.yn, c->ybuf[cur], N);
+    slots_of<double*>(A.yo, c->yhalf, N);
+    CUDA_TRY(c, launch_recorded(c, 0, 1, A));
+    slots_of<const double*>(A.yt, c->yhalf, N);
+    slots_of<double*>(A.yo, c->ybuf[cur ^ 1], N);
+    CUDA_TRY(c, launch_recorded(c, 1, 2, A));
+    c->launches += 2;
+    cur ^= 1;
+  }
+  c->pending = true;
+  c->pending_n = nsteps;
+  c->pending_dt = dt;
+  c->pending_cur0 = c->cur;
+  return RHD_OK;
+}
+
+rhd_status rhd_sync(rhd_ctx* c, rhd_step_info* info) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (!c->pending) return fail(c, RHD_ERR_STATE, "no step batch is pending");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  c->pending = false;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const DevStatus& st = *c->h_status;
+  const int n = c->pending_n;
+  rhd_status code = RHD_OK;
+  int done = n;
+  int64_t cell = -1;
+  if (st.fail_key != ~0ull) {
+    code = (rhd_status)(st.fail_key & 0xffull);
+    cell = (int64_t)(st.fail_key >> 8);
+    done = st.fail_step;
+  }
+  c->cur = c->pending_cur0 ^ (done & 1);
+  c->t += done * c->pending_dt;
+  if (info) {
+    info->status = code;
+    info->steps_done = done;
+    info->fail_cell = cell;
+    info->fail_step = code == RHD_OK ? -1 : st.fail_step;
+    info->fail_stage = code == RHD_OK ? 0 : st.fail_stage;
+    info->max_newton = st.max_newton;
+    info->max_outer = st.max_outer;
+    info->sum_newton = (int64_t)st.sum_newton;
+    info->n_solves = (int64_t)st.n_solves;
+    info->sum_outer = (int64_t)st.sum_outer;
+    info->t = c->t;
+    info->dt = c->pending_dt;
+  }
+  if (code != RHD_OK)
+    return fail(c, code, "step %d stage %d failed at cell %lld (status %d)", st.fail_step,
+                st.fail_stage, (long long)cell, (int)code);
+  return RHD_OK;
+}
+
+rhd_status rhd_step(rhd_ctx* c, int nsteps, double dt, rhd_step_info* info) {
+  rhd_status s = rhd_step_async(c, nsteps, dt);
+  if (s != RHD_OK) {
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->status = s;
+      info->fail_cell = -1;
+      info->fail_step = -1;
+      info->t = c ? c->t : 0.0;
+    }
+    return s;
+  }
+  return rhd_sync(c, info);
+}
+
+rhd_status rhd_totals(rhd_ctx* c, double out[4]) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (!out) return fail(c, RHD_ERR_ARG, "out is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (c->prof) {
+    Rec r;
+    r.a = take_event(c);
+    r.b = take_event(c);
+    r.kind = 2;
+    cudaEventRecord(r.a, c->stream);
+    CUDA_TRY(c, launch_totals(c->g, c->ph, c->ybuf[c->cur], c->d_partials,
+                              totals_partials_needed(), c->d_tot, c->stream));
+    cudaEventRecord(r.b, c->stream);
+    c->recs.push_back(r);
+  } else {
+    CUDA_TRY(c, launch_totals(c->g, c->ph, c->ybuf[c->cur], c->d_partials,
+                              totals_partials_needed(), c->d_tot, c->stream));
+  }
+  c->launches += 2;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_tot, c->d_tot, sizeof(double) * 4,
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < 4; ++q) out[q] = c->h_tot[q];
+  return RHD_OK;
+}
+
+rhd_status rhd_profile(rhd_ctx* c, int enable) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (enable) recycle_records(c);
+  c->prof = enable != 0;
+  return RHD_OK;
+}
+
+rhd_status rhd_profile_read(rhd_ctx* c, int64_t launches[3], double ms[3]) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (!launches || !ms) return fail(c, RHD_ERR_ARG, "output is NULL");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 3; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, r.a, r.b));
+    launches[r.kind] += 1;
+    ms[r.kind] += (double)t;
+  }
+  return RHD_OK;
+}
+
+int64_t rhd_launch_count(const rhd_ctx* c) { return c ? c->launches : 0; }
+
+double rhd_time(const rhd_ctx* c) { return c ? c->t : 0.0; }
+
+const char* rhd_last_error(const rhd_ctx* c) { return c ? c->err : g_err; }
+
+void rhd_destroy(rhd_ctx* c) { release(c); }
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+// rhd_internal.cuh -- device-side building blocks of the IMEX PD-ARS step.
+//
+// Internal to the library (csrc/*.cu).  Every routine cites the passage of
+// He, Wibking & Krumholz (2024) it implements; readings of passages the paper
+// leaves open are the library's documented choices (M1 closure, PLM with the
+// monotonised-central limiter, symmetric HLL speeds floored at chat/sqrt(3),
+// E_tot = Egas + (c/chat) E, energy closure E = E(t) - (chat/c) dEgas).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rhd.h"
+
+namespace rhd {
+
+// evolved-field slots of a state buffer (NY * ncell doubles, slot-major)
+enum { Y_EGAS = 0, Y_MX, Y_MY, Y_MZ, Y_ERAD, Y_FX, Y_FY, Y_FZ, NY };
+
+// Device status block: the first failing launch records its step, stage and
+// the smallest failing cell; every later kernel of the batch sees the key and
+// skips its work, so the last good ping-pong buffer is never overwritten.
+struct DevStatus {
+  unsigned long long fail_key;  // (cell << 8) | rhd_status, ~0ull if none
+  int fail_step;
+  int fail_stage;
+  int max_newton;
+  int max_outer;
+  unsigned long long sum_newton;
+  unsigned long long n_solves;
+  unsigned long long sum_outer;
+};
+
+struct Geometry {
+  int ndim;
+  int n[3];
+  int stride[3];
+  int ncell;
+  int bc[3][2];
+  double dx[3];
+  double inv_dx[3];
+};
+
+struct Physics {
+  double c, chat, a_rad;
+  double cv_spec;       // kB_over_mu / (gamma - 1): C_v = rho cv_spec
+  double inv_c;         // 1/c
+  double c_over_chat;   // c/chat
+  double chat_over_c;   // chat/c
+  double inv_c2;        // 1/c^2
+  double inv_cchat;     // 1/(c chat)
+  int closure, vc_order, hll_mode;
+  double newton_rtol, outer_rtol;
+  int newton_max, outer_max;
+};
+
+struct StageArgs {
+  Geometry g;
+  Physics ph;
+  double dt;
+  int step;            // step index within the batch (for the status block)
+  const double* rho;
+  const double* kappa;
+  const double* yt[NY];  // state whose transport s(.) is taken, one pointer per slot
+  const double* yn[NY];  // y(n) (stage 2 only)
+  double* yo[NY];        // stage output
+  DevStatus* st;
+};
+
+// slot pointers of a slot-major buffer of NY * n doubles
+template <typename P>
+inline void slots_of(P* out, P base, int n) {
+  for (int q = 0; q < NY; ++q) out[q] = base + (size_t)q * n;
+}
+
+// ---------------------------------------------------------------- limiter
+// PLM slope with the monotonised-central limiter:
+// minmod(2 d-, (d- + d+)/2, 2 d+), zero unless all three share a sign.
+template <typename R>
+__device__ __forceinline__ R mc_slope(R um, R u0, R up) {
+  R dm = u0 - um;
+  R dp = up - u0;
+  bool pos = (dm > R(0)) && (dp > R(0));
+  bool neg = (dm < R(0)) && (dp < R(0));
+  R m = fmin(fabs(R(2) * dm), fmin(fabs(R(0.5) * (dm + dp)), fabs(R(2) * dp)));
+  return pos ? m : (neg ? -m : R(0));
+}
+
+// ---------------------------------------------------------------- closure
+// Levermore M1 closure (the paper leaves the closure free, Sec. 2.1):
+// D = (1 - xi)/2 I + (3 xi - 1)/2 n n, xi = (3 + 4 f^2)/(5 + 2 sqrt(4 - 3 f^2)),
+// f = |F|/(cE) in [0, 1].  Ft is F/c.  Returns the row D_d. (times E in P)
+// and D_dd.  Zero flux or the Eddington option give D = I/3.
+template <typename R>
+__device__ __forceinline__ void closure_row(int d, R E, const R Ft[3], int closure,
+                                            R P[3], R& Ddd) {
+  R F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
+  if (closure == RHD_CLOSURE_EDDINGTON || !(F2 > R(0))) {
+    Ddd = R(1) / R(3);
+    P[0] = P[1] = P[2] = R(0);
+    P[d] = E / R(3);
+    return;
+  }
+  R f2 = fmin(F2 / (E * E), R(1));
+  R xi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
+  R ha = R(0.5) * (R(1) - xi);
+  R hb = R(0.5) * (R(3) * xi - R(1)) / F2;
+  R bd = hb * Ft[d];
+  Ddd = ha + bd * Ft[d];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) P[j] = E * (bd * Ft[j]);
+  P[d] += E * ha;
+}
+
+// ------------------------------------------------------------------- HLL
+// Flux through one face along axis d (Sec. 3.3 Godunov step, Sec. 4.3 wave
+// speeds) for the RSLA system dE/dt = -chat div(Ft), dFt/dt = -chat div(P),
+// Ft = F/c.  Symmetric speeds S_R = -S_L = chat max(sqrt(D_dd,L),
+// sqrt(D_dd,R), 1/sqrt(3)), so HLL takes the form
+//   Phi = (Phi_L + Phi_R)/2 - S (U_R - U_L)/2,
+// with the optical-depth factor eps on the energy part (1 for HLL NONE).
+// Face states: PLM from the 4-cell stencil (am, a | b, bp), scaled back onto
+// |Ft| <= E when the reconstruction oversteps the free-streaming limit.
+// Returns false for a face state with E <= 0 (or NaN).
+template <typename R>
+__device__ __forceinline__ bool hll_face(int d, const R am[4], const R a[4],
+                                         const R b[4], const R bp[4], R eps,
+                                         R chat, int closure, R out[4]) {
+  R L[4], Rr[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    L[q] = a[q] + R(0.5) * mc_slope(am[q], a[q], b[q]);
+    Rr[q] = b[q] - R(0.5) * mc_slope(a[q], b[q], bp[q]);
+  }
+  if (!(L[0] > R(0)) || !(Rr[0] > R(0))) return false;
+  {
+    R n2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+    if (n2 > L[0] * L[0]) {
+      R s = L[0] / sqrt(n2);
+      L[1] *= s; L[2] *= s; L[3] *= s;
+    }
+    n2 = Rr[1] * Rr[1] + Rr[2] * Rr[2] + Rr[3] * Rr[3];
+    if (n2 > Rr[0] * Rr[0]) {
+      R s = Rr[0] / sqrt(n2);
+      Rr[1] *= s; Rr[2] *= s; Rr[3] *= s;
+    }
+  }
+  R PL[3], PR[3], DL, DR;
+  closure_row(d, L[0], &L[1], closure, PL, DL);
+  closure_row(d, Rr[0], &Rr[1], closure, PR, DR);
+  R S = chat * sqrt(fmax(fmax(DL, DR), R(1) / R(3)));
+  R hc = R(0.5) * chat;
+  R hS = R(0.5) * S;
+  out[0] = hc * (L[1 + d] + Rr[1 + d]) - eps * hS * (Rr[0] - L[0]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) out[1 + j] = hc * (PL[j] + PR[j]) - hS * (Rr[1 + j] - L[1 + j]);
+  return true;
+}
+
+// Optical-depth factor of the HLL energy dissipation (reading of Sec. 4.3):
+// (1 - exp(-tau))/tau, 1 in the thin limit, 1/tau in the thick limit.
+__device__ __forceinline__ double tau_factor(double tau) {
+  return tau > 0.0 ? -expm1(-tau) / tau : 1.0;
+}
+
+// ------------------------------------------------------------ local solve
+// Implicit stage of one cell (Sec. 3.3), grey chi.  y = {Egas, m, E, F}
+// holds the explicit state on entry and the solution on exit.  tdt = theta dt.
+//
+// Inner stage: Newton on (Egas, R) for eq. (FGFR) with eq. (Rnew) and the
+// paper's Jacobian (beta^2 dropped).  The R-row is multiplied by
+// k = chat chi theta dt, which leaves the Newton iterates unchanged and keeps
+// the system regular for small k:
+//   r0 = Egas - Egas(t) + (c/chat) R
+//   r1 = k F_R = k (aT^4 - E(t) - R) + (k v.F/c^2 - R)/g,  g = 1 + beta^2/2
+//   J  = [[1, c/chat], [k 4 a T^3 / C_v, -1 - k]]
+// converged when |r0| < eps E_tot and (c/chat)|r1| <= eps E_tot k,
+// E_tot = Egas(t) + (c/chat) E(t).
+// Energy closure: E = E(t) - (chat/c)(Egas - Egas(t)).
+// Outer stage: eq. (numF2) (order 2) or (numF1) (order 1) for F with P from
+// the new E and the previous outer flux, momentum m = m(t) - (F - F(t))/(c chat),
+// repeated until Q = k[(g - 1)(aT^4 - E) + v.F/c^2] settles.
+__device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double rho,
+                                           double chi, double y[8], int& nn, int& no) {
+  nn = 0;
+  no = 0;
+  if (chi == 0.0) return RHD_OK;
+  const double Cv = rho * ph.cv_spec;
+  const double inv_Cv = 1.0 / Cv;
+  const double inv_rho = 1.0 / rho;
+  const double cr = ph.c_over_chat;
+  const double a = ph.a_rad;
+  const double Eg0 = y[0], E0 = y[4];
+  const double Etot = Eg0 + cr * E0;
+  const double k = ph.chat * chi * tdt;
+  const double tolG = ph.newton_rtol * Etot;
+  const double tolR = tolG * k;
+  double Eg = Eg0, R = 0.0, E = E0;
+  double m[3] = {y[1], y[2], y[3]};
+  double F[3] = {y[5], y[6], y[7]};
+
+  for (int outer = 0; outer < ph.outer_max; ++outer) {
+    no = outer + 1;
+    double v[3] = {m[0] * inv_rho, m[1] * inv_rho, m[2] * inv_rho};
+    double beta2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * ph.inv_c2;
+    double g = (ph.vc_order == 2) ? 1.0 + 0.5 * beta2 : 1.0;
+    double inv_g = 1.0 / g;
+    double w = (v[0] * F[0] + v[1] * F[1] + v[2] * F[2]) * ph.inv_c2;
+    double Ekin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * inv_rho;
+    double kE0 = k * E0;
+    double kw = k * w;
+
+    bool conv = false;
+    for (int it = 0;; ++it) {
+      double T = (Eg - Ekin) * inv_Cv;
+      if (!(T > 0.0) || !isfinite(T) || !isfinite(R)) return RHD_ERR_NONPHYSICAL;
+      double T2 = T * T;
+      double aT4 = a * T2 * T2;
+      double r0 = (Eg - Eg0) + cr * R;
+      double r1 = (k * aT4 - kE0 - k * R) + (kw - R) * inv_g;
+      if (fabs(r0) < tolG && cr * fabs(r1) <= tolR) {
+        conv = true;
+        break;
+      }
+      if (it >= ph.newton_max) break;
+      double J10 = 4.0 * k * a * T2 * T * inv_Cv;
+      double opk = 1.0 + k;
+      double det = -opk - cr * J10;
+      double inv_det = 1.0 / det;
+      double dEg = (r0 * opk + cr * r1) * inv_det;
+      double dR = (r0 * J10 - r1) * inv_det;
+      Eg += dEg;
+      R += dR;
+      ++nn;
+    }
+    if (!conv) return RHD_ERR_NEWTON;
+
+    E = E0 - ph.chat_over_c * (Eg - Eg0);
+    double T = (Eg - Ekin) * inv_Cv;
+    double T2 = T * T;
+    double aT4 = a * T2 * T2;
+
+    // v_j P_ji of the closure at (E, F)
+    double vP[3];
+    {
+      double Ft[3] = {F[0] * ph.inv_c, F[1] * ph.inv_c, F[2] * ph.inv_c};
+      double F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
+      if (ph.closure == RHD_CLOSURE_EDDINGTON || !(F2 > 0.0)) {
+        double e3 = E / 3.0;
+        vP[0] = v[0] * e3; vP[1] = v[1] * e3; vP[2] = v[2] * e3;
+      } else {
+        double f2 = fmin(F2 / (E * E), 1.0);
+        double xi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
+        double ha = 0.5 * (1.0 - xi);
+        double hb = 0.5 * (3.0 * xi - 1.0) / F2;
+        double vFt = v[0] * Ft[0] + v[1] * Ft[1] + v[2] * Ft[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) vP[i] = E * (ha * v[i] + hb * vFt * Ft[i]);
+      }
+    }
+    double inv_den = 1.0 / (1.0 + k * g);
+    double Fn[3], mn[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Fn[i] = (y[5 + i] + k * (aT4 * v[i] + vP[i])) * inv_den;
+      mn[i] = y[1 + i] - (Fn[i] - y[5 + i]) * ph.inv_cchat;
+    }
+    double Q_old = k * ((g - 1.0) * (aT4 - E) + w);
+    double vn[3] = {mn[0] * inv_rho, mn[1] * inv_rho, mn[2] * inv_rho};
+    double beta2n = (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]) * ph.inv_c2;
+    double gn = (ph.vc_order == 2) ? 1.0 + 0.5 * beta2n : 1.0;
+    double wn = (vn[0] * Fn[0] + vn[1] * Fn[1] + vn[2] * Fn[2]) * ph.inv_c2;
+    double Q_new = k * ((gn - 1.0) * (aT4 - E) + wn);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      F[i] = Fn[i];
+      m[i] = mn[i];
+    }
+    double dQ = fabs(Q_new - Q_old);
+    if (dQ <= ph.outer_rtol * fabs(Q_old) || dQ <= ph.outer_rtol * fabs(R)) {
+      y[0] = Eg;
+      y[1] = m[0]; y[2] = m[1]; y[3] = m[2];
+      y[4] = E;
+      y[5] = F[0]; y[6] = F[1]; y[7] = F[2];
+      if (!(E > 0.0) || !isfinite(E) || !isfinite(F[0]) || !isfinite(F[1]) ||
+          !isfinite(F[2]))
+        return RHD_ERR_NONPHYSICAL;
+      return RHD_OK;
+    }
+  }
+  return RHD_ERR_OUTER;
+}
+
+// ------------------------------------------------------------ launchers
+// (host side, defined in the .cu files)
+cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s);
+cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
+cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
+                          double* partials, int npart, double* out4, cudaStream_t s);
+int totals_partials_needed();
+cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
+                               cudaStream_t s);
+
+}  // namespace rhd

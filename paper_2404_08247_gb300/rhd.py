@@ -1,0 +1,316 @@
+"""ctypes binding of the C ABI in ``include/rhd.h`` (librhd.so).
+
+Argument marshalling only: every step of the radiation update runs in the
+CUDA kernels behind the ABI.  The functions keep the C names; ``RHDContext``
+adds a small object wrapper that accepts numpy arrays (host) or torch CUDA
+tensors (device) in the (10, nz, ny, nx) field-major layout of
+``paper_2404_08247_gb300.inputs``.
+
+There is no fallback: if librhd.so is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RHD_OK, RHD_ERR_ARG, RHD_ERR_CUDA, RHD_ERR_NEWTON, RHD_ERR_OUTER, \
+    RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE = range(8)
+STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "newton", 4: "outer",
+                5: "nonphysical", 6: "timeout", 7: "state"}
+RHD_BC_PERIODIC, RHD_BC_REFLECT = 0, 1
+RHD_CLOSURE_M1, RHD_CLOSURE_EDDINGTON = 0, 1
+RHD_HLL_TAU, RHD_HLL_NONE = 0, 1
+RHD_PREC_FP64, RHD_PREC_MIXED = 0, 1
+RHD_NFIELDS = 10
+(RHD_F_RHO, RHD_F_MX, RHD_F_MY, RHD_F_MZ, RHD_F_EGAS, RHD_F_ERAD, RHD_F_FX,
+ RHD_F_FY, RHD_F_FZ, RHD_F_KAPPA) = range(10)
+
+_BC = {"periodic": RHD_BC_PERIODIC, "reflect": RHD_BC_REFLECT}
+_CLOSURE = {"m1": RHD_CLOSURE_M1, "eddington": RHD_CLOSURE_EDDINGTON}
+_HLL = {"tau": RHD_HLL_TAU, "none": RHD_HLL_NONE}
+_PREC = {"fp64": RHD_PREC_FP64, "mixed": RHD_PREC_MIXED}
+
+
+class RHDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class rhd_params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int64 * 3),
+        ("dx", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("gamma", ctypes.c_double),
+        ("c", ctypes.c_double),
+        ("chat", ctypes.c_double),
+        ("a_rad", ctypes.c_double),
+        ("kB_over_mu", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("closure", ctypes.c_int),
+        ("vc_order", ctypes.c_int),
+        ("hll_mode", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("newton_rtol", ctypes.c_double),
+        ("outer_rtol", ctypes.c_double),
+        ("newton_max_iter", ctypes.c_int),
+        ("outer_max_iter", ctypes.c_int),
+    ]
+
+
+class rhd_step_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("steps_done", ctypes.c_int),
+        ("fail_cell", ctypes.c_int64),
+        ("fail_step", ctypes.c_int),
+        ("fail_stage", ctypes.c_int),
+        ("max_newton", ctypes.c_int),
+        ("max_outer", ctypes.c_int),
+        ("sum_newton", ctypes.c_int64),
+        ("n_solves", ctypes.c_int64),
+        ("t", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("sum_outer", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every function the header declares: name -> (restype, argtypes)
+_P = ctypes.POINTER(rhd_params)
+_V = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.c_int64
+SIGNATURES = {
+    "rhd_params_default": (None, [_P]),
+    "rhd_params_validate": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int]),
+    "rhd_default_dt": (ctypes.c_double, [_P]),
+    "rhd_init": (ctypes.c_int, [_P, ctypes.POINTER(_V)]),
+    "rhd_set_stream": (ctypes.c_int, [_V, _V]),
+    "rhd_use_private_stream": (ctypes.c_int, [_V]),
+    "rhd_state_set": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
+    "rhd_state_set_all": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
+    "rhd_state_get": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
+    "rhd_state_get_all": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
+    "rhd_step": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double,
+                                ctypes.POINTER(rhd_step_info)]),
+    "rhd_step_async": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
+    "rhd_sync": (ctypes.c_int, [_V, ctypes.POINTER(rhd_step_info)]),
+    "rhd_totals": (ctypes.c_int, [_V, _D]),
+    "rhd_profile": (ctypes.c_int, [_V, ctypes.c_int]),
+    "rhd_profile_read": (ctypes.c_int, [_V, ctypes.POINTER(_I64), _D]),
+    "rhd_launch_count": (_I64, [_V]),
+    "rhd_time": (ctypes.c_double, [_V]),
+    "rhd_last_error": (ctypes.c_char_p, [_V]),
+    "rhd_destroy": (None, [_V]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load librhd.so (built in-tree by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "librhd.so not found at %s: build it with __graft_entry__.build() "
+            "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, ctx=None):
+    if st != RHD_OK:
+        msg = load().rhd_last_error(ctx)
+        raise RHDError(st, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------ thin wrappers
+
+def rhd_params_default() -> rhd_params:
+    p = rhd_params()
+    load().rhd_params_default(ctypes.byref(p))
+    return p
+
+
+def rhd_params_validate(p: rhd_params):
+    buf = ctypes.create_string_buffer(256)
+    st = load().rhd_params_validate(ctypes.byref(p), buf, 256)
+    return st, buf.value.decode()
+
+
+def rhd_default_dt(p: rhd_params) -> float:
+    return load().rhd_default_dt(ctypes.byref(p))
+
+
+def params_from_problem(prob: dict, precision: str | int = "fp64") -> rhd_params:
+    """rhd_params for a problem dict of ``paper_2404_08247_gb300.inputs``."""
+    p = rhd_params_default()
+    p.ndim = int(prob["ndim"])
+    n = list(prob["n"]) + [1] * (3 - len(prob["n"]))
+    dx = list(prob["dx"]) + [1.0] * (3 - len(prob["dx"]))
+    bc = prob.get("bc", "periodic")
+    for d in range(3):
+        p.n[d] = int(n[d])
+        p.dx[d] = float(dx[d])
+        for s in range(2):
+            kind = bc if isinstance(bc, str) else (bc[d][s] if d < len(bc) else "periodic")
+            p.bc[d][s] = _BC[kind]
+    p.gamma = float(prob["gamma"])
+    p.c = float(prob["c"])
+    p.chat = float(prob["chat"])
+    p.a_rad = float(prob.get("a_rad", 1.0))
+    p.kB_over_mu = float(prob.get("kB_over_mu", 1.0))
+    p.cfl = float(prob.get("cfl", 0.4))
+    p.closure = _CLOSURE[prob.get("closure", "m1")]
+    p.vc_order = int(prob.get("vc_order", 2))
+    p.hll_mode = _HLL[prob.get("hll_mode", "tau")]
+    p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    p.newton_rtol = float(prob.get("newton_rtol", 1e-13))
+    p.outer_rtol = float(prob.get("outer_rtol", 1e-13))
+    p.newton_max_iter = int(prob.get("newton_max_iter", 64))
+    p.outer_max_iter = int(prob.get("outer_max_iter", 32))
+    return p
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or torch tensor (float64, contiguous)."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 array")
+        return x.ctypes.data, 0
+    # torch tensor
+    if str(x.dtype) != "torch.float64" or not x.is_contiguous():
+        raise ValueError("expected a contiguous float64 tensor")
+    return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+class RHDContext:
+    """One grid's device state behind the C ABI."""
+
+    def __init__(self, prob: dict, precision="fp64", stream=None):
+        self.lib = load()
+        self.prob = prob
+        self.params = params_from_problem(prob, precision)
+        h = ctypes.c_void_p()
+        _check(self.lib.rhd_init(ctypes.byref(self.params), ctypes.byref(h)))
+        self.h = h
+        n = self.params.n
+        self.ncell = int(n[0] * n[1] * n[2])
+        self.shape = (RHD_NFIELDS, int(n[2]), int(n[1]), int(n[0]))
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rhd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream or an integer cudaStream_t handle (0 is
+        CUDA's legacy default stream, torch's default); None switches back to
+        the context's private stream."""
+        if stream is None:
+            _check(self.lib.rhd_use_private_stream(self.h), self.h)
+            return
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(self.lib.rhd_set_stream(self.h, ctypes.c_void_p(int(handle))), self.h)
+
+    def set_state(self, U):
+        ptr, dev = _ptr(U)
+        _check(self.lib.rhd_state_set_all(self.h, ctypes.c_void_p(ptr),
+                                          RHD_NFIELDS * self.ncell, dev), self.h)
+
+    def set_field(self, field: int, x):
+        ptr, dev = _ptr(x)
+        _check(self.lib.rhd_state_set(self.h, field, ctypes.c_void_p(ptr),
+                                      self.ncell, dev), self.h)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        ptr, dev = _ptr(out)
+        _check(self.lib.rhd_state_get_all(self.h, ctypes.c_void_p(ptr),
+                                          RHD_NFIELDS * self.ncell, dev), self.h)
+        return out
+
+    def get_field(self, field: int, out=None):
+        if out is None:
+            out = np.empty(self.shape[1:], dtype=np.float64)
+        ptr, dev = _ptr(out)
+        _check(self.lib.rhd_state_get(self.h, field, ctypes.c_void_p(ptr),
+                                      self.ncell, dev), self.h)
+        return out
+
+    def step(self, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
+        info = rhd_step_info()
+        st = self.lib.rhd_step(self.h, int(nsteps), float(dt), ctypes.byref(info))
+        if raise_on_error:
+            _check(st, self.h)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def step_async(self, nsteps: int = 1, dt: float = 0.0):
+        _check(self.lib.rhd_step_async(self.h, int(nsteps), float(dt)), self.h)
+
+    def sync(self, raise_on_error=True) -> dict:
+        info = rhd_step_info()
+        st = self.lib.rhd_sync(self.h, ctypes.byref(info))
+        if raise_on_error:
+            _check(st, self.h)
+        return info.as_dict()
+
+    def totals(self) -> np.ndarray:
+        out = np.zeros(4, dtype=np.float64)
+        _check(self.lib.rhd_totals(self.h, out.ctypes.data_as(_D)), self.h)
+        return out
+
+    def profile(self, enable: bool):
+        _check(self.lib.rhd_profile(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self):
+        launches = (_I64 * 3)()
+        ms = (ctypes.c_double * 3)()
+        _check(self.lib.rhd_profile_read(self.h, launches, ms), self.h)
+        return list(launches), list(ms)
+
+    def launch_count(self) -> int:
+        return int(self.lib.rhd_launch_count(self.h))
+
+    def time(self) -> float:
+        return float(self.lib.rhd_time(self.h))
+
+    def default_dt(self) -> float:
+        return rhd_default_dt(self.params)

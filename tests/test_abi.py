@@ -1,0 +1,133 @@
+"""The C ABI library: loads, exports every declared symbol, and its host-side
+logic (parameter validation, default step) behaves as the header states.
+No GPU work: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2404_08247_gb300 import build as B
+from paper_2404_08247_gb300 import inputs as I
+
+HEADER = os.path.join(B.INCLUDE, "rhd.h")
+
+
+@pytest.fixture(scope="module")
+def rhd():
+    B.build()
+    from paper_2404_08247_gb300 import rhd as R
+    R.load()
+    return R
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rhd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rhd_init", "rhd_step", "rhd_state_get", "rhd_state_set",
+                     "rhd_totals", "rhd_destroy", "rhd_set_stream"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(rhd):
+    lib = ctypes.CDLL(B.LIB)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    # the binding wraps exactly the declared functions
+    assert sorted(rhd.SIGNATURES) == declared_functions()
+
+
+def test_struct_layouts_match_header(rhd, tmp_path):
+    """sizeof/offsetof of the ABI structs, as the C compiler lays them out,
+    equal the ctypes mirrors of the binding."""
+    fields = {"rhd_params": [f for f, _ in rhd.rhd_params._fields_],
+              "rhd_step_info": [f for f, _ in rhd.rhd_step_info._fields_]}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rhd.h"',
+             "int main(void) {"]
+    for st, fl in fields.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st, st))
+        for f in fl:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st, f, st, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", B.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True,
+                                                 text=True, check=True).stdout.splitlines())
+    for st, fl in fields.items():
+        cls = getattr(rhd, st)
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f in fl:
+            assert int(out["%s.%s" % (st, f)]) == getattr(cls, f).offset, (st, f)
+
+
+def test_defaults_and_validation(rhd):
+    p = rhd.rhd_params_default()
+    assert p.c == 1.0 and p.chat == 1.0 and abs(p.gamma - 5 / 3) < 1e-15
+    assert p.newton_rtol == 1e-13 and p.outer_rtol == 1e-13
+    assert p.hll_mode == rhd.RHD_HLL_TAU and p.vc_order == 2
+    st, msg = rhd.rhd_params_validate(p)
+    assert st == rhd.RHD_OK, msg
+
+    def bad(**kw):
+        q = rhd.rhd_params_default()
+        for k, v in kw.items():
+            setattr(q, k, v)
+        st, msg = rhd.rhd_params_validate(q)
+        assert st == rhd.RHD_ERR_ARG and msg, kw
+        return msg
+
+    bad(ndim=0)
+    bad(ndim=4)
+    bad(gamma=1.0)
+    bad(chat=2.0)          # chat > c
+    bad(chat=0.0)
+    bad(cfl=-1.0)
+    bad(vc_order=3)
+    bad(closure=7)
+    bad(precision=5)
+    bad(newton_max_iter=0)
+    q = rhd.rhd_params_default()
+    q.n[0] = 1
+    q.bc[0][0] = q.bc[0][1] = rhd.RHD_BC_REFLECT
+    assert rhd.rhd_params_validate(q)[0] == rhd.RHD_ERR_ARG
+    q = rhd.rhd_params_default()
+    q.n[1] = 4  # axis beyond ndim must be 1
+    assert rhd.rhd_params_validate(q)[0] == rhd.RHD_ERR_ARG
+    q = rhd.rhd_params_default()
+    q.dx[0] = float("nan")
+    assert rhd.rhd_params_validate(q)[0] == rhd.RHD_ERR_ARG
+    q = rhd.rhd_params_default()
+    q.n[0] = 1 << 31
+    assert rhd.rhd_params_validate(q)[0] == rhd.RHD_ERR_ARG
+
+
+def test_init_rejects_bad_params_before_touching_the_device(rhd):
+    q = rhd.rhd_params_default()
+    q.gamma = 0.5
+    h = ctypes.c_void_p()
+    st = rhd.load().rhd_init(ctypes.byref(q), ctypes.byref(h))
+    assert st == rhd.RHD_ERR_ARG and not h.value
+    assert b"gamma" in rhd.load().rhd_last_error(None)
+
+
+def test_default_dt_matches_oracle(rhd, oracle_mod):
+    for prob in (I.static_diffusion_1d(n=64)[0],
+                 I.base_problem(3, [8, 6, 4], [0.1, 0.2, 0.3], c=5.0, chat=2.0)):
+        p = rhd.params_from_problem(prob)
+        assert rhd.rhd_default_dt(p) == pytest.approx(oracle_mod.dt(prob), rel=1e-15)
+
+
+def test_problem_mapping(rhd):
+    prob = I.regime_sweep_1d(n=64)[0]
+    p = rhd.params_from_problem(prob, "mixed")
+    assert p.precision == rhd.RHD_PREC_MIXED
+    assert p.n[0] == 64 and p.n[1] == 1 and p.ndim == 1
+    assert p.chat == prob["chat"] and p.c == prob["c"]
