@@ -306,20 +306,28 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
 
     /* reading: the "terms proportional to v and F in R" are
      * Q = theta dt chat chi [(g - 1)(aT^4 - E) + v.F/c^2]; compare the Q the
-     * inner stage used with the Q of the updated v and F. */
+     * inner stage used with the Q of the updated v and F.  The relative change
+     * is also measured against the magnitude of those terms,
+     * Qs = theta dt chat chi [|(g - 1)(aT^4 - E)| + sum_i |v_i F_i|/c^2], so
+     * that a Q which is a cancelling sum cannot cycle at its rounding level. */
     double Q_old = chat * chi * tdt * ((g - 1.0) * (aT4 - E) + vF / (c * c));
     double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
     double beta2n = (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]) / (c * c);
     double gn = (p->vc_order == 2) ? 1.0 + 0.5 * beta2n : 1.0;
     double vFn = vn[0] * Fn[0] + vn[1] * Fn[1] + vn[2] * Fn[2];
     double Q_new = chat * chi * tdt * ((gn - 1.0) * (aT4 - E) + vFn / (c * c));
+    double Q_scale = chat * chi * tdt *
+                     (fabs((gn - 1.0) * (aT4 - E)) +
+                      (fabs(vn[0] * Fn[0]) + fabs(vn[1] * Fn[1]) + fabs(vn[2] * Fn[2])) /
+                          (c * c));
 
     for (int i = 0; i < 3; ++i) {
       F[i] = Fn[i];
       m[i] = mn[i];
     }
     double dQ = fabs(Q_new - Q_old);
-    if (dQ <= p->outer_rtol * fabs(Q_old) || dQ <= p->outer_rtol * fabs(R)) {
+    if (dQ <= p->outer_rtol * fabs(Q_old) || dQ <= p->outer_rtol * fabs(R) ||
+        dQ <= p->outer_rtol * Q_scale) {
       y[0] = Eg;
       y[1] = m[0];
       y[2] = m[1];

@@ -72,6 +72,8 @@ static rhd_status fail(rhd_ctx* c, rhd_status s, const char* fmt, ...) {
   return s;
 }
 
+void rhd::set_global_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 #define CUDA_TRY(ctx, call)                                                       \
   do {                                                                            \
     cudaError_t e_ = (call);                                                      \

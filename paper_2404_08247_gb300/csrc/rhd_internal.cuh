@@ -179,7 +179,8 @@ __device__ __forceinline__ double tau_factor(double tau) {
 // Energy closure: E = E(t) - (chat/c)(Egas - Egas(t)).
 // Outer stage: eq. (numF2) (order 2) or (numF1) (order 1) for F with P from
 // the new E and the previous outer flux, momentum m = m(t) - (F - F(t))/(c chat),
-// repeated until Q = k[(g - 1)(aT^4 - E) + v.F/c^2] settles.
+// repeated until Q = k[(g - 1)(aT^4 - E) + v.F/c^2] settles: its change is at
+// most outer_rtol times |Q|, |R| or the magnitude of its terms.
 __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double rho,
                                            double chi, double y[8], int& nn, int& no) {
   nn = 0;
@@ -271,13 +272,18 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
     double gn = (ph.vc_order == 2) ? 1.0 + 0.5 * beta2n : 1.0;
     double wn = (vn[0] * Fn[0] + vn[1] * Fn[1] + vn[2] * Fn[2]) * ph.inv_c2;
     double Q_new = k * ((gn - 1.0) * (aT4 - E) + wn);
+    // magnitude of the terms of Q: the rounding level of a cancelling v.F
+    double Q_scale = k * (fabs((gn - 1.0) * (aT4 - E)) +
+                          (fabs(vn[0] * Fn[0]) + fabs(vn[1] * Fn[1]) + fabs(vn[2] * Fn[2])) *
+                              ph.inv_c2);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       F[i] = Fn[i];
       m[i] = mn[i];
     }
     double dQ = fabs(Q_new - Q_old);
-    if (dQ <= ph.outer_rtol * fabs(Q_old) || dQ <= ph.outer_rtol * fabs(R)) {
+    if (dQ <= ph.outer_rtol * fabs(Q_old) || dQ <= ph.outer_rtol * fabs(R) ||
+        dQ <= ph.outer_rtol * Q_scale) {
       y[0] = Eg;
       y[1] = m[0]; y[2] = m[1]; y[3] = m[2];
       y[4] = E;
@@ -300,5 +306,7 @@ cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
 int totals_partials_needed();
 cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
                                cudaStream_t s);
+// message returned by rhd_last_error(NULL) on this thread
+void set_global_error(const char* msg);
 
 }  // namespace rhd
