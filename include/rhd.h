@@ -201,6 +201,36 @@ const char* rhd_last_error(const rhd_ctx* ctx);
 /* Release all device memory and the private stream.  NULL is ignored. */
 void rhd_destroy(rhd_ctx* ctx);
 
+/* Largest grid, in cells, that rhd_step_noalloc accepts. */
+#define RHD_NOALLOC_MAX_CELLS 262144
+
+/* One IMEX step that allocates no device memory.  The paper has no
+ * counterpart to this call: it serves callers that cannot allocate, such as
+ * code whose device memory is wholly owned by another allocator (a
+ * framework's caching pool) or code that must not call cudaMalloc/cudaFree
+ * because those calls can synchronise the whole device.
+ *
+ * state_in, state_out: device pointers on the current device, each holding
+ * RHD_NFIELDS*ncell doubles, field-major as in rhd_state_set_all; they must
+ * not overlap.  state_out receives y(n+1) (rho and kappa are copied).  Input
+ * values are not checked.  dt <= 0 selects rhd_default_dt(p); stream is a
+ * cudaStream_t (NULL: the legacy default stream).  The caller owns both
+ * buffers.
+ *
+ * The stage buffer y(n+1/2) and the status block live in file-scope device
+ * arrays sized for RHD_NOALLOC_MAX_CELLS cells (16 MiB), which every GPU that
+ * loads the library holds until the process exits; a larger grid returns
+ * RHD_ERR_ARG with a message.  The first call on a device resolves the
+ * arrays' device addresses (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the arrays: each call clears
+ * the status block and rewrites the stage buffer, and calls that overlap on
+ * the GPU (other streams or host threads) race.  The call waits for the
+ * stream to read the status; info (nullable) is filled as by rhd_step, with
+ * t = dt.  Messages: rhd_last_error(NULL). */
+rhd_status rhd_step_noalloc(const rhd_params* p, const double* state_in,
+                            double* state_out, double dt, void* stream,
+                            rhd_step_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,7 +112,10 @@ SIGNATURES = {
     "rhd_time": (ctypes.c_double, [_V]),
     "rhd_last_error": (ctypes.c_char_p, [_V]),
     "rhd_destroy": (None, [_V]),
+    "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
+                                        ctypes.POINTER(rhd_step_info)]),
 }
+RHD_NOALLOC_MAX_CELLS = 262144
 
 _lib = None
 
