@@ -158,6 +158,13 @@ rhd_status rhd_state_set_all(rhd_ctx* ctx, const double* src, int64_t count,
 rhd_status rhd_state_get(rhd_ctx* ctx, int field, double* dst, int64_t count,
                          int dst_on_device);
 
+/* One evolved field of the stage state y(n+1/2) of the last step the context
+ * took (eq. imex1), e.g. for checkpointing the two stages; valid until the
+ * next rhd_step/rhd_step_async.  RHO and KAPPA are rejected (RHD_ERR_ARG).
+ * Synchronises the stream. */
+rhd_status rhd_stage_get(rhd_ctx* ctx, int field, double* dst, int64_t count,
+                         int dst_on_device);
+
 /* All ten fields to one field-major array of RHD_NFIELDS*ncell doubles. */
 rhd_status rhd_state_get_all(rhd_ctx* ctx, double* dst, int64_t count,
                              int dst_on_device);
@@ -176,6 +183,14 @@ rhd_status rhd_step_async(rhd_ctx* ctx, int nsteps, double dt);
 
 /* Wait for the pending rhd_step_async batch and report it like rhd_step. */
 rhd_status rhd_sync(rhd_ctx* ctx, rhd_step_info* info);
+
+/* Transport operator of the current state, s(y) of eq. (yrsla): the rates
+ * dE/dt and dF/dt (physical flux) of the explicit stage (Sec. 3.3 face states
+ * and HLL fluxes), without the local source terms.  rates: 4*ncell doubles,
+ * field-major (E, Fx, Fy, Fz), on the host (dst_on_device = 0) or the device.
+ * Returns RHD_ERR_NONPHYSICAL if a face state has E <= 0.  Uses the idle
+ * ping-pong buffer as scratch for host destinations; synchronises. */
+rhd_status rhd_transport(rhd_ctx* ctx, double* rates, int64_t count, int dst_on_device);
 
 /* Conserved totals of the current state (Sec. 3.3): out[0] = sum over cells
  * of (Egas + (c/chat) E) V, out[1..3] = sum of (m + F/(c chat)) V, V the cell

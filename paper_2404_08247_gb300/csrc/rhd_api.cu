@@ -40,6 +40,8 @@ struct rhd_ctx {
   double* yhalf = nullptr;
   double* rho = nullptr;
   double* kappa = nullptr;
+  double* eps[3] = {nullptr, nullptr, nullptr};  // TAU-mode face factors
+  bool eps_dirty = true;
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;
   double* d_partials = nullptr;
@@ -252,6 +254,7 @@ static void release(rhd_ctx* c) {
   cudaFree(c->yhalf);
   cudaFree(c->rho);
   cudaFree(c->kappa);
+  for (int d = 0; d < 3; ++d) cudaFree(c->eps[d]);
   cudaFree(c->d_status);
   cudaFree(c->d_partials);
   cudaFree(c->d_tot);
@@ -307,6 +310,9 @@ rhd_status rhd_init(const rhd_params* p, rhd_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->yhalf, ybytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->rho, sizeof(double) * N);
   if (e == cudaSuccess) e = cudaMalloc(&c->kappa, sizeof(double) * N);
+  if (p->hll_mode == RHD_HLL_TAU)
+    for (int d = 0; d < p->ndim && e == cudaSuccess; ++d)
+      e = cudaMalloc(&c->eps[d], sizeof(double) * N);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(DevStatus));
   if (e == cudaSuccess)
     e = cudaMalloc(&c->d_partials, sizeof(double) * totals_partials_needed());
@@ -356,6 +362,7 @@ static rhd_status check_copy_args(rhd_ctx* c, int field, const void* ptr, int64_
 }
 
 static rhd_status copy_in(rhd_ctx* c, int field, const double* src, int on_dev) {
+  if (field == RHD_F_RHO || field == RHD_F_KAPPA) c->eps_dirty = true;
   CUDA_TRY(c, cudaMemcpyAsync(field_ptr(c, field), src, sizeof(double) * c->ncell,
                               on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               c->stream));
@@ -420,6 +427,22 @@ rhd_status rhd_state_get(rhd_ctx* c, int field, double* dst, int64_t count,
   return RHD_OK;
 }
 
+rhd_status rhd_stage_get(rhd_ctx* c, int field, double* dst, int64_t count,
+                         int dst_on_device) {
+  rhd_status s = check_copy_args(c, field, dst, count);
+  if (s != RHD_OK) return s;
+  int slot = slot_of(field);
+  if (slot < 0) return fail(c, RHD_ERR_ARG, "the stage buffer holds evolved fields only");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaMemcpyAsync(dst, c->yhalf + (size_t)slot * c->ncell,
+                              sizeof(double) * c->ncell,
+                              dst_on_device ? cudaMemcpyDeviceToDevice
+                                            : cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RHD_OK;
+}
+
 rhd_status rhd_state_get_all(rhd_ctx* c, double* dst, int64_t count, int dst_on_device) {
   if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
   if (count != (int64_t)RHD_NFIELDS * c->ncell)
@@ -461,7 +484,13 @@ rhd_status rhd_step_async(rhd_ctx* c, int nsteps, double dt) {
   CUDA_TRY(c, cudaSetDevice(c->device));
   CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
   c->launches += 1;
+  if (c->p.hll_mode == RHD_HLL_TAU && c->eps_dirty) {
+    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->eps, c->stream));
+    c->launches += 1;
+    c->eps_dirty = false;
+  }
   StageArgs A;
+  for (int d = 0; d < 3; ++d) A.eps[d] = c->eps[d];
   A.g = c->g;
   A.ph = c->ph;
   A.dt = dt;
@@ -542,6 +571,50 @@ rhd_status rhd_step(rhd_ctx* c, int nsteps, double dt, rhd_step_info* info) {
     return s;
   }
   return rhd_sync(c, info);
+}
+
+rhd_status rhd_transport(rhd_ctx* c, double* rates, int64_t count, int dst_on_device) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (!rates) return fail(c, RHD_ERR_ARG, "rates is NULL");
+  if (count != 4 * (int64_t)c->ncell) return fail(c, RHD_ERR_ARG, "count must be 4 * ncell");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const size_t N = (size_t)c->ncell;
+  double* out = rates;
+  if (!dst_on_device) out = c->ybuf[c->cur ^ 1];  // the idle ping-pong buffer as staging
+  CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+  if (c->p.hll_mode == RHD_HLL_TAU && c->eps_dirty) {
+    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->eps, c->stream));
+    c->launches += 1;
+    c->eps_dirty = false;
+  }
+  StageArgs A;
+  A.g = c->g;
+  A.ph = c->ph;
+  A.dt = 0.0;
+  A.step = 0;
+  A.rho = c->rho;
+  A.kappa = c->kappa;
+  A.st = c->d_status;
+  for (int d = 0; d < 3; ++d) A.eps[d] = c->eps[d];
+  slots_of<const double*>(A.yt, c->ybuf[c->cur], c->ncell);
+  slots_of<const double*>(A.yn, c->ybuf[c->cur], c->ncell);
+  slots_of<double*>(A.yo, c->yhalf, c->ncell);
+  for (int q = 0; q < 4; ++q) A.rate[q] = out + q * N;
+  CUDA_TRY(c, launch_stage(0, c->p.precision, A, c->stream));
+  c->launches += 2;
+  if (!dst_on_device)
+    CUDA_TRY(c, cudaMemcpyAsync(rates, out, sizeof(double) * 4 * N, cudaMemcpyDeviceToHost,
+                                c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->h_status->fail_key != ~0ull)
+    return fail(c, RHD_ERR_NONPHYSICAL, "a face state has E <= 0 near cell %lld",
+                (long long)(c->h_status->fail_key >> 8));
+  return RHD_OK;
 }
 
 rhd_status rhd_totals(rhd_ctx* c, double out[4]) {

@@ -64,6 +64,9 @@ struct StageArgs {
   const double* yt[NY];  // state whose transport s(.) is taken, one pointer per slot
   const double* yn[NY];  // y(n) (stage 2 only)
   double* yo[NY];        // stage output
+  const double* eps[3];  // TAU mode: per-face optical-depth factors, or null
+                         // (then computed from kappa and rho on the fly)
+  double* rate[4];       // transport-only launch: dE/dt, dFx/dt, dFy/dt, dFz/dt
   DevStatus* st;
 };
 
@@ -74,81 +77,92 @@ inline void slots_of(P* out, P base, int n) {
 }
 
 // ---------------------------------------------------------------- limiter
-// PLM slope with the monotonised-central limiter:
-// minmod(2 d-, (d- + d+)/2, 2 d+), zero unless all three share a sign.
+// Half of the PLM slope with the monotonised-central limiter:
+// (1/2) minmod(2 d-, (d- + d+)/2, 2 d+) = sgn * min(|d-|, |d+|, |d- + d+|/4),
+// zero unless d- and d+ share a sign.  Face states are u -+ half_slope.
 template <typename R>
-__device__ __forceinline__ R mc_slope(R um, R u0, R up) {
+__device__ __forceinline__ R half_slope(R um, R u0, R up) {
   R dm = u0 - um;
   R dp = up - u0;
-  bool pos = (dm > R(0)) && (dp > R(0));
-  bool neg = (dm < R(0)) && (dp < R(0));
-  R m = fmin(fabs(R(2) * dm), fmin(fabs(R(0.5) * (dm + dp)), fabs(R(2) * dp)));
-  return pos ? m : (neg ? -m : R(0));
+  R m = fmin(fmin(fabs(dm), fabs(dp)), R(0.25) * fabs(dm + dp));
+  return (dm > R(0) && dp > R(0)) ? m : ((dm < R(0) && dp < R(0)) ? -m : R(0));
 }
 
 // ---------------------------------------------------------------- closure
 // Levermore M1 closure (the paper leaves the closure free, Sec. 2.1):
-// D = (1 - xi)/2 I + (3 xi - 1)/2 n n, xi = (3 + 4 f^2)/(5 + 2 sqrt(4 - 3 f^2)),
-// f = |F|/(cE) in [0, 1].  Ft is F/c.  Returns the row D_d. (times E in P)
-// and D_dd.  Zero flux or the Eddington option give D = I/3.
+// P = E [(1 - xi)/2 I + (3 xi - 1)/2 n n], xi = (3 + 4 f^2)/(5 + 2 sqrt(4 - 3 f^2)),
+// f = |Ft|/E clipped to [0, 1], Ft = F/c.  With s = sqrt(4 E^2 - 3 |Ft|^2)
+// the same tensor is exactly
+//     P = (s - E)/3 I + 3/(2E + s) Ft Ft^T          (|Ft| <= E),
+// which needs one square root and one reciprocal and no division by |Ft|
+// (zero flux gives E/3 I without a special case).  Above the free-streaming
+// limit f is clipped to 1: P = E n n = (E/|Ft|^2) Ft Ft^T.  m1_coeffs returns
+// (ha, hb) with P = ha I + hb Ft Ft^T; m1_row returns row d of P.
 template <typename R>
-__device__ __forceinline__ void closure_row(int d, R E, const R Ft[3], int closure,
-                                            R P[3], R& Ddd) {
+__device__ __forceinline__ void m1_coeffs(R E, const R Ft[3], R& ha, R& hb) {
   R F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
-  if (closure == RHD_CLOSURE_EDDINGTON || !(F2 > R(0))) {
-    Ddd = R(1) / R(3);
+  R E2 = E * E;
+  if (F2 > E2) {
+    ha = R(0);
+    hb = E / F2;
+  } else {
+    R s = sqrt(R(4) * E2 - R(3) * F2);
+    ha = (s - E) * (R(1) / R(3));
+    hb = R(3) / (R(2) * E + s);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void m1_row(int d, R E, const R Ft[3], int closure, R P[3]) {
+  if (closure == RHD_CLOSURE_EDDINGTON) {
     P[0] = P[1] = P[2] = R(0);
-    P[d] = E / R(3);
+    P[d] = E * (R(1) / R(3));
     return;
   }
-  R f2 = fmin(F2 / (E * E), R(1));
-  R xi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
-  R ha = R(0.5) * (R(1) - xi);
-  R hb = R(0.5) * (R(3) * xi - R(1)) / F2;
-  R bd = hb * Ft[d];
-  Ddd = ha + bd * Ft[d];
+  R ha, hb;
+  m1_coeffs(E, Ft, ha, hb);
+  R t = hb * Ft[d];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) P[j] = E * (bd * Ft[j]);
-  P[d] += E * ha;
+  for (int j = 0; j < 3; ++j) P[j] = t * Ft[j];
+  P[d] += ha;
 }
 
 // ------------------------------------------------------------------- HLL
 // Flux through one face along axis d (Sec. 3.3 Godunov step, Sec. 4.3 wave
 // speeds) for the RSLA system dE/dt = -chat div(Ft), dFt/dt = -chat div(P),
-// Ft = F/c.  Symmetric speeds S_R = -S_L = chat max(sqrt(D_dd,L),
-// sqrt(D_dd,R), 1/sqrt(3)), so HLL takes the form
+// from the reconstructed face states L and R (E, Ft).  Reconstructed fluxes
+// above the free-streaming limit are scaled back onto |Ft| = E.  Symmetric
+// speeds S_R = -S_L = chat sqrt(max(D_dd,L, D_dd,R, 1/3)), D = P/E, so HLL is
 //   Phi = (Phi_L + Phi_R)/2 - S (U_R - U_L)/2,
 // with the optical-depth factor eps on the energy part (1 for HLL NONE).
-// Face states: PLM from the 4-cell stencil (am, a | b, bp), scaled back onto
-// |Ft| <= E when the reconstruction oversteps the free-streaming limit.
 // Returns false for a face state with E <= 0 (or NaN).
 template <typename R>
-__device__ __forceinline__ bool hll_face(int d, const R am[4], const R a[4],
-                                         const R b[4], const R bp[4], R eps,
-                                         R chat, int closure, R out[4]) {
-  R L[4], Rr[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    L[q] = a[q] + R(0.5) * mc_slope(am[q], a[q], b[q]);
-    Rr[q] = b[q] - R(0.5) * mc_slope(a[q], b[q], bp[q]);
+__device__ __forceinline__ bool hll_states(int d, R L[4], R Rr[4], R eps, R chat,
+                                           int closure, R out[4]) {
+  if (!(L[0] > R(0)) || !(Rr[0] > R(0))) {
+    out[0] = out[1] = out[2] = out[3] = R(0);
+    return false;
   }
-  if (!(L[0] > R(0)) || !(Rr[0] > R(0))) return false;
   {
     R n2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
     if (n2 > L[0] * L[0]) {
-      R s = L[0] / sqrt(n2);
-      L[1] *= s; L[2] *= s; L[3] *= s;
+      R sc = L[0] / sqrt(n2);
+      L[1] *= sc; L[2] *= sc; L[3] *= sc;
     }
     n2 = Rr[1] * Rr[1] + Rr[2] * Rr[2] + Rr[3] * Rr[3];
     if (n2 > Rr[0] * Rr[0]) {
-      R s = Rr[0] / sqrt(n2);
-      Rr[1] *= s; Rr[2] *= s; Rr[3] *= s;
+      R sc = Rr[0] / sqrt(n2);
+      Rr[1] *= sc; Rr[2] *= sc; Rr[3] *= sc;
     }
   }
-  R PL[3], PR[3], DL, DR;
-  closure_row(d, L[0], &L[1], closure, PL, DL);
-  closure_row(d, Rr[0], &Rr[1], closure, PR, DR);
-  R S = chat * sqrt(fmax(fmax(DL, DR), R(1) / R(3)));
+  R PL[3], PR[3];
+  m1_row(d, L[0], &L[1], closure, PL);
+  m1_row(d, Rr[0], &Rr[1], closure, PR);
+  // largest of D_dd,L, D_dd,R and 1/3 without dividing each
+  R num = PL[d], den = L[0];
+  if (PR[d] * L[0] > PL[d] * Rr[0]) { num = PR[d]; den = Rr[0]; }
+  if (R(3) * num < den) { num = R(1); den = R(3); }
+  R S = chat * sqrt(num / den);
   R hc = R(0.5) * chat;
   R hS = R(0.5) * S;
   out[0] = hc * (L[1 + d] + Rr[1 + d]) - eps * hS * (Rr[0] - L[0]);
@@ -241,22 +255,19 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
     double T2 = T * T;
     double aT4 = a * T2 * T2;
 
-    // v_j P_ji of the closure at (E, F)
+    // v_j P_ji of the closure at (E, F): P = ha I + hb Ft Ft^T
     double vP[3];
     {
       double Ft[3] = {F[0] * ph.inv_c, F[1] * ph.inv_c, F[2] * ph.inv_c};
-      double F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
-      if (ph.closure == RHD_CLOSURE_EDDINGTON || !(F2 > 0.0)) {
-        double e3 = E / 3.0;
+      if (ph.closure == RHD_CLOSURE_EDDINGTON) {
+        double e3 = E * (1.0 / 3.0);
         vP[0] = v[0] * e3; vP[1] = v[1] * e3; vP[2] = v[2] * e3;
       } else {
-        double f2 = fmin(F2 / (E * E), 1.0);
-        double xi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
-        double ha = 0.5 * (1.0 - xi);
-        double hb = 0.5 * (3.0 * xi - 1.0) / F2;
-        double vFt = v[0] * Ft[0] + v[1] * Ft[1] + v[2] * Ft[2];
+        double ha, hb;
+        m1_coeffs(E, Ft, ha, hb);  // the cell flux may exceed the free-streaming limit
+        double t = hb * (v[0] * Ft[0] + v[1] * Ft[1] + v[2] * Ft[2]);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) vP[i] = E * (ha * v[i] + hb * vFt * Ft[i]);
+        for (int i = 0; i < 3; ++i) vP[i] = ha * v[i] + t * Ft[i];
       }
     }
     double inv_den = 1.0 / (1.0 + k * g);
@@ -304,6 +315,8 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
 cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
                           double* partials, int npart, double* out4, cudaStream_t s);
 int totals_partials_needed();
+cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
+                           double* const eps[3], cudaStream_t s);
 cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
                                cudaStream_t s);
 // message returned by rhd_last_error(NULL) on this thread

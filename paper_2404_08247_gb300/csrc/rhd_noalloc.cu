@@ -146,6 +146,8 @@ extern "C" rhd_status rhd_step_noalloc(const rhd_params* p, const double* state_
   A.rho = state_in + (size_t)RHD_F_RHO * N;
   A.kappa = state_in + (size_t)RHD_F_KAPPA * N;
   A.st = sym->status;
+  for (int d = 0; d < 3; ++d) A.eps[d] = nullptr;  // TAU factors from kappa, rho on the fly
+  for (int q = 0; q < 4; ++q) A.rate[q] = nullptr;
   for (int q = 0; q < NY; ++q) {
     A.yt[q] = state_in + (size_t)kSlotField[q] * N;
     A.yn[q] = A.yt[q];

@@ -1,4 +1,4 @@
-// rhd_stage.cu -- the two stage kernels of one IMEX PD-ARS step (FP64).
+// rhd_stage.cu -- the two stage kernels of one IMEX PD-ARS step.
 //
 // Stage 1 (eq. imex1):  y* = y(n) + dt s(y(n)),       y(n+1/2) = y* + dt f(y(n+1/2))
 // Stage 2 (eq. imex2):  y** = (y(n) + y(n+1/2))/2 + dt s(y(n+1/2))/2,
@@ -6,150 +6,375 @@
 // The stage-2 explicit state is eq. (imex2) with dt f(y(n+1/2)) replaced by
 // y(n+1/2) - y*, which eq. (imex1) makes exact.
 //
-// One thread per cell: the thread gathers the 5-cell stencil of E and F along
-// each active axis (ghost cells by index folding: periodic wrap or mirror with
-// the normal flux negated), builds both face fluxes, applies the conservative
-// update and then runs the cell's local implicit solve, so the explicit state
-// never leaves registers.
+// Work layout (3-D): a block owns a 32 x 8 column of cells and marches
+// through a chunk of z planes.  E and F/c of four consecutive planes sit in a
+// shared-memory ring, each plane with a 2-cell halo in x and y (ghost cells
+// folded in at load time: periodic wrap, or mirror with the normal flux
+// negated).  Every face flux is computed exactly once: x- and y-faces of the
+// current plane by one thread each (into shared memory), z-faces by the thread
+// that owns the column (kept in registers from one plane to the next,
+// together with the half z-slope of the current cell).  The thread then
+// applies the conservative update and runs the cell's local implicit solve in
+// registers, so the explicit state never reaches HBM.  2-D grids use the same
+// kernel on one plane; 1-D grids use 256-cell rows.
 #include "rhd_internal.cuh"
 
 namespace rhd {
 
-// Neighbour of cell idx (coordinate q along axis d) at offset o, with the
-// boundary condition applied; flip = the normal flux changes sign (mirror).
-__device__ __forceinline__ int neighbour(const Geometry& g, int d, int q, int idx, int o,
-                                         bool& flip) {
-  const int n = g.n[d];
-  int x = q + o;
+template <int NDIM>
+struct Tile;
+template <>
+struct Tile<3> {
+  static constexpr int TX = 32, TY = 8, LZ = 32, HX = 2, HY = 2, NPL = 4;
+};
+template <>
+struct Tile<2> {
+  static constexpr int TX = 32, TY = 8, LZ = 1, HX = 2, HY = 2, NPL = 1;
+};
+template <>
+struct Tile<1> {
+  static constexpr int TX = 256, TY = 1, LZ = 1, HX = 2, HY = 0, NPL = 1;
+};
+
+template <int NDIM>
+struct Smem {
+  using T = Tile<NDIM>;
+  static constexpr int PW = T::TX + 2 * T::HX;
+  static constexpr int PH = T::TY + 2 * T::HY;
+  static constexpr int PS = PW * PH;                   // cells per plane
+  static constexpr int RING = T::NPL * 4 * PS;         // doubles
+  static constexpr int FX = 4 * T::TY * (T::TX + 1);   // x-face fluxes
+  static constexpr int FY = NDIM >= 2 ? 4 * (T::TY + 1) * T::TX : 0;
+  static constexpr size_t BYTES = sizeof(double) * (RING + FX + FY);
+};
+
+// Coordinate x >= -2 folded onto [0, n) by the boundary condition (padding
+// of a partial tile beyond n + 1 is clamped first); flip = mirror image.
+__device__ __forceinline__ int fold(int x, int n, int bclo, int bchi, bool& flip) {
   flip = false;
+  x = min(x, n + 1);
   if (x < 0) {
-    if (g.bc[d][0] == RHD_BC_PERIODIC) {
+    if (bclo == RHD_BC_PERIODIC) {
       x = ((x % n) + n) % n;
     } else {
       x = -1 - x;
       flip = true;
     }
   } else if (x >= n) {
-    if (g.bc[d][1] == RHD_BC_PERIODIC) {
+    if (bchi == RHD_BC_PERIODIC) {
       x = x % n;
     } else {
       x = 2 * n - 1 - x;
       flip = true;
     }
   }
-  return idx + (x - q) * g.stride[d];
+  return x;
+}
+
+__device__ __forceinline__ double eps_direct(const StageArgs& A, int ia, int ib, int d) {
+  double tau = 0.5 * (A.kappa[ia] * A.rho[ia] + A.kappa[ib] * A.rho[ib]) * A.g.dx[d];
+  return tau_factor(tau);
+}
+
+// Optical-depth factor of the face on the +d side of the cell c (c[d] may be
+// -1: the low wall face).  TAU mode only; 1 otherwise.
+__device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, int cy, int cz) {
+  if (A.ph.hll_mode != RHD_HLL_TAU) return 1.0;
+  const Geometry& g = A.g;
+  int c[3] = {cx, cy, cz};
+  if (c[d] < 0) {
+    if (g.bc[d][0] != RHD_BC_PERIODIC) {
+      c[d] = 0;  // reflecting wall: the ghost mirrors cell 0
+      int i0 = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+      return eps_direct(A, i0, i0, d);
+    }
+    c[d] = g.n[d] - 1;  // periodic: the same face as the top one
+  }
+  int il = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+  if (A.eps[d]) return __ldg(A.eps[d] + il);
+  bool flip;
+  int xb = fold(c[d] + 1, g.n[d], g.bc[d][0], g.bc[d][1], flip);
+  return eps_direct(A, il, il + (xb - c[d]) * g.stride[d], d);
+}
+
+// load plane zg (global z, may be a ghost plane) into ring slot `slot`
+template <int NDIM>
+__device__ __forceinline__ void load_plane(const StageArgs& A, double* ring, int slot, int zg,
+                                           int x0, int y0) {
+  using T = Tile<NDIM>;
+  using S = Smem<NDIM>;
+  const Geometry& g = A.g;
+  bool fz = false;
+  int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz) : 0;
+  double* pl = ring + slot * 4 * S::PS;
+  for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
+    int ii = c % S::PW, jj = c / S::PW;
+    bool fx = false, fy = false;
+    int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx);
+    int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy) : 0;
+    int idx = xf + g.n[0] * (yf + g.n[1] * zf);
+    double E = __ldg(A.yt[Y_ERAD] + idx);
+    double Fx = __ldg(A.yt[Y_FX] + idx) * A.ph.inv_c;
+    double Fy = __ldg(A.yt[Y_FY] + idx) * A.ph.inv_c;
+    double Fz = __ldg(A.yt[Y_FZ] + idx) * A.ph.inv_c;
+    pl[0 * S::PS + c] = E;
+    pl[1 * S::PS + c] = fx ? -Fx : Fx;
+    pl[2 * S::PS + c] = fy ? -Fy : Fy;
+    pl[3 * S::PS + c] = fz ? -Fz : Fz;
+  }
+}
+
+template <int NDIM>
+__device__ __forceinline__ void cell_of(const double* pl, int c, double u[4]) {
+  using S = Smem<NDIM>;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) u[q] = pl[q * S::PS + c];
+}
+
+// flux through the face between plane cells c - st and c (stride st)
+template <int NDIM>
+__device__ __forceinline__ bool plane_face(const double* pl, int c, int st, int d,
+                                           double eps, double chat, int closure,
+                                           double out[4]) {
+  double am[4], a[4], b[4], bp[4];
+  cell_of<NDIM>(pl, c - 2 * st, am);
+  cell_of<NDIM>(pl, c - st, a);
+  cell_of<NDIM>(pl, c, b);
+  cell_of<NDIM>(pl, c + st, bp);
+  double L[4], R[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    L[q] = a[q] + half_slope(am[q], a[q], b[q]);
+    R[q] = b[q] - half_slope(a[q], b[q], bp[q]);
+  }
+  return hll_states<double>(d, L, R, eps, chat, closure, out);
 }
 
 template <int STAGE, int NDIM>
-__global__ void __launch_bounds__(128) stage_fp64(const StageArgs A) {
+__global__ void __launch_bounds__(Tile<NDIM>::TX * Tile<NDIM>::TY, 2)
+stage_kernel(const StageArgs A) {
+  using T = Tile<NDIM>;
+  using S = Smem<NDIM>;
+  constexpr int TX = T::TX, TY = T::TY, NT = TX * TY;
+  extern __shared__ double smem[];
+  double* ring = smem;
+  double* fxs = ring + S::RING;
+  double* fys = fxs + S::FX;
   __shared__ int s_skip;
-  __shared__ int s_max_nn[4], s_max_no[4];
-  __shared__ unsigned long long s_sum_nn[4], s_cnt[4], s_sum_no[4];
+  __shared__ int s_max_nn[NT / 32], s_max_no[NT / 32];
+  __shared__ unsigned long long s_sum_nn[NT / 32], s_cnt[NT / 32], s_sum_no[NT / 32];
+
   if (threadIdx.x == 0) s_skip = (A.st->fail_key != ~0ull) ? 1 : 0;
   __syncthreads();
   if (s_skip) return;  // a previous launch of this batch failed
 
   const Geometry& g = A.g;
   const Physics& ph = A.ph;
-  const int N = g.ncell;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = idx < N;
-  int nn = 0, no = 0, code = RHD_OK;
+  const double chat = ph.chat;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int ix = x0 + tx, iy = y0 + ty;
+  const bool col = ix < g.n[0] && (NDIM < 2 || iy < g.n[1]);
+  const int cy = NDIM >= 2 ? min(iy, g.n[1] - 1) : 0;  // clamped row of the column
+  const int cx = min(ix, g.n[0] - 1);
+  const int kbeg = blockIdx.z * T::LZ;
+  const int kend = min(kbeg + T::LZ, g.n[2]);
+  const int own = (tx + T::HX) + (ty + T::HY) * S::PW;  // own cell in a plane
 
-  if (active) {
-    int coord[3];
-    coord[0] = idx % g.n[0];
-    int r = idx / g.n[0];
-    coord[1] = r % g.n[1];
-    coord[2] = r / g.n[1];
+  int nn_max = 0, no_max = 0;
+  unsigned long long nn_sum = 0, no_sum = 0, cnt = 0;
+  bool zbad = false;
 
-    double rate[4] = {0.0, 0.0, 0.0, 0.0};  // dE/dt, dFt/dt (Ft = F/c)
+  double zlo[4] = {0.0, 0.0, 0.0, 0.0};  // z-face flux below the current cell
+  double hz[4] = {0.0, 0.0, 0.0, 0.0};   // half z-slope of the current cell
+  if (NDIM == 3) {
+    for (int o = -2; o <= 1; ++o) load_plane<NDIM>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
+    __syncthreads();
+    double um[4], u0[4], up[4], upp[4];
+    cell_of<NDIM>(ring + ((kbeg - 2) & 3) * 4 * S::PS, own, um);
+    cell_of<NDIM>(ring + ((kbeg - 1) & 3) * 4 * S::PS, own, u0);
+    cell_of<NDIM>(ring + ((kbeg + 0) & 3) * 4 * S::PS, own, up);
+    cell_of<NDIM>(ring + ((kbeg + 1) & 3) * 4 * S::PS, own, upp);
+    double L[4], R[4];
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      double c5[5][4];
-      double chi3[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-      for (int o = -2; o <= 2; ++o) {
-        bool flip;
-        int nb = neighbour(g, d, coord[d], idx, o, flip);
-        c5[o + 2][0] = __ldg(A.yt[Y_ERAD] + nb);
-        c5[o + 2][1] = __ldg(A.yt[Y_FX] + nb) * ph.inv_c;
-        c5[o + 2][2] = __ldg(A.yt[Y_FY] + nb) * ph.inv_c;
-        c5[o + 2][3] = __ldg(A.yt[Y_FZ] + nb) * ph.inv_c;
-        if (flip) c5[o + 2][1 + d] = -c5[o + 2][1 + d];
-        if (ph.hll_mode == RHD_HLL_TAU && o >= -1 && o <= 1)
-          chi3[o + 1] = __ldg(A.kappa + nb) * __ldg(A.rho + nb);
-      }
-      double eps_lo = 1.0, eps_hi = 1.0;
-      if (ph.hll_mode == RHD_HLL_TAU) {
-        eps_lo = tau_factor(0.5 * (chi3[0] + chi3[1]) * g.dx[d]);
-        eps_hi = tau_factor(0.5 * (chi3[1] + chi3[2]) * g.dx[d]);
-      }
-      double lo[4], hi[4];
-      bool ok_lo = hll_face<double>(d, c5[0], c5[1], c5[2], c5[3], eps_lo, ph.chat,
-                                    ph.closure, lo);
-      bool ok_hi = hll_face<double>(d, c5[1], c5[2], c5[3], c5[4], eps_hi, ph.chat,
-                                    ph.closure, hi);
-      if (!ok_lo || !ok_hi) code = RHD_ERR_NONPHYSICAL;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) rate[q] -= (hi[q] - lo[q]) * g.inv_dx[d];
+    for (int q = 0; q < 4; ++q) {
+      hz[q] = half_slope(u0[q], up[q], upp[q]);
+      L[q] = u0[q] + half_slope(um[q], u0[q], up[q]);
+      R[q] = up[q] - hz[q];
     }
+    double eps = face_eps(A, 2, cx, cy, kbeg - 1);
+    zbad = !hll_states<double>(2, L, R, eps, chat, ph.closure, zlo);
+    __syncthreads();  // plane kbeg-2's slot is reloaded by the first iteration
+  }
 
-    double y[8];
-    if (STAGE == 1) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) y[q] = A.yt[q][idx];
-      y[Y_ERAD] += A.dt * rate[0];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) y[Y_FX + j] += A.dt * ph.c * rate[1 + j];
+  for (int k = kbeg; k < kend; ++k) {
+    if (NDIM == 3) {
+      load_plane<NDIM>(A, ring, (k + 2) & 3, k + 2, x0, y0);
     } else {
+      load_plane<NDIM>(A, ring, 0, 0, x0, y0);
+    }
+    __syncthreads();
+    const double* pl = ring + (NDIM == 3 ? (k & 3) : 0) * 4 * S::PS;
+    bool bad = zbad;
+
+    // ---- z-face k+1/2 of the own column
+    double zhi[4] = {0.0, 0.0, 0.0, 0.0};
+    double hz1[4] = {0.0, 0.0, 0.0, 0.0};
+    if (NDIM == 3) {
+      double u0[4], u1[4], u2[4];
+      cell_of<NDIM>(pl, own, u0);
+      cell_of<NDIM>(ring + ((k + 1) & 3) * 4 * S::PS, own, u1);
+      cell_of<NDIM>(ring + ((k + 2) & 3) * 4 * S::PS, own, u2);
+      double L[4], R[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        y[q] = 0.5 * (A.yn[q][idx] + A.yt[q][idx]);
-      y[Y_ERAD] += 0.5 * A.dt * rate[0];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) y[Y_FX + j] += 0.5 * A.dt * ph.c * rate[1 + j];
+      for (int q = 0; q < 4; ++q) {
+        hz1[q] = half_slope(u0[q], u1[q], u2[q]);
+        L[q] = u0[q] + hz[q];
+        R[q] = u1[q] - hz1[q];
+      }
+      double eps = face_eps(A, 2, cx, cy, k);
+      zbad = !hll_states<double>(2, L, R, eps, chat, ph.closure, zhi);
+      bad = bad || zbad;
     }
 
-    const double rho = A.rho[idx];
-    const double chi = A.kappa[idx] * rho;
-    if (code == RHD_OK)
-      code = local_solve(ph, STAGE == 1 ? A.dt : 0.5 * A.dt, rho, chi, y, nn, no);
+    // ---- x-faces of plane k: face f lies between tile cells fi-1 and fi
+    for (int f = threadIdx.x; f < (TX + 1) * TY; f += NT) {
+      int fi = f % (TX + 1), fj = f / (TX + 1);
+      int c = fi + T::HX + (fj + T::HY) * S::PW;
+      int xl = x0 + fi - 1;
+      int yr = NDIM >= 2 ? y0 + fj : 0;
+      bool real = xl < g.n[0] && (NDIM < 2 || yr < g.n[1]);
+      double eps = real ? face_eps(A, 0, xl, yr, k) : 1.0;
+      double out[4];
+      if (!plane_face<NDIM>(pl, c, 1, 0, eps, chat, ph.closure, out) && real) {
+        // a face with E <= 0 poisons both neighbours' fluxes
 #pragma unroll
-    for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
-    if (code != RHD_OK) {
-      atomicMin(&A.st->fail_key, ((unsigned long long)idx << 8) | (unsigned)code);
-      A.st->fail_step = A.step;
-      A.st->fail_stage = STAGE;
+        for (int q = 0; q < 4; ++q) out[q] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fxs[q * TY * (TX + 1) + f] = out[q];
     }
+    // ---- y-faces of plane k: face f lies between rows fj-1 and fj
+    if (NDIM >= 2) {
+      for (int f = threadIdx.x; f < TX * (TY + 1); f += NT) {
+        int fi = f % TX, fj = f / TX;
+        int c = fi + T::HX + (fj + T::HY) * S::PW;
+        int xr = x0 + fi, yl = y0 + fj - 1;
+        bool real = xr < g.n[0] && yl < g.n[1];
+        double eps = real ? face_eps(A, 1, xr, yl, k) : 1.0;
+        double out[4];
+        if (!plane_face<NDIM>(pl, c, S::PW, 1, eps, chat, ph.closure, out) && real) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) out[q] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fys[q * (TY + 1) * TX + f] = out[q];
+      }
+    }
+    __syncthreads();
+
+    if (col) {
+      const int idx = ix + g.n[0] * (iy + g.n[1] * k);
+      double rate[4];
+      const int fl = tx + ty * (TX + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double* fq = fxs + q * TY * (TX + 1);
+        rate[q] = -(fq[fl + 1] - fq[fl]) * g.inv_dx[0];
+      }
+      if (NDIM >= 2) {
+        const int fb = tx + ty * TX;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double* fq = fys + q * (TY + 1) * TX;
+          rate[q] -= (fq[fb + TX] - fq[fb]) * g.inv_dx[1];
+        }
+      }
+      if (NDIM == 3) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rate[q] -= (zhi[q] - zlo[q]) * g.inv_dx[2];
+      }
+      bad = bad || !isfinite(rate[0]) || !isfinite(rate[1]) || !isfinite(rate[2]) ||
+            !isfinite(rate[3]);
+
+      double y[8];
+      if (STAGE == 0) {
+        // transport only: s(y) of eq. (yrsla) for E and the physical flux F
+        A.rate[0][idx] = rate[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A.rate[1 + j][idx] = ph.c * rate[1 + j];
+        if (bad) {
+          atomicMin(&A.st->fail_key, ((unsigned long long)idx << 8) | RHD_ERR_NONPHYSICAL);
+          A.st->fail_step = A.step;
+          A.st->fail_stage = 0;
+        }
+      } else if (STAGE == 1) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = A.yt[q][idx];
+        y[Y_ERAD] += A.dt * rate[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y[Y_FX + j] += A.dt * ph.c * rate[1 + j];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = 0.5 * (A.yn[q][idx] + A.yt[q][idx]);
+        y[Y_ERAD] += 0.5 * A.dt * rate[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y[Y_FX + j] += 0.5 * A.dt * ph.c * rate[1 + j];
+      }
+      const double rho = A.rho[idx];
+      const double chi = A.kappa[idx] * rho;
+      int nn = 0, no = 0;
+      int code = RHD_OK;
+      if (STAGE != 0) {
+        code = bad ? RHD_ERR_NONPHYSICAL
+                   : local_solve(ph, STAGE == 1 ? A.dt : 0.5 * A.dt, rho, chi, y, nn, no);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
+      }
+      if (code != RHD_OK) {
+        atomicMin(&A.st->fail_key, ((unsigned long long)idx << 8) | (unsigned)code);
+        A.st->fail_step = A.step;
+        A.st->fail_stage = STAGE;
+      }
+      nn_max = max(nn_max, nn);
+      no_max = max(no_max, no);
+      nn_sum += nn;
+      no_sum += no;
+      cnt += 1;
+    }
+    if (NDIM == 3) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        zlo[q] = zhi[q];
+        hz[q] = hz1[q];
+      }
+    }
+    __syncthreads();
   }
 
   // iteration statistics: warp, then block, then one atomic per block
   const unsigned full = 0xffffffffu;
-  int wmax_nn = __reduce_max_sync(full, nn);
-  int wmax_no = __reduce_max_sync(full, no);
-  unsigned long long wsum = (unsigned long long)nn;
-  unsigned long long wcnt = active ? 1ull : 0ull;
-  unsigned long long wso = (unsigned long long)no;
+  int wmax_nn = __reduce_max_sync(full, nn_max);
+  int wmax_no = __reduce_max_sync(full, no_max);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    wsum += __shfl_down_sync(full, wsum, off);
-    wcnt += __shfl_down_sync(full, wcnt, off);
-    wso += __shfl_down_sync(full, wso, off);
+    nn_sum += __shfl_down_sync(full, nn_sum, off);
+    no_sum += __shfl_down_sync(full, no_sum, off);
+    cnt += __shfl_down_sync(full, cnt, off);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     s_max_nn[warp] = wmax_nn;
     s_max_no[warp] = wmax_no;
-    s_sum_nn[warp] = wsum;
-    s_cnt[warp] = wcnt;
-    s_sum_no[warp] = wso;
+    s_sum_nn[warp] = nn_sum;
+    s_sum_no[warp] = no_sum;
+    s_cnt[warp] = cnt;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int bmn = 0, bmo = 0;
     unsigned long long bs = 0, bc = 0, bo = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       bmn = max(bmn, s_max_nn[w]);
       bmo = max(bmo, s_max_no[w]);
       bs += s_sum_nn[w];
@@ -180,20 +405,64 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Optical-depth factors of every face (TAU mode): eps_d[i] belongs to the face
+// between cell i and its +d neighbour (periodic wrap, or the mirror of cell i
+// at a reflecting wall).  Depends on the static rho and kappa only.
+__global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
+                               const double* __restrict__ kappa, double* e0, double* e1,
+                               double* e2) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.ncell) return;
+  int c[3];
+  c[0] = idx % g.n[0];
+  int r = idx / g.n[0];
+  c[1] = r % g.n[1];
+  c[2] = r / g.n[1];
+  double* out[3] = {e0, e1, e2};
+  double chi_a = kappa[idx] * rho[idx];
+  for (int d = 0; d < g.ndim; ++d) {
+    bool flip;
+    int xb = fold(c[d] + 1, g.n[d], g.bc[d][0], g.bc[d][1], flip);
+    int nb = idx + (xb - c[d]) * g.stride[d];
+    double tau = 0.5 * (chi_a + kappa[nb] * rho[nb]) * g.dx[d];
+    out[d][idx] = tau_factor(tau);
+  }
+}
+
+cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
+                           double* const eps[3], cudaStream_t s) {
+  int blocks = (g.ncell + 255) / 256;
+  tau_eps_kernel<<<blocks, 256, 0, s>>>(g, rho, kappa, eps[0], eps[1], eps[2]);
+  return cudaGetLastError();
+}
+
+template <int STAGE, int NDIM>
+static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s) {
+  using T = Tile<NDIM>;
+  using S = Smem<NDIM>;
+  // opt in to more than 48 KiB of dynamic shared memory (idempotent)
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<STAGE, NDIM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)S::BYTES);
+  if (e != cudaSuccess) return e;
+  dim3 grid((A.g.n[0] + T::TX - 1) / T::TX, (A.g.n[1] + T::TY - 1) / T::TY,
+            (A.g.n[2] + T::LZ - 1) / T::LZ);
+  stage_kernel<STAGE, NDIM><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
+  return cudaGetLastError();
+}
+
 template <int STAGE>
 static cudaError_t launch_fp64(const StageArgs& A, cudaStream_t s) {
-  const int block = 128;
-  const int grid = (A.g.ncell + block - 1) / block;
   switch (A.g.ndim) {
-    case 1: stage_fp64<STAGE, 1><<<grid, block, 0, s>>>(A); break;
-    case 2: stage_fp64<STAGE, 2><<<grid, block, 0, s>>>(A); break;
-    default: stage_fp64<STAGE, 3><<<grid, block, 0, s>>>(A); break;
+    case 1: return launch_nd<STAGE, 1>(A, s);
+    case 2: return launch_nd<STAGE, 2>(A, s);
+    default: return launch_nd<STAGE, 3>(A, s);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s) {
   (void)precision;
+  if (stage == 0) return launch_fp64<0>(A, s);
   return stage == 1 ? launch_fp64<1>(A, s) : launch_fp64<2>(A, s);
 }
 

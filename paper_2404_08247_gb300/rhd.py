@@ -101,10 +101,12 @@ SIGNATURES = {
     "rhd_state_set_all": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
     "rhd_state_get": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
     "rhd_state_get_all": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
+    "rhd_stage_get": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
     "rhd_step": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double,
                                 ctypes.POINTER(rhd_step_info)]),
     "rhd_step_async": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "rhd_sync": (ctypes.c_int, [_V, ctypes.POINTER(rhd_step_info)]),
+    "rhd_transport": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
     "rhd_totals": (ctypes.c_int, [_V, _D]),
     "rhd_profile": (ctypes.c_int, [_V, ctypes.c_int]),
     "rhd_profile_read": (ctypes.c_int, [_V, ctypes.POINTER(_I64), _D]),
@@ -276,6 +278,15 @@ class RHDContext:
                                       self.ncell, dev), self.h)
         return out
 
+    def get_stage_field(self, field: int, out=None):
+        """One evolved field of y(n+1/2) of the last step."""
+        if out is None:
+            out = np.empty(self.shape[1:], dtype=np.float64)
+        ptr, dev = _ptr(out)
+        _check(self.lib.rhd_stage_get(self.h, field, ctypes.c_void_p(ptr), self.ncell, dev),
+               self.h)
+        return out
+
     def step(self, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
         info = rhd_step_info()
         st = self.lib.rhd_step(self.h, int(nsteps), float(dt), ctypes.byref(info))
@@ -294,6 +305,15 @@ class RHDContext:
         if raise_on_error:
             _check(st, self.h)
         return info.as_dict()
+
+    def transport(self, out=None):
+        """Rates (dE/dt, dFx/dt, dFy/dt, dFz/dt) of s(y), shape (4, nz, ny, nx)."""
+        if out is None:
+            out = np.empty((4,) + self.shape[1:], dtype=np.float64)
+        ptr, dev = _ptr(out)
+        _check(self.lib.rhd_transport(self.h, ctypes.c_void_p(ptr), 4 * self.ncell, dev),
+               self.h)
+        return out
 
     def totals(self) -> np.ndarray:
         out = np.zeros(4, dtype=np.float64)

@@ -222,3 +222,39 @@ def test_newton_failure_reports_first_cell_and_keeps_state(R, oracle_mod):
         assert info["fail_cell"] == infos[-1]["fail_cell"]
         assert np.array_equal(ctx.get_state(), U)
         assert ctx.time() == 0.0
+
+
+TRANSPORT_CASES = {
+    "1d": dict(ndim=1, n=[300], bc="periodic"),
+    "1d_reflect": dict(ndim=1, n=[77], bc="reflect"),
+    "2d": dict(ndim=2, n=[33, 17], bc="periodic"),
+    "2d_reflect_x": dict(ndim=2, n=[33, 17],
+                         bc=[["reflect", "reflect"], ["periodic", "periodic"],
+                             ["periodic", "periodic"]]),
+    "3d": dict(ndim=3, n=[37, 23, 19], bc="periodic"),
+    "3d_small": dict(ndim=3, n=[9, 8, 7], bc="periodic"),
+    # cell fluxes up to 1.5 c E: reconstructed faces beyond the free-streaming
+    # limit are scaled back and the closure clips f to 1
+    "3d_overflux": dict(ndim=3, n=[20, 12, 10], bc="periodic", flux_frac=1.5),
+}
+
+
+@pytest.mark.parametrize("case", sorted(TRANSPORT_CASES))
+@pytest.mark.parametrize("closure", ["m1", "eddington"])
+@pytest.mark.parametrize("hll", ["tau", "none"])
+def test_transport_rates_match_oracle(R, oracle_mod, case, closure, hll):
+    """s(y) of eq. (yrsla) alone: the rates of E and F from the GPU's shared
+    face fluxes equal the oracle's per-cell faces (max-norm relative, 1e-11)."""
+    cfg = TRANSPORT_CASES[case]
+    n = cfg["n"]
+    prob = I.base_problem(cfg["ndim"], n, [1.0 / v for v in n], c=1e3, chat=2e2,
+                          bc=cfg["bc"], closure=closure, hll_mode=hll)
+    U = I.random_state(prob, seed=31, beta_max=1e-2, flux_frac=cfg.get("flux_frac", 0.1))
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        rg = ctx.transport()
+    ro = oracle_mod.transport(prob, U)
+    for q in range(4):
+        s = np.abs(ro[q]).max()
+        err = np.abs(rg[q] - ro[q]).max() / s if s > 0 else np.abs(rg[q]).max()
+        assert err <= TOL, (q, err)
