@@ -178,23 +178,58 @@ __device__ __forceinline__ double tau_factor(double tau) {
 }
 
 // ------------------------------------------------------------ local solve
+// Start of the inner Newton iteration.  With v and F frozen, eq. (FGFR) and
+// eq. (Rnew) reduce exactly to a quartic for the gas temperature:
+//   A T^4 + C_v T = C,  A = (c/chat) k g a/(1 + k g),
+//   C = Egas(t) - E_kin + (c/chat) k (g E(t) - v.F/c^2)/(1 + k g),
+// whose positive root is the converged inner state.  quartic_start solves
+// a4 T^4 + T = rhs (a4 = A/C_v, rhs = C/C_v) in single precision in the
+// variable t = T/T(t) (alpha t^4 + beta t = 1, coefficients of order one) by
+// Newton from the upper bound min(1/beta, alpha^-1/4), where the convex
+// quartic converges monotonically.  The double-precision Newton of the paper
+// then starts from it instead of from (Egas(t), 0) and needs fewer updates;
+// it converges to the same root.  Returns false (cold start) if the
+// single-precision numbers are not finite.
+__device__ __forceinline__ bool quartic_start(double a4, double rhs, double T0, double& T) {
+  float al = (float)(a4 * (T0 * T0) * (T0 * T0) / rhs);
+  float be = (float)(T0 / rhs);
+  if (!(al >= 0.f) || !(be > 0.f) || !isfinite(al) || !isfinite(be)) return false;
+  float t = fminf(1.0f / be, al > 0.f ? rsqrtf(sqrtf(al)) : INFINITY);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float t2 = t * t;
+    float f = fmaf(al * t2, t2, fmaf(be, t, -1.0f));
+    float fp = fmaf(4.0f * al * t2, t, be);
+    t = t - __fdividef(f, fp);
+  }
+  if (!(t > 0.f) || !isfinite(t)) return false;
+  T = (double)t * T0;
+  return true;
+}
+
 // Implicit stage of one cell (Sec. 3.3), grey chi.  y = {Egas, m, E, F}
 // holds the explicit state on entry and the solution on exit.  tdt = theta dt.
 //
 // Inner stage: Newton on (Egas, R) for eq. (FGFR) with eq. (Rnew) and the
 // paper's Jacobian (beta^2 dropped).  The R-row is multiplied by
-// k = chat chi theta dt, which leaves the Newton iterates unchanged and keeps
-// the system regular for small k:
+// k g (k = chat chi theta dt, g = 1 + beta^2/2), which leaves the Newton
+// iterates unchanged and keeps the system regular for small k:
 //   r0 = Egas - Egas(t) + (c/chat) R
-//   r1 = k F_R = k (aT^4 - E(t) - R) + (k v.F/c^2 - R)/g,  g = 1 + beta^2/2
-//   J  = [[1, c/chat], [k 4 a T^3 / C_v, -1 - k]]
-// converged when |r0| < eps E_tot and (c/chat)|r1| <= eps E_tot k,
-// E_tot = Egas(t) + (c/chat) E(t).
+//   r1 = k g F_R = k g (aT^4 - E(t) - R) + k v.F/c^2 - R
+//   J  = [[1, c/chat], [g k 4 a T^3 / C_v, -g (1 + k)]]
+// converged when |r0| < eps E_tot and (c/chat)|r1| <= eps E_tot k g,
+// E_tot = Egas(t) + (c/chat) E(t).  The first pass starts from quartic_start.
 // Energy closure: E = E(t) - (chat/c)(Egas - Egas(t)).
 // Outer stage: eq. (numF2) (order 2) or (numF1) (order 1) for F with P from
 // the new E and the previous outer flux, momentum m = m(t) - (F - F(t))/(c chat),
 // repeated until Q = k[(g - 1)(aT^4 - E) + v.F/c^2] settles: its change is at
 // most outer_rtol times |Q|, |R| or the magnitude of its terms.
+// MIXED: the Newton step's reciprocal of the Jacobian determinant is taken in
+// single precision (a step off by 1e-7 only slows the last iteration by that
+// factor); residuals, the state, the closure of the exchange term v.P and
+// every update stay double, so the solve meets the double-precision
+// convergence tests (inner and outer) and conserves to rounding.
+template <bool MIXED>
 __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double rho,
                                            double chi, double y[8], int& nn, int& no) {
   nn = 0;
@@ -214,16 +249,32 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
   double m[3] = {y[1], y[2], y[3]};
   double F[3] = {y[5], y[6], y[7]};
 
+  // v, beta^2, g, v.F/c^2 and the kinetic energy of the frozen (m, F)
+  double v[3] = {m[0] * inv_rho, m[1] * inv_rho, m[2] * inv_rho};
+  double beta2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * ph.inv_c2;
+  double g = (ph.vc_order == 2) ? 1.0 + 0.5 * beta2 : 1.0;
+  double w = (v[0] * F[0] + v[1] * F[1] + v[2] * F[2]) * ph.inv_c2;
+  double Ekin = 0.5 * (m[0] * v[0] + m[1] * v[1] + m[2] * v[2]);
+
+  {
+    double T0 = (Eg0 - Ekin) * inv_Cv;
+    if (T0 > 0.0) {
+      double kg = k * g;
+      double inv1 = 1.0 / (1.0 + kg);
+      double a4 = cr * kg * a * inv1 * inv_Cv;
+      double rhs = T0 + cr * k * (g * E0 - w) * inv1 * inv_Cv;
+      double Tg;
+      if (rhs > 0.0 && quartic_start(a4, rhs, T0, Tg)) {
+        Eg = Cv * Tg + Ekin;
+        R = -ph.chat_over_c * (Eg - Eg0);
+      }
+    }
+  }
+
   for (int outer = 0; outer < ph.outer_max; ++outer) {
     no = outer + 1;
-    double v[3] = {m[0] * inv_rho, m[1] * inv_rho, m[2] * inv_rho};
-    double beta2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * ph.inv_c2;
-    double g = (ph.vc_order == 2) ? 1.0 + 0.5 * beta2 : 1.0;
-    double inv_g = 1.0 / g;
-    double w = (v[0] * F[0] + v[1] * F[1] + v[2] * F[2]) * ph.inv_c2;
-    double Ekin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * inv_rho;
-    double kE0 = k * E0;
-    double kw = k * w;
+    const double kg = k * g;
+    const double kw = k * w;
 
     bool conv = false;
     for (int it = 0;; ++it) {
@@ -232,17 +283,17 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
       double T2 = T * T;
       double aT4 = a * T2 * T2;
       double r0 = (Eg - Eg0) + cr * R;
-      double r1 = (k * aT4 - kE0 - k * R) + (kw - R) * inv_g;
-      if (fabs(r0) < tolG && cr * fabs(r1) <= tolR) {
+      double r1 = kg * (aT4 - E0 - R) + (kw - R);
+      if (fabs(r0) < tolG && cr * fabs(r1) <= tolR * g) {
         conv = true;
         break;
       }
       if (it >= ph.newton_max) break;
-      double J10 = 4.0 * k * a * T2 * T * inv_Cv;
-      double opk = 1.0 + k;
-      double det = -opk - cr * J10;
-      double inv_det = 1.0 / det;
-      double dEg = (r0 * opk + cr * r1) * inv_det;
+      double J10 = 4.0 * kg * a * T2 * T * inv_Cv;
+      double gpk = g * (1.0 + k);
+      double det = -gpk - cr * J10;
+      double inv_det = MIXED ? (double)(1.0f / (float)det) : 1.0 / det;
+      double dEg = (r0 * gpk + cr * r1) * inv_det;
       double dR = (r0 * J10 - r1) * inv_det;
       Eg += dEg;
       R += dR;
@@ -270,7 +321,7 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
         for (int i = 0; i < 3; ++i) vP[i] = ha * v[i] + t * Ft[i];
       }
     }
-    double inv_den = 1.0 / (1.0 + k * g);
+    double inv_den = 1.0 / (1.0 + kg);
     double Fn[3], mn[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -278,6 +329,7 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
       mn[i] = y[1 + i] - (Fn[i] - y[5 + i]) * ph.inv_cchat;
     }
     double Q_old = k * ((g - 1.0) * (aT4 - E) + w);
+    // the updated v, beta^2, g, v.F/c^2: the next pass freezes these
     double vn[3] = {mn[0] * inv_rho, mn[1] * inv_rho, mn[2] * inv_rho};
     double beta2n = (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]) * ph.inv_c2;
     double gn = (ph.vc_order == 2) ? 1.0 + 0.5 * beta2n : 1.0;
@@ -291,7 +343,11 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
     for (int i = 0; i < 3; ++i) {
       F[i] = Fn[i];
       m[i] = mn[i];
+      v[i] = vn[i];
     }
+    g = gn;
+    w = wn;
+    Ekin = 0.5 * (m[0] * v[0] + m[1] * v[1] + m[2] * v[2]);
     double dQ = fabs(Q_new - Q_old);
     if (dQ <= ph.outer_rtol * fabs(Q_old) || dQ <= ph.outer_rtol * fabs(R) ||
         dQ <= ph.outer_rtol * Q_scale) {

@@ -36,7 +36,7 @@ struct Tile<1> {
   static constexpr int TX = 256, TY = 1, LZ = 1, HX = 2, HY = 0, NPL = 1;
 };
 
-template <int NDIM>
+template <int NDIM, typename R>
 struct Smem {
   using T = Tile<NDIM>;
   static constexpr int PW = T::TX + 2 * T::HX;
@@ -45,7 +45,7 @@ struct Smem {
   static constexpr int RING = T::NPL * 4 * PS;         // doubles
   static constexpr int FX = 4 * T::TY * (T::TX + 1);   // x-face fluxes
   static constexpr int FY = NDIM >= 2 ? 4 * (T::TY + 1) * T::TX : 0;
-  static constexpr size_t BYTES = sizeof(double) * (RING + FX + FY);
+  static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY);
 };
 
 // Coordinate x >= -2 folded onto [0, n) by the boundary condition (padding
@@ -97,26 +97,28 @@ __device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, in
   return eps_direct(A, il, il + (xb - c[d]) * g.stride[d], d);
 }
 
-// load plane zg (global z, may be a ghost plane) into ring slot `slot`
-template <int NDIM>
-__device__ __forceinline__ void load_plane(const StageArgs& A, double* ring, int slot, int zg,
+// load plane zg (global z, may be a ghost plane) into ring slot `slot`,
+// converting to the transport precision R
+template <int NDIM, typename R>
+__device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot, int zg,
                                            int x0, int y0) {
   using T = Tile<NDIM>;
-  using S = Smem<NDIM>;
+  using S = Smem<NDIM, R>;
   const Geometry& g = A.g;
+  const R inv_c = (R)A.ph.inv_c;
   bool fz = false;
   int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz) : 0;
-  double* pl = ring + slot * 4 * S::PS;
+  R* pl = ring + slot * 4 * S::PS;
   for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
     int ii = c % S::PW, jj = c / S::PW;
     bool fx = false, fy = false;
     int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx);
     int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy) : 0;
     int idx = xf + g.n[0] * (yf + g.n[1] * zf);
-    double E = __ldg(A.yt[Y_ERAD] + idx);
-    double Fx = __ldg(A.yt[Y_FX] + idx) * A.ph.inv_c;
-    double Fy = __ldg(A.yt[Y_FY] + idx) * A.ph.inv_c;
-    double Fz = __ldg(A.yt[Y_FZ] + idx) * A.ph.inv_c;
+    R E = (R)__ldg(A.yt[Y_ERAD] + idx);
+    R Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
+    R Fy = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
+    R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
     pl[0 * S::PS + c] = E;
     pl[1 * S::PS + c] = fx ? -Fx : Fx;
     pl[2 * S::PS + c] = fy ? -Fy : Fy;
@@ -124,42 +126,45 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, double* ring, int
   }
 }
 
-template <int NDIM>
-__device__ __forceinline__ void cell_of(const double* pl, int c, double u[4]) {
-  using S = Smem<NDIM>;
+template <int NDIM, typename R>
+__device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
+  using S = Smem<NDIM, R>;
 #pragma unroll
   for (int q = 0; q < 4; ++q) u[q] = pl[q * S::PS + c];
 }
 
 // flux through the face between plane cells c - st and c (stride st)
-template <int NDIM>
-__device__ __forceinline__ bool plane_face(const double* pl, int c, int st, int d,
-                                           double eps, double chat, int closure,
-                                           double out[4]) {
-  double am[4], a[4], b[4], bp[4];
-  cell_of<NDIM>(pl, c - 2 * st, am);
-  cell_of<NDIM>(pl, c - st, a);
-  cell_of<NDIM>(pl, c, b);
-  cell_of<NDIM>(pl, c + st, bp);
-  double L[4], R[4];
+template <int NDIM, typename R>
+__device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R eps, R chat,
+                                           int closure, R out[4]) {
+  R am[4], a[4], b[4], bp[4];
+  cell_of<NDIM, R>(pl, c - 2 * st, am);
+  cell_of<NDIM, R>(pl, c - st, a);
+  cell_of<NDIM, R>(pl, c, b);
+  cell_of<NDIM, R>(pl, c + st, bp);
+  R L[4], Rr[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     L[q] = a[q] + half_slope(am[q], a[q], b[q]);
-    R[q] = b[q] - half_slope(a[q], b[q], bp[q]);
+    Rr[q] = b[q] - half_slope(a[q], b[q], bp[q]);
   }
-  return hll_states<double>(d, L, R, eps, chat, closure, out);
+  return hll_states<R>(d, L, Rr, eps, chat, closure, out);
 }
 
-template <int STAGE, int NDIM>
+// R: precision of reconstruction, closure and HLL fluxes (double for FP64,
+// float for MIXED); the state, the flux differences, the updates and the
+// local solve are double in both.
+template <int STAGE, int NDIM, typename R>
 __global__ void __launch_bounds__(Tile<NDIM>::TX * Tile<NDIM>::TY, 2)
 stage_kernel(const StageArgs A) {
   using T = Tile<NDIM>;
-  using S = Smem<NDIM>;
+  using S = Smem<NDIM, R>;
   constexpr int TX = T::TX, TY = T::TY, NT = TX * TY;
-  extern __shared__ double smem[];
-  double* ring = smem;
-  double* fxs = ring + S::RING;
-  double* fys = fxs + S::FX;
+  constexpr bool MIXED = sizeof(R) == sizeof(float);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* ring = reinterpret_cast<R*>(smem_raw);
+  R* fxs = ring + S::RING;
+  R* fys = fxs + S::FX;
   __shared__ int s_skip;
   __shared__ int s_max_nn[NT / 32], s_max_no[NT / 32];
   __shared__ unsigned long long s_sum_nn[NT / 32], s_cnt[NT / 32], s_sum_no[NT / 32];
@@ -170,7 +175,7 @@ stage_kernel(const StageArgs A) {
 
   const Geometry& g = A.g;
   const Physics& ph = A.ph;
-  const double chat = ph.chat;
+  const R chat = (R)ph.chat;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int ix = x0 + tx, iy = y0 + ty;
@@ -185,55 +190,56 @@ stage_kernel(const StageArgs A) {
   unsigned long long nn_sum = 0, no_sum = 0, cnt = 0;
   bool zbad = false;
 
-  double zlo[4] = {0.0, 0.0, 0.0, 0.0};  // z-face flux below the current cell
-  double hz[4] = {0.0, 0.0, 0.0, 0.0};   // half z-slope of the current cell
+  R zlo[4] = {R(0), R(0), R(0), R(0)};  // z-face flux below the current cell
+  R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell
   if (NDIM == 3) {
-    for (int o = -2; o <= 1; ++o) load_plane<NDIM>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
+    for (int o = -2; o <= 1; ++o)
+      load_plane<NDIM, R>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
     __syncthreads();
-    double um[4], u0[4], up[4], upp[4];
-    cell_of<NDIM>(ring + ((kbeg - 2) & 3) * 4 * S::PS, own, um);
-    cell_of<NDIM>(ring + ((kbeg - 1) & 3) * 4 * S::PS, own, u0);
-    cell_of<NDIM>(ring + ((kbeg + 0) & 3) * 4 * S::PS, own, up);
-    cell_of<NDIM>(ring + ((kbeg + 1) & 3) * 4 * S::PS, own, upp);
-    double L[4], R[4];
+    R um[4], u0[4], up[4], upp[4];
+    cell_of<NDIM, R>(ring + ((kbeg - 2) & 3) * 4 * S::PS, own, um);
+    cell_of<NDIM, R>(ring + ((kbeg - 1) & 3) * 4 * S::PS, own, u0);
+    cell_of<NDIM, R>(ring + ((kbeg + 0) & 3) * 4 * S::PS, own, up);
+    cell_of<NDIM, R>(ring + ((kbeg + 1) & 3) * 4 * S::PS, own, upp);
+    R L[4], Rr[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       hz[q] = half_slope(u0[q], up[q], upp[q]);
       L[q] = u0[q] + half_slope(um[q], u0[q], up[q]);
-      R[q] = up[q] - hz[q];
+      Rr[q] = up[q] - hz[q];
     }
-    double eps = face_eps(A, 2, cx, cy, kbeg - 1);
-    zbad = !hll_states<double>(2, L, R, eps, chat, ph.closure, zlo);
+    R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
+    zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
     __syncthreads();  // plane kbeg-2's slot is reloaded by the first iteration
   }
 
   for (int k = kbeg; k < kend; ++k) {
     if (NDIM == 3) {
-      load_plane<NDIM>(A, ring, (k + 2) & 3, k + 2, x0, y0);
+      load_plane<NDIM, R>(A, ring, (k + 2) & 3, k + 2, x0, y0);
     } else {
-      load_plane<NDIM>(A, ring, 0, 0, x0, y0);
+      load_plane<NDIM, R>(A, ring, 0, 0, x0, y0);
     }
     __syncthreads();
-    const double* pl = ring + (NDIM == 3 ? (k & 3) : 0) * 4 * S::PS;
+    const R* pl = ring + (NDIM == 3 ? (k & 3) : 0) * 4 * S::PS;
     bool bad = zbad;
 
     // ---- z-face k+1/2 of the own column
-    double zhi[4] = {0.0, 0.0, 0.0, 0.0};
-    double hz1[4] = {0.0, 0.0, 0.0, 0.0};
+    R zhi[4] = {R(0), R(0), R(0), R(0)};
+    R hz1[4] = {R(0), R(0), R(0), R(0)};
     if (NDIM == 3) {
-      double u0[4], u1[4], u2[4];
-      cell_of<NDIM>(pl, own, u0);
-      cell_of<NDIM>(ring + ((k + 1) & 3) * 4 * S::PS, own, u1);
-      cell_of<NDIM>(ring + ((k + 2) & 3) * 4 * S::PS, own, u2);
-      double L[4], R[4];
+      R u0[4], u1[4], u2[4];
+      cell_of<NDIM, R>(pl, own, u0);
+      cell_of<NDIM, R>(ring + ((k + 1) & 3) * 4 * S::PS, own, u1);
+      cell_of<NDIM, R>(ring + ((k + 2) & 3) * 4 * S::PS, own, u2);
+      R L[4], Rr[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         hz1[q] = half_slope(u0[q], u1[q], u2[q]);
         L[q] = u0[q] + hz[q];
-        R[q] = u1[q] - hz1[q];
+        Rr[q] = u1[q] - hz1[q];
       }
-      double eps = face_eps(A, 2, cx, cy, k);
-      zbad = !hll_states<double>(2, L, R, eps, chat, ph.closure, zhi);
+      R eps = (R)face_eps(A, 2, cx, cy, k);
+      zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
       bad = bad || zbad;
     }
 
@@ -244,12 +250,12 @@ stage_kernel(const StageArgs A) {
       int xl = x0 + fi - 1;
       int yr = NDIM >= 2 ? y0 + fj : 0;
       bool real = xl < g.n[0] && (NDIM < 2 || yr < g.n[1]);
-      double eps = real ? face_eps(A, 0, xl, yr, k) : 1.0;
-      double out[4];
-      if (!plane_face<NDIM>(pl, c, 1, 0, eps, chat, ph.closure, out) && real) {
+      R eps = real ? (R)face_eps(A, 0, xl, yr, k) : R(1);
+      R out[4];
+      if (!plane_face<NDIM, R>(pl, c, 1, 0, eps, chat, ph.closure, out) && real) {
         // a face with E <= 0 poisons both neighbours' fluxes
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[q] = __longlong_as_double(0x7ff8000000000000ll);
+        for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) fxs[q * TY * (TX + 1) + f] = out[q];
@@ -261,11 +267,11 @@ stage_kernel(const StageArgs A) {
         int c = fi + T::HX + (fj + T::HY) * S::PW;
         int xr = x0 + fi, yl = y0 + fj - 1;
         bool real = xr < g.n[0] && yl < g.n[1];
-        double eps = real ? face_eps(A, 1, xr, yl, k) : 1.0;
-        double out[4];
-        if (!plane_face<NDIM>(pl, c, S::PW, 1, eps, chat, ph.closure, out) && real) {
+        R eps = real ? (R)face_eps(A, 1, xr, yl, k) : R(1);
+        R out[4];
+        if (!plane_face<NDIM, R>(pl, c, S::PW, 1, eps, chat, ph.closure, out) && real) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) out[q] = __longlong_as_double(0x7ff8000000000000ll);
+          for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) fys[q * (TY + 1) * TX + f] = out[q];
@@ -277,22 +283,25 @@ stage_kernel(const StageArgs A) {
       const int idx = ix + g.n[0] * (iy + g.n[1] * k);
       double rate[4];
       const int fl = tx + ty * (TX + 1);
+      // flux differences in double: the difference of two floats is exact in
+      // double, so the update telescopes across cells in both precisions
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const double* fq = fxs + q * TY * (TX + 1);
-        rate[q] = -(fq[fl + 1] - fq[fl]) * g.inv_dx[0];
+        const R* fq = fxs + q * TY * (TX + 1);
+        rate[q] = -((double)fq[fl + 1] - (double)fq[fl]) * g.inv_dx[0];
       }
       if (NDIM >= 2) {
         const int fb = tx + ty * TX;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const double* fq = fys + q * (TY + 1) * TX;
-          rate[q] -= (fq[fb + TX] - fq[fb]) * g.inv_dx[1];
+          const R* fq = fys + q * (TY + 1) * TX;
+          rate[q] -= ((double)fq[fb + TX] - (double)fq[fb]) * g.inv_dx[1];
         }
       }
       if (NDIM == 3) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) rate[q] -= (zhi[q] - zlo[q]) * g.inv_dx[2];
+        for (int q = 0; q < 4; ++q)
+          rate[q] -= ((double)zhi[q] - (double)zlo[q]) * g.inv_dx[2];
       }
       bad = bad || !isfinite(rate[0]) || !isfinite(rate[1]) || !isfinite(rate[2]) ||
             !isfinite(rate[3]);
@@ -327,7 +336,7 @@ stage_kernel(const StageArgs A) {
       int code = RHD_OK;
       if (STAGE != 0) {
         code = bad ? RHD_ERR_NONPHYSICAL
-                   : local_solve(ph, STAGE == 1 ? A.dt : 0.5 * A.dt, rho, chi, y, nn, no);
+                   : local_solve<MIXED>(ph, STAGE == 1 ? A.dt : 0.5 * A.dt, rho, chi, y, nn, no);
 #pragma unroll
         for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
       }
@@ -436,34 +445,39 @@ cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* k
   return cudaGetLastError();
 }
 
-template <int STAGE, int NDIM>
+template <int STAGE, int NDIM, typename R>
 static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s) {
   using T = Tile<NDIM>;
-  using S = Smem<NDIM>;
+  using S = Smem<NDIM, R>;
   // opt in to more than 48 KiB of dynamic shared memory (idempotent)
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<STAGE, NDIM>,
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<STAGE, NDIM, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)S::BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid((A.g.n[0] + T::TX - 1) / T::TX, (A.g.n[1] + T::TY - 1) / T::TY,
             (A.g.n[2] + T::LZ - 1) / T::LZ);
-  stage_kernel<STAGE, NDIM><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
+  stage_kernel<STAGE, NDIM, R><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
   return cudaGetLastError();
 }
 
-template <int STAGE>
-static cudaError_t launch_fp64(const StageArgs& A, cudaStream_t s) {
+template <int STAGE, typename R>
+static cudaError_t launch_prec(const StageArgs& A, cudaStream_t s) {
   switch (A.g.ndim) {
-    case 1: return launch_nd<STAGE, 1>(A, s);
-    case 2: return launch_nd<STAGE, 2>(A, s);
-    default: return launch_nd<STAGE, 3>(A, s);
+    case 1: return launch_nd<STAGE, 1, R>(A, s);
+    case 2: return launch_nd<STAGE, 2, R>(A, s);
+    default: return launch_nd<STAGE, 3, R>(A, s);
   }
 }
 
+template <int STAGE>
+static cudaError_t launch_stage_t(int precision, const StageArgs& A, cudaStream_t s) {
+  return precision == RHD_PREC_MIXED ? launch_prec<STAGE, float>(A, s)
+                                     : launch_prec<STAGE, double>(A, s);
+}
+
 cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s) {
-  (void)precision;
-  if (stage == 0) return launch_fp64<0>(A, s);
-  return stage == 1 ? launch_fp64<1>(A, s) : launch_fp64<2>(A, s);
+  if (stage == 0) return launch_stage_t<0>(precision, A, s);
+  return stage == 1 ? launch_stage_t<1>(precision, A, s) : launch_stage_t<2>(precision, A, s);
 }
 
 }  // namespace rhd
