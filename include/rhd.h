@@ -216,6 +216,56 @@ const char* rhd_last_error(const rhd_ctx* ctx);
 /* Release all device memory and the private stream.  NULL is ignored. */
 void rhd_destroy(rhd_ctx* ctx);
 
+/* ---------------------------------------------------------------------
+ * Batched form: many independent 1-D and 2-D grids advanced together.
+ *
+ * Every problem has its own grid, physics and default time step
+ * (rhd_default_dt of its params); all share one precision.  The fields of all
+ * problems live in pooled device arrays.  One step is two launches of a
+ * persistent kernel (stage 1 and stage 2 of eq. imex1/imex2) whose blocks
+ * take (problem, tile) work items from an atomic counter; the launches of an
+ * rhd_batch_step call are captured once into a CUDA graph and replayed on
+ * later calls with the same step count.
+ * ------------------------------------------------------------------- */
+typedef struct rhd_batch rhd_batch;
+
+/* Validate and allocate nprob problems (probs[p].ndim must be 1 or 2, one
+ * precision for all).  *out is NULL on error (message: rhd_last_error(NULL)). */
+rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out);
+
+/* Run on this CUDA stream (drops the captured graphs).  The legacy default
+ * stream (NULL) cannot hold a graph capture: with NULL the batch waits for
+ * the legacy stream's earlier work and runs on its private stream. */
+rhd_status rhd_batch_set_stream(rhd_batch* b, void* cuda_stream);
+
+/* Launch configuration: tile2d selects the 2-D tile (0: 32 x 8, 1: 64 x 4,
+ * 2: 16 x 16 cells), blocks_per_sm the persistent grid (1 or 2 blocks per SM).
+ * Results do not depend on it (the autotuner in paper_2404_08247_gb300/autotune.py
+ * picks it from timings). */
+rhd_status rhd_batch_configure(rhd_batch* b, int tile2d, int blocks_per_sm);
+
+/* Cells of problem prob, or of the whole batch for prob < 0 (-1 on error). */
+int64_t rhd_batch_cells(const rhd_batch* b, int prob);
+
+/* State of one problem: RHD_NFIELDS * ncell doubles, field-major as in
+ * rhd_state_set_all, host or device; same validation as rhd_state_set. */
+rhd_status rhd_batch_state_set(rhd_batch* b, int prob, const double* src, int64_t count,
+                               int src_on_device);
+rhd_status rhd_batch_state_get(rhd_batch* b, int prob, double* dst, int64_t count,
+                               int dst_on_device);
+
+/* Advance every problem nsteps steps of its own dt.  On failure every problem
+ * stays at the last completed step and info->fail_cell is a pooled cell index
+ * (see rhd_batch_locate); info->t counts steps.  Synchronises. */
+rhd_status rhd_batch_step(rhd_batch* b, int nsteps, rhd_step_info* info);
+
+/* Map a pooled cell index to (problem, cell). */
+rhd_status rhd_batch_locate(const rhd_batch* b, int64_t pooled_cell, int* prob,
+                            int64_t* cell);
+
+const char* rhd_batch_last_error(const rhd_batch* b);
+void rhd_batch_destroy(rhd_batch* b);
+
 /* Largest grid, in cells, that rhd_step_noalloc accepts. */
 #define RHD_NOALLOC_MAX_CELLS 262144
 

@@ -490,6 +490,7 @@ rhd_status rhd_step_async(rhd_ctx* c, int nsteps, double dt) {
     c->eps_dirty = false;
   }
   StageArgs A;
+  A.cell_base = 0;
   for (int d = 0; d < 3; ++d) A.eps[d] = c->eps[d];
   A.g = c->g;
   A.ph = c->ph;
@@ -591,6 +592,7 @@ rhd_status rhd_transport(rhd_ctx* c, double* rates, int64_t count, int dst_on_de
     c->eps_dirty = false;
   }
   StageArgs A;
+  A.cell_base = 0;
   A.g = c->g;
   A.ph = c->ph;
   A.dt = 0.0;

@@ -67,6 +67,7 @@ struct StageArgs {
   const double* eps[3];  // TAU mode: per-face optical-depth factors, or null
                          // (then computed from kappa and rho on the fly)
   double* rate[4];       // transport-only launch: dE/dt, dFx/dt, dFy/dt, dFz/dt
+  long long cell_base;   // added to cell indices in failure reports (batched pools)
   DevStatus* st;
 };
 

@@ -140,6 +140,7 @@ extern "C" rhd_status rhd_step_noalloc(const rhd_params* p, const double* state_
 
   cudaStream_t s = (cudaStream_t)stream;
   StageArgs A;
+  A.cell_base = 0;
   fill(p, A.g, A.ph);
   A.dt = dt;
   A.step = 0;

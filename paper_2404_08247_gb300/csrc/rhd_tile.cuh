@@ -1,0 +1,406 @@
+// rhd_tile.cuh -- one tile of one IMEX stage, shared by the grid kernels
+// (rhd_stage.cu) and the batched persistent kernel (rhd_batch.cu).
+//
+// Work layout (3-D): a block owns a TX x TY column of cells and marches
+// through a chunk of z planes.  E and F/c of four consecutive planes sit in a
+// shared-memory ring, each plane with a 2-cell halo in x and y (ghost cells
+// folded in at load time: periodic wrap, or mirror with the normal flux
+// negated).  Every face flux is computed exactly once: x- and y-faces of the
+// current plane by one thread each (into shared memory), z-faces by the thread
+// that owns the column (kept in registers from one plane to the next,
+// together with the half z-slope of the current cell).  The thread then
+// applies the conservative update and runs the cell's local implicit solve in
+// registers, so the explicit state never reaches HBM.  2-D grids use one
+// plane; 1-D grids use rows of TX cells.
+#pragma once
+
+#include "rhd_internal.cuh"
+
+namespace rhd {
+
+// A tile: TX x TY threads (one per cell of a plane), LZ planes per block in
+// 3-D.  HX, HY: halo widths; NPL: planes kept in the shared-memory ring.
+template <int NDIM_, int TX_, int TY_, int LZ_>
+struct TileT {
+  static constexpr int NDIM = NDIM_, TX = TX_, TY = TY_, LZ = LZ_;
+  static constexpr int HX = 2, HY = NDIM >= 2 ? 2 : 0, NPL = NDIM == 3 ? 4 : 1;
+  static constexpr int NT = TX * TY;
+};
+
+template <int NDIM>
+struct DefaultTileOf;
+template <>
+struct DefaultTileOf<3> { using type = TileT<3, 32, 8, 32>; };
+template <>
+struct DefaultTileOf<2> { using type = TileT<2, 32, 8, 1>; };
+template <>
+struct DefaultTileOf<1> { using type = TileT<1, 256, 1, 1>; };
+template <int NDIM>
+using Tile = typename DefaultTileOf<NDIM>::type;
+
+template <class T, typename R>
+struct SmemT {
+  static constexpr int PW = T::TX + 2 * T::HX;
+  static constexpr int PH = T::TY + 2 * T::HY;
+  static constexpr int PS = PW * PH;                   // cells per plane
+  static constexpr int RING = T::NPL * 4 * PS;         // doubles
+  static constexpr int FX = 4 * T::TY * (T::TX + 1);   // x-face fluxes
+  static constexpr int FY = T::NDIM >= 2 ? 4 * (T::TY + 1) * T::TX : 0;
+  static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY);
+};
+
+// Coordinate x >= -2 folded onto [0, n) by the boundary condition (padding
+// of a partial tile beyond n + 1 is clamped first); flip = mirror image.
+__device__ __forceinline__ int fold(int x, int n, int bclo, int bchi, bool& flip) {
+  flip = false;
+  x = min(x, n + 1);
+  if (x < 0) {
+    if (bclo == RHD_BC_PERIODIC) {
+      x = ((x % n) + n) % n;
+    } else {
+      x = -1 - x;
+      flip = true;
+    }
+  } else if (x >= n) {
+    if (bchi == RHD_BC_PERIODIC) {
+      x = x % n;
+    } else {
+      x = 2 * n - 1 - x;
+      flip = true;
+    }
+  }
+  return x;
+}
+
+__device__ __forceinline__ double eps_direct(const StageArgs& A, int ia, int ib, int d) {
+  double tau = 0.5 * (A.kappa[ia] * A.rho[ia] + A.kappa[ib] * A.rho[ib]) * A.g.dx[d];
+  return tau_factor(tau);
+}
+
+// Optical-depth factor of the face on the +d side of the cell c (c[d] may be
+// -1: the low wall face).  TAU mode only; 1 otherwise.
+__device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, int cy, int cz) {
+  if (A.ph.hll_mode != RHD_HLL_TAU) return 1.0;
+  const Geometry& g = A.g;
+  int c[3] = {cx, cy, cz};
+  if (c[d] < 0) {
+    if (g.bc[d][0] != RHD_BC_PERIODIC) {
+      c[d] = 0;  // reflecting wall: the ghost mirrors cell 0
+      int i0 = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+      return eps_direct(A, i0, i0, d);
+    }
+    c[d] = g.n[d] - 1;  // periodic: the same face as the top one
+  }
+  int il = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+  if (A.eps[d]) return __ldg(A.eps[d] + il);
+  bool flip;
+  int xb = fold(c[d] + 1, g.n[d], g.bc[d][0], g.bc[d][1], flip);
+  return eps_direct(A, il, il + (xb - c[d]) * g.stride[d], d);
+}
+
+// load plane zg (global z, may be a ghost plane) into ring slot `slot`,
+// converting to the transport precision R
+template <class T, typename R>
+__device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot, int zg,
+                                           int x0, int y0) {
+  constexpr int NDIM = T::NDIM;
+  using S = SmemT<T, R>;
+  const Geometry& g = A.g;
+  const R inv_c = (R)A.ph.inv_c;
+  bool fz = false;
+  int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz) : 0;
+  R* pl = ring + slot * 4 * S::PS;
+  for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
+    int ii = c % S::PW, jj = c / S::PW;
+    bool fx = false, fy = false;
+    int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx);
+    int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy) : 0;
+    int idx = xf + g.n[0] * (yf + g.n[1] * zf);
+    R E = (R)__ldg(A.yt[Y_ERAD] + idx);
+    R Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
+    R Fy = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
+    R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+    pl[0 * S::PS + c] = E;
+    pl[1 * S::PS + c] = fx ? -Fx : Fx;
+    pl[2 * S::PS + c] = fy ? -Fy : Fy;
+    pl[3 * S::PS + c] = fz ? -Fz : Fz;
+  }
+}
+
+template <class T, typename R>
+__device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
+  using S = SmemT<T, R>;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) u[q] = pl[q * S::PS + c];
+}
+
+// flux through the face between plane cells c - st and c (stride st)
+template <class T, typename R>
+__device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R eps, R chat,
+                                           int closure, R out[4]) {
+  R am[4], a[4], b[4], bp[4];
+  cell_of<T, R>(pl, c - 2 * st, am);
+  cell_of<T, R>(pl, c - st, a);
+  cell_of<T, R>(pl, c, b);
+  cell_of<T, R>(pl, c + st, bp);
+  R L[4], Rr[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    L[q] = a[q] + half_slope(am[q], a[q], b[q]);
+    Rr[q] = b[q] - half_slope(a[q], b[q], bp[q]);
+  }
+  return hll_states<R>(d, L, Rr, eps, chat, closure, out);
+}
+
+// Per-thread iteration statistics of the cells a thread has solved.
+struct TileStats {
+  int nn_max = 0, no_max = 0;
+  unsigned long long nn_sum = 0, no_sum = 0, cnt = 0;
+};
+
+// One tile of one stage (STAGE 1, 2, or 0 = transport rates only): the block
+// of T::NT threads owns the cells x0 + [0, TX) x y0 + [0, TY) x planes
+// [kbeg, kbeg + LZ) of the grid described by A.  R: precision of
+// reconstruction, closure and HLL fluxes (double for FP64, float for MIXED);
+// the state, the flux differences, the updates and the local solve are double
+// in both.  Every thread of the block must call it (it synchronises).
+template <int STAGE, class T, typename R>
+__device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, int kbeg,
+                                           unsigned char* smem_raw, TileStats& ts) {
+  using S = SmemT<T, R>;
+  constexpr int NDIM = T::NDIM;
+  constexpr int TX = T::TX, TY = T::TY, NT = TX * TY;
+  constexpr bool MIXED = sizeof(R) == sizeof(float);
+  R* ring = reinterpret_cast<R*>(smem_raw);
+  R* fxs = ring + S::RING;
+  R* fys = fxs + S::FX;
+
+  const Geometry& g = A.g;
+  const Physics& ph = A.ph;
+  const R chat = (R)ph.chat;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int ix = x0 + tx, iy = y0 + ty;
+  const bool col = ix < g.n[0] && (NDIM < 2 || iy < g.n[1]);
+  const int cy = NDIM >= 2 ? min(iy, g.n[1] - 1) : 0;  // clamped row of the column
+  const int cx = min(ix, g.n[0] - 1);
+  const int kend = min(kbeg + T::LZ, g.n[2]);
+  const int own = (tx + T::HX) + (ty + T::HY) * S::PW;  // own cell in a plane
+
+  bool zbad = false;
+
+  R zlo[4] = {R(0), R(0), R(0), R(0)};  // z-face flux below the current cell
+  R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell
+  if (NDIM == 3) {
+    for (int o = -2; o <= 1; ++o)
+      load_plane<T, R>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
+    __syncthreads();
+    R um[4], u0[4], up[4], upp[4];
+    cell_of<T, R>(ring + ((kbeg - 2) & 3) * 4 * S::PS, own, um);
+    cell_of<T, R>(ring + ((kbeg - 1) & 3) * 4 * S::PS, own, u0);
+    cell_of<T, R>(ring + ((kbeg + 0) & 3) * 4 * S::PS, own, up);
+    cell_of<T, R>(ring + ((kbeg + 1) & 3) * 4 * S::PS, own, upp);
+    R L[4], Rr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      hz[q] = half_slope(u0[q], up[q], upp[q]);
+      L[q] = u0[q] + half_slope(um[q], u0[q], up[q]);
+      Rr[q] = up[q] - hz[q];
+    }
+    R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
+    zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
+    __syncthreads();  // plane kbeg-2's slot is reloaded by the first iteration
+  }
+
+  for (int k = kbeg; k < kend; ++k) {
+    if (NDIM == 3) {
+      load_plane<T, R>(A, ring, (k + 2) & 3, k + 2, x0, y0);
+    } else {
+      load_plane<T, R>(A, ring, 0, 0, x0, y0);
+    }
+    __syncthreads();
+    const R* pl = ring + (NDIM == 3 ? (k & 3) : 0) * 4 * S::PS;
+    bool bad = zbad;
+
+    // ---- z-face k+1/2 of the own column
+    R zhi[4] = {R(0), R(0), R(0), R(0)};
+    R hz1[4] = {R(0), R(0), R(0), R(0)};
+    if (NDIM == 3) {
+      R u0[4], u1[4], u2[4];
+      cell_of<T, R>(pl, own, u0);
+      cell_of<T, R>(ring + ((k + 1) & 3) * 4 * S::PS, own, u1);
+      cell_of<T, R>(ring + ((k + 2) & 3) * 4 * S::PS, own, u2);
+      R L[4], Rr[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        hz1[q] = half_slope(u0[q], u1[q], u2[q]);
+        L[q] = u0[q] + hz[q];
+        Rr[q] = u1[q] - hz1[q];
+      }
+      R eps = (R)face_eps(A, 2, cx, cy, k);
+      zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
+      bad = bad || zbad;
+    }
+
+    // ---- x-faces of plane k: face f lies between tile cells fi-1 and fi
+    for (int f = threadIdx.x; f < (TX + 1) * TY; f += NT) {
+      int fi = f % (TX + 1), fj = f / (TX + 1);
+      int c = fi + T::HX + (fj + T::HY) * S::PW;
+      int xl = x0 + fi - 1;
+      int yr = NDIM >= 2 ? y0 + fj : 0;
+      bool real = xl < g.n[0] && (NDIM < 2 || yr < g.n[1]);
+      R eps = real ? (R)face_eps(A, 0, xl, yr, k) : R(1);
+      R out[4];
+      if (!plane_face<T, R>(pl, c, 1, 0, eps, chat, ph.closure, out) && real) {
+        // a face with E <= 0 poisons both neighbours' fluxes
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fxs[q * TY * (TX + 1) + f] = out[q];
+    }
+    // ---- y-faces of plane k: face f lies between rows fj-1 and fj
+    if (NDIM >= 2) {
+      for (int f = threadIdx.x; f < TX * (TY + 1); f += NT) {
+        int fi = f % TX, fj = f / TX;
+        int c = fi + T::HX + (fj + T::HY) * S::PW;
+        int xr = x0 + fi, yl = y0 + fj - 1;
+        bool real = xr < g.n[0] && yl < g.n[1];
+        R eps = real ? (R)face_eps(A, 1, xr, yl, k) : R(1);
+        R out[4];
+        if (!plane_face<T, R>(pl, c, S::PW, 1, eps, chat, ph.closure, out) && real) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fys[q * (TY + 1) * TX + f] = out[q];
+      }
+    }
+    __syncthreads();
+
+    if (col) {
+      const int idx = ix + g.n[0] * (iy + g.n[1] * k);
+      double rate[4];
+      const int fl = tx + ty * (TX + 1);
+      // flux differences in double: the difference of two floats is exact in
+      // double, so the update telescopes across cells in both precisions
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R* fq = fxs + q * TY * (TX + 1);
+        rate[q] = -((double)fq[fl + 1] - (double)fq[fl]) * g.inv_dx[0];
+      }
+      if (NDIM >= 2) {
+        const int fb = tx + ty * TX;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const R* fq = fys + q * (TY + 1) * TX;
+          rate[q] -= ((double)fq[fb + TX] - (double)fq[fb]) * g.inv_dx[1];
+        }
+      }
+      if (NDIM == 3) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          rate[q] -= ((double)zhi[q] - (double)zlo[q]) * g.inv_dx[2];
+      }
+      bad = bad || !isfinite(rate[0]) || !isfinite(rate[1]) || !isfinite(rate[2]) ||
+            !isfinite(rate[3]);
+
+      double y[8];
+      if (STAGE == 0) {
+        // transport only: s(y) of eq. (yrsla) for E and the physical flux F
+        A.rate[0][idx] = rate[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A.rate[1 + j][idx] = ph.c * rate[1 + j];
+        if (bad) {
+          atomicMin(&A.st->fail_key, ((unsigned long long)(A.cell_base + idx) << 8) | RHD_ERR_NONPHYSICAL);
+          A.st->fail_step = A.step;
+          A.st->fail_stage = 0;
+        }
+      } else if (STAGE == 1) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = A.yt[q][idx];
+        y[Y_ERAD] += A.dt * rate[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y[Y_FX + j] += A.dt * ph.c * rate[1 + j];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) y[q] = 0.5 * (A.yn[q][idx] + A.yt[q][idx]);
+        y[Y_ERAD] += 0.5 * A.dt * rate[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y[Y_FX + j] += 0.5 * A.dt * ph.c * rate[1 + j];
+      }
+      const double rho = A.rho[idx];
+      const double chi = A.kappa[idx] * rho;
+      int nn = 0, no = 0;
+      int code = RHD_OK;
+      if (STAGE != 0) {
+        code = bad ? RHD_ERR_NONPHYSICAL
+                   : local_solve<MIXED>(ph, STAGE == 1 ? A.dt : 0.5 * A.dt, rho, chi, y, nn, no);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
+      }
+      if (code != RHD_OK) {
+        atomicMin(&A.st->fail_key, ((unsigned long long)(A.cell_base + idx) << 8) | (unsigned)code);
+        A.st->fail_step = A.step;
+        A.st->fail_stage = STAGE;
+      }
+      ts.nn_max = max(ts.nn_max, nn);
+      ts.no_max = max(ts.no_max, no);
+      ts.nn_sum += nn;
+      ts.no_sum += no;
+      ts.cnt += 1;
+    }
+    if (NDIM == 3) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        zlo[q] = zhi[q];
+        hz[q] = hz1[q];
+      }
+    }
+    __syncthreads();
+  }
+
+}
+
+// Block reduction of TileStats (warp shuffles, then one atomic per block).
+template <int NT>
+__device__ __forceinline__ void flush_stats(DevStatus* st, TileStats& ts) {
+  __shared__ int s_max_nn[NT / 32], s_max_no[NT / 32];
+  __shared__ unsigned long long s_sum_nn[NT / 32], s_cnt[NT / 32], s_sum_no[NT / 32];
+  const unsigned full = 0xffffffffu;
+  int wmax_nn = __reduce_max_sync(full, ts.nn_max);
+  int wmax_no = __reduce_max_sync(full, ts.no_max);
+  unsigned long long nn_sum = ts.nn_sum, no_sum = ts.no_sum, cnt = ts.cnt;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    nn_sum += __shfl_down_sync(full, nn_sum, off);
+    no_sum += __shfl_down_sync(full, no_sum, off);
+    cnt += __shfl_down_sync(full, cnt, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_max_nn[warp] = wmax_nn;
+    s_max_no[warp] = wmax_no;
+    s_sum_nn[warp] = nn_sum;
+    s_sum_no[warp] = no_sum;
+    s_cnt[warp] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int bmn = 0, bmo = 0;
+    unsigned long long bs = 0, bc = 0, bo = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      bmn = max(bmn, s_max_nn[w]);
+      bmo = max(bmo, s_max_no[w]);
+      bs += s_sum_nn[w];
+      bc += s_cnt[w];
+      bo += s_sum_no[w];
+    }
+    if (bmn > 0) atomicMax(&st->max_newton, bmn);
+    if (bmo > 0) atomicMax(&st->max_outer, bmo);
+    if (bs) atomicAdd(&st->sum_newton, bs);
+    if (bc) atomicAdd(&st->n_solves, bc);
+    if (bo) atomicAdd(&st->sum_outer, bo);
+  }
+}
+
+}  // namespace rhd

@@ -214,3 +214,43 @@ def random_state(prob: dict, seed: int, tau_range=(1e-3, 1e3), T_range=(1.0, 3.0
     for d in range(3):
         U[F_FX + d] = fdir[d] / norm * mag
     return np.ascontiguousarray(U)
+
+
+def batched_problems(nprob: int = 512, seed: int = 11, c: float = 1e3,
+                     chat: float = 1e2, **kw):
+    """Independent problems of uneven size for the batched form: each is 1-D
+    with N ~ U{64..4096} or 2-D with side ~ U{32..256} (probability 1/2 each),
+    periodic on [0, 1]^d, rho = 1, log10 tau_cell iid U[-3, 3] per cell, a
+    Gaussian temperature pulse T = 1 + exp(-(r/0.05)^2) at the centre, and a
+    uniform velocity of random direction with |v|/c ~ U[0, 1e-3].
+    Returns a list of (problem, state)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nprob):
+        if rng.uniform() < 0.5:
+            n = [int(rng.integers(64, 4097))]
+        else:
+            side = int(rng.integers(32, 257))
+            n = [side, side]
+        ndim = len(n)
+        dx = [1.0 / v for v in n]
+        prob = base_problem(ndim, n, dx, bc="periodic", c=c, chat=chat, **kw)
+        sh = (1, n[1] if ndim == 2 else 1, n[0])
+        x, y, _ = cell_centres(prob)
+        r2 = (x - 0.5) ** 2 + ((y - 0.5) ** 2 if ndim == 2 else 0.0)
+        T = np.broadcast_to(1.0 + np.exp(-r2 / 0.05 ** 2), sh)
+        tau = 10.0 ** rng.uniform(-3.0, 3.0, sh)
+        rho = np.ones(sh)
+        kappa = tau / (rho * dx[0])
+        direction = rng.standard_normal(3)
+        if ndim == 1:
+            direction[1:] = 0.0
+        else:
+            direction[2] = 0.0
+        direction /= np.linalg.norm(direction)
+        speed = rng.uniform(0.0, 1e-3) * c
+        v = np.zeros((3,) + sh)
+        for d in range(3):
+            v[d] = speed * direction[d]
+        out.append((prob, equilibrium_state(prob, rho, T, v, kappa)))
+    return out

@@ -116,6 +116,17 @@ SIGNATURES = {
     "rhd_destroy": (None, [_V]),
     "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
                                         ctypes.POINTER(rhd_step_info)]),
+    "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
+    "rhd_batch_set_stream": (ctypes.c_int, [_V, _V]),
+    "rhd_batch_configure": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+    "rhd_batch_cells": (_I64, [_V, ctypes.c_int]),
+    "rhd_batch_state_set": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
+    "rhd_batch_state_get": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
+    "rhd_batch_step": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(rhd_step_info)]),
+    "rhd_batch_locate": (ctypes.c_int, [_V, _I64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(_I64)]),
+    "rhd_batch_last_error": (ctypes.c_char_p, [_V]),
+    "rhd_batch_destroy": (None, [_V]),
 }
 RHD_NOALLOC_MAX_CELLS = 262144
 
@@ -337,3 +348,83 @@ class RHDContext:
 
     def default_dt(self) -> float:
         return rhd_default_dt(self.params)
+
+
+class RHDBatch:
+    """Many independent 1-D/2-D problems behind the rhd_batch C ABI."""
+
+    TILES = {0: (32, 8), 1: (64, 4), 2: (16, 16)}
+
+    def __init__(self, probs, precision="fp64", stream=None):
+        self.lib = load()
+        self.probs = list(probs)
+        arr = (rhd_params * len(self.probs))(
+            *[params_from_problem(p, precision) for p in self.probs])
+        h = ctypes.c_void_p()
+        _check(self.lib.rhd_batch_init(arr, len(self.probs), ctypes.byref(h)))
+        self.h = h
+        self.shapes = [(RHD_NFIELDS, int(p["n"][2]), int(p["n"][1]), int(p["n"][0]))
+                       for p in self.probs]
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, st):
+        if st != RHD_OK:
+            msg = self.lib.rhd_batch_last_error(self.h)
+            raise RHDError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rhd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.rhd_batch_set_stream(self.h, ctypes.c_void_p(int(handle or 0))))
+
+    def configure(self, tile2d: int, blocks_per_sm: int):
+        self._check(self.lib.rhd_batch_configure(self.h, int(tile2d), int(blocks_per_sm)))
+
+    def cells(self, prob: int = -1) -> int:
+        return int(self.lib.rhd_batch_cells(self.h, prob))
+
+    def set_state(self, prob: int, U):
+        ptr, dev = _ptr(U)
+        self._check(self.lib.rhd_batch_state_set(self.h, prob, ctypes.c_void_p(ptr),
+                                                 RHD_NFIELDS * self.cells(prob), dev))
+
+    def get_state(self, prob: int, out=None):
+        if out is None:
+            out = np.empty(self.shapes[prob], dtype=np.float64)
+        ptr, dev = _ptr(out)
+        self._check(self.lib.rhd_batch_state_get(self.h, prob, ctypes.c_void_p(ptr),
+                                                 RHD_NFIELDS * self.cells(prob), dev))
+        return out
+
+    def step(self, nsteps: int = 1, raise_on_error=True) -> dict:
+        info = rhd_step_info()
+        st = self.lib.rhd_batch_step(self.h, int(nsteps), ctypes.byref(info))
+        if raise_on_error:
+            self._check(st)
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def locate(self, pooled_cell: int):
+        p = ctypes.c_int()
+        c = _I64()
+        self._check(self.lib.rhd_batch_locate(self.h, int(pooled_cell), ctypes.byref(p),
+                                              ctypes.byref(c)))
+        return p.value, c.value
