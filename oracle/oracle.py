@@ -1,4 +1,5 @@
-"""Python access to the serial FP64 CPU oracle in ``rhd_oracle.c``.
+"""Python access to the serial FP64 CPU oracle in ``rhd_oracle.c`` and its
+adjoint in ``rhd_oracle_adj.c``.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only callers.  The library never imports
@@ -20,6 +21,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "rhd_oracle.c")
+SRC_ADJ = os.path.join(HERE, "rhd_oracle_adj.c")
 HDR = os.path.join(HERE, "rhd_oracle.h")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
@@ -39,11 +41,11 @@ def build(force: bool = False) -> str:
     stale = force or not os.path.exists(LIB)
     if not stale:
         t = os.path.getmtime(LIB)
-        stale = any(os.path.getmtime(f) > t for f in (SRC, HDR))
+        stale = any(os.path.getmtime(f) > t for f in (SRC, SRC_ADJ, HDR))
     if stale:
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, SRC, "-lm"]
+               "-o", tmp, SRC, SRC_ADJ, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB
@@ -107,6 +109,14 @@ def lib():
         L.orc_step.restype = ctypes.c_int
         L.orc_totals.argtypes = [P, dp, dp]
         L.orc_totals.restype = None
+        L.orc_step_tape.argtypes = [P, dp, ctypes.c_double, dp]
+        L.orc_step_tape.restype = ctypes.c_int
+        L.orc_step_adjoint.argtypes = [P, dp, dp, dp, ctypes.c_double, dp, dp, dp]
+        L.orc_step_adjoint.restype = ctypes.c_int
+        L.orc_local_solve_adjoint.argtypes = [P, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, dp, dp,
+                                              dp, dp]
+        L.orc_local_solve_adjoint.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -211,3 +221,69 @@ def totals(prob: dict, U: np.ndarray) -> np.ndarray:
     out = np.zeros(4, dtype=np.float64)
     lib().orc_totals(ctypes.byref(p), _dptr(U), _dptr(out))
     return out
+
+
+# ------------------------------------------------------------------ adjoint
+
+SLOT_FIELDS = ("egas", "mx", "my", "mz", "erad", "fx", "fy", "fz")
+SLOT_INDEX = tuple(FIELDS.index(f) for f in SLOT_FIELDS)
+
+
+def step_tape(prob: dict, U: np.ndarray, dt: float = 0.0) -> np.ndarray:
+    """One step of U (modified in place); returns the tape, shape
+    (3, 8) + grid: y(n), y(n+1/2), y(n+1) in the slot order SLOT_FIELDS."""
+    p = make_params(prob)
+    tape = np.zeros((3, 8) + U.shape[1:], dtype=np.float64)
+    st = lib().orc_step_tape(ctypes.byref(p), _dptr(U), float(dt), _dptr(tape))
+    if st != 0:
+        raise RuntimeError("oracle taped step failed: %s" % STATUS.get(st, st))
+    return tape
+
+
+def step_adjoint(prob: dict, rho: np.ndarray, kappa: np.ndarray, tape: np.ndarray,
+                 ybar1: np.ndarray, kbar: np.ndarray, dt: float = 0.0) -> np.ndarray:
+    """Adjoint of one taped step: returns dL/dy(n) (8 slots) from
+    ybar1 = dL/dy(n+1); adds dL/dkappa into kbar (modified in place)."""
+    p = make_params(prob)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    ybar1 = np.ascontiguousarray(ybar1, dtype=np.float64)
+    ybar0 = np.zeros_like(ybar1)
+    assert kbar.dtype == np.float64 and kbar.flags["C_CONTIGUOUS"]
+    st = lib().orc_step_adjoint(ctypes.byref(p), _dptr(rho), _dptr(kappa), _dptr(tape),
+                                float(dt), _dptr(ybar1), _dptr(ybar0), _dptr(kbar))
+    if st != 0:
+        raise RuntimeError("oracle step adjoint failed: %s" % STATUS.get(st, st))
+    return ybar0
+
+
+def local_solve_adjoint(prob: dict, theta: float, dt: float, rho: float, chi: float,
+                        yout, ybar_out) -> tuple:
+    """Adjoint of one converged local solve with output yout.
+    Returns (status, ybar_in, chibar)."""
+    p = make_params(prob)
+    y = np.ascontiguousarray(np.asarray(yout, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(ybar_out, dtype=np.float64))
+    bin_ = np.zeros(8, dtype=np.float64)
+    cb = np.zeros(1, dtype=np.float64)
+    st = lib().orc_local_solve_adjoint(ctypes.byref(p), float(theta), float(dt),
+                                       float(rho), float(chi), _dptr(y), _dptr(b),
+                                       _dptr(bin_), _dptr(cb))
+    return st, bin_, float(cb[0])
+
+
+def trajectory_gradient(prob: dict, U0: np.ndarray, nsteps: int, loss_grad,
+                        dt: float = 0.0):
+    """Reverse-mode gradient of a loss of the final state after nsteps.
+
+    loss_grad(U_final) -> (L, dL/dU_final as 8 slots).  Returns
+    (L, ybar0 (8 slots, dL/dy(0)), kbar (dL/dkappa)).  Keeps every tape."""
+    U = U0.copy()
+    tapes = [step_tape(prob, U, dt) for _ in range(nsteps)]
+    L, ybar = loss_grad(U)
+    rho = U0[FIELDS.index("rho")]
+    kappa = U0[FIELDS.index("kappa")]
+    kbar = np.zeros_like(rho)
+    for tape in reversed(tapes):
+        ybar = step_adjoint(prob, rho, kappa, tape, ybar, kbar, dt)
+    return L, ybar, kbar

@@ -93,6 +93,25 @@ int orc_step(const orc_params* p, double* U, double dt, orc_info* info);
  * [1..3] = sum (m + F/(c chat)) V. */
 void orc_totals(const orc_params* p, const double* U, double out[4]);
 
+/* ---- adjoint (rhd_oracle_adj.c) ----
+ * Tapes and adjoint states are slot-major: 8 slots (Egas, mx, my, mz, E, Fx,
+ * Fy, Fz) of ncell doubles each. */
+
+/* One step as orc_step that also writes the tape: y(n), y(n+1/2), y(n+1),
+ * 3 x 8 x ncell doubles. */
+int orc_step_tape(const orc_params* p, double* U, double dt, double* tape);
+
+/* Adjoint of one taped step: ybar0 = dL/dy(n) from ybar1 = dL/dy(n+1);
+ * kbar (ncell) += dL/dkappa.  rho, kappa: the static fields. */
+int orc_step_adjoint(const orc_params* p, const double* rho, const double* kappa,
+                     const double* tape, double dt, const double* ybar1,
+                     double* ybar0, double* kbar);
+
+/* Adjoint of one converged local solve (implicit-function theorem). */
+int orc_local_solve_adjoint(const orc_params* p, double theta, double dt, double rho,
+                            double chi, const double yout[8], const double ybar_out[8],
+                            double ybar_in[8], double* chibar);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,7 +108,7 @@ def gaussian_random_field(shape, slope: float, rng: np.random.Generator) -> np.n
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (slope / 4.0)  # sqrt(P) = k^(slope/2)
-    field = np.fft.irfftn(fk * amp, s=shape)
+    field = np.fft.irfftn(fk * amp, s=shape, axes=tuple(range(len(shape))))
     field -= field.mean()
     sd = field.std()
     return field / sd if sd > 0 else field
@@ -254,3 +254,51 @@ def batched_problems(nprob: int = 512, seed: int = 11, c: float = 1e3,
             v[d] = speed * direction[d]
         out.append((prob, equilibrium_state(prob, rho, T, v, kappa)))
     return out
+
+
+def pulse_inverse_problem_2d(n: int = 512, seed_chi: int = 7, seed_target: int = 8,
+                             seed_T: int = 9, T_ripple: float = 0.01, c: float = 1e3,
+                             nsteps: int = 200, **kw):
+    """Differentiation workload: a radiation pulse on a periodic n^2 grid
+    through a log-normal opacity field, with a target radiation field.
+
+    rho = 1, gas at rest; ln chi is a k^-4 Gaussian random field (sigma = 1,
+    seed ``seed_chi``) scaled so that the median tau_cell = chi dx is 1;
+    T = (1 + 9 exp(-r^2 / (2 0.05^2))) (1 + T_ripple g) about the centre, with g
+    a unit-variance k^-4 Gaussian random field (seed ``seed_T``); radiation in
+    equilibrium (E = a T^4, F = 0); chat = c.  The ripple keeps every region
+    of the grid non-uniform: on exactly uniform data the limited slopes sit
+    at the limiter's kink, where the step has one-sided derivatives only.  The target is
+    E_tgt = a (1 + 9 exp(-|x - x1|^2 / (2 0.08^2)))^4 with x1 uniform in
+    [0.25, 0.75]^2 (seed ``seed_target``).  The loss is
+    L = sum (E(nsteps) - E_tgt)^2 over cells.
+
+    Returns (problem, T0 (1, n, n), log_kappa (1, n, n), E_tgt (1, n, n), nsteps)."""
+    dx = 1.0 / n
+    prob = base_problem(2, [n, n], [dx, dx], bc="periodic", c=c, chat=c, **kw)
+    sh = (1, n, n)
+    lnchi = gaussian_random_field(sh, -4.0, np.random.default_rng(seed_chi))
+    chi = np.exp(lnchi)
+    chi *= 1.0 / (np.median(chi) * dx)
+    x, y, _ = cell_centres(prob)
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
+    ripple = gaussian_random_field(sh, -4.0, np.random.default_rng(seed_T))
+    T0 = np.ascontiguousarray((1.0 + 9.0 * np.exp(-r2 / (2 * 0.05 ** 2))) *
+                              (1.0 + T_ripple * ripple))
+    x1 = np.random.default_rng(seed_target).uniform(0.25, 0.75, 2)
+    r2t = (x - x1[0]) ** 2 + (y - x1[1]) ** 2
+    a = prob.get("a_rad", 1.0)
+    E_tgt = np.ascontiguousarray(
+        np.broadcast_to(a * (1.0 + 9.0 * np.exp(-r2t / (2 * 0.08 ** 2))) ** 4, sh))
+    log_kappa = np.log(chi)  # rho = 1
+    return prob, T0, np.ascontiguousarray(log_kappa), E_tgt, nsteps
+
+
+def rest_state(prob: dict, T, log_kappa) -> np.ndarray:
+    """State of gas at rest (rho = 1) with radiation in equilibrium at T and
+    opacity exp(log_kappa): the map from the differentiation workload's
+    parameters to the step's input."""
+    T = np.asarray(T, dtype=np.float64)
+    sh = T.shape
+    return equilibrium_state(prob, np.ones(sh), T, np.zeros((3,) + sh),
+                             np.exp(np.asarray(log_kappa, dtype=np.float64)))
