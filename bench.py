@@ -69,6 +69,9 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-problem batched workload")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the 512^2 differentiation workload")
+    ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--single-form", action="store_true",
                     help="time only --precision (default: FP64 and mixed)")
     return ap.parse_args(argv)
@@ -298,6 +301,105 @@ def run_batched(args, rhd, torch, rank, ws, dist, barrier):
                         "c=1e3, chat=100 (seed 11)"}
 
 
+def run_adjoint(args, rhd, torch, rank, ws, dist, barrier):
+    """Differentiation workload: a radiation pulse through a log-normal opacity
+    field on a periodic 512^2 grid, L = sum (E(200) - E_tgt)^2, gradient with
+    respect to the initial temperature and log opacity by the hand-written
+    adjoint with checkpoints every 20 steps (FP64)."""
+    from paper_2404_08247_gb300 import adjoint as A
+    from paper_2404_08247_gb300 import inputs as I
+    prob, T0, lk, Et, nsteps = I.pulse_inverse_problem_2d(args.adj_n, seed_chi=7 + 100 * rank)
+    every = 20
+    N = T0.size
+    cv = prob["kB_over_mu"] / (prob["gamma"] - 1.0)
+    a = prob["a_rad"]
+    stream = torch.cuda.current_stream()
+    ctx = rhd.RHDContext(prob, stream=stream)
+    ctx.set_state(I.rest_state(prob, T0, lk))
+    Tt = torch.from_numpy(T0.reshape(-1).copy()).cuda()
+    lkt = torch.from_numpy(lk.reshape(-1).copy()).cuda()
+    Ett = torch.from_numpy(Et.reshape(-1).copy()).cuda()
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # forward steps alone (the cost unit of the ratio)
+    U0 = torch.from_numpy(I.rest_state(prob, T0, lk)).cuda()
+    ctx.set_state(U0)
+    ctx.step(3)
+    ctx.set_state(U0)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = events()
+    e0.record(stream)
+    ctx.step(nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = reduce_max(e0.elapsed_time(e1), dist, "cuda") / nsteps
+
+    def grad_pass():
+        T = Tt.clone().requires_grad_(True)
+        logk = lkt.clone().requires_grad_(True)
+        z = torch.zeros_like(T)
+        y0 = torch.stack([cv * T, z, z, z, a * T ** 4, z, z, z])
+        ea, eb = events()
+        y = A.trajectory(ctx, y0, torch.exp(logk), nsteps, 0.0, every)
+        loss = ((y[4] - Ett) ** 2).sum()
+        ea.record(stream)
+        loss.backward()
+        eb.record(stream)
+        torch.cuda.synchronize()
+        return ea.elapsed_time(eb), float(loss.detach()), T.grad, logk.grad
+
+    grad_pass()  # warm-up (allocates the adjoint scratch)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = events()
+    e0.record(stream)
+    bwd_ms_total, loss, gT, glk = grad_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    bwd_ms = reduce_max(bwd_ms_total, dist, "cuda") / nsteps
+
+    # the two parts of the backward: re-run with recording, then the adjoint
+    tape = torch.empty((2 * every + 1) * 8 * N, dtype=torch.float64, device="cuda")
+    ybar = torch.zeros(8 * N, dtype=torch.float64, device="cuda")
+    kbar = torch.zeros(N, dtype=torch.float64, device="cuda")
+    ctx.set_state(U0)
+    e0, e1 = events()
+    e0.record(stream)
+    ctx.step_record(every, 0.0, tape)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rec_ms = e0.elapsed_time(e1) / every
+    ybar[4 * N:5 * N] = 1.0
+    e0, e1 = events()
+    e0.record(stream)
+    ctx.adjoint(tape, every, 0.0, ybar, kbar)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1) / every
+    launches = ctx.launch_count()
+    ctx.close()
+    return {
+        "value": whole_job_rate(N, nsteps, ws, bwd_ms * nsteps * 1e-3), "unit": UNIT,
+        "what": "backward cell-updates/s (re-run with recording + adjoint)",
+        "fwd_ms_per_step": fwd_ms, "bwd_ms_per_step": bwd_ms,
+        "fwd_plus_bwd_ms_per_step": total_ms / nsteps,
+        "record_ms_per_step": rec_ms, "adjoint_kernels_ms_per_step": adj_ms,
+        "ratio_bwd_over_fwd": bwd_ms / fwd_ms,
+        "ratio_adjoint_kernels_over_fwd": adj_ms / fwd_ms,
+        "steps": nsteps, "checkpoint_every": every, "cells": int(N), "precision": "fp64",
+        "loss": loss, "grad_T_norm": float(gT.norm()), "grad_logk_norm": float(glk.norm()),
+        "launches_total": int(launches),
+        "workload": "%d^2 periodic, rho=1, gas at rest, ln chi k^-4 GRF sigma=1 median "
+                    "tau_cell=1 (seed 7), T=(1+9exp(-r^2/(2*0.05^2)))(1+0.2u), u iid U[-1,1] (seed 9), "
+                    "c=chat=1e3, "
+                    "L=sum(E_200-E_tgt)^2" % args.adj_n,
+    }
+
+
 def run_ours(args):
     import torch
     from paper_2404_08247_gb300 import rhd
@@ -385,6 +487,10 @@ def run_ours(args):
     if not args.no_batched:
         batched = run_batched(args, rhd, torch, rank, ws, dist, barrier)
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(args, rhd, torch, rank, ws, dist, barrier)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -417,6 +523,7 @@ def run_ours(args):
             "gpu_launches": int(head["launches"]), "clocks": head["clocks"],
             "forms": form_lines,
             "batched": batched,
+            "adjoint": adjoint,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -204,6 +204,37 @@ rhd_status rhd_totals(rhd_ctx* ctx, double out[4]);
 rhd_status rhd_profile(rhd_ctx* ctx, int enable);
 rhd_status rhd_profile_read(rhd_ctx* ctx, int64_t launches[3], double ms[3]);
 
+/* ---- Differentiation: reverse mode through whole steps ----
+ * The paper has no adjoint; this derivative of the step it defines serves
+ * gradient-based inversion (e.g. of initial temperatures or opacities).
+ * A recorded state is 8 slots of ncell doubles (Egas, mx, my, mz, E, Fx, Fy,
+ * Fz: the evolved fields in rhd_field order), one slot after another. */
+
+/* Advance nsteps like rhd_step (dt <= 0: rhd_default_dt) and record the tape
+ * the adjoint needs.  tape: device buffer owned by the caller, count =
+ * (2*nsteps + 1) * 8 * ncell doubles, written as y(0), y(1/2), y(1), y(3/2),
+ * ..., y(nsteps): every step's start state and its stage-1 state y(n+1/2) of
+ * eq. (imex1).  The stage kernels write the tape directly; the context's
+ * state becomes y(nsteps) on success and stays at y(0) on failure (info as
+ * rhd_step's, nullable).  Synchronises. */
+rhd_status rhd_step_record(rhd_ctx* ctx, int nsteps, double dt, double* tape,
+                           int64_t count, rhd_step_info* info);
+
+/* Reverse-mode derivative of nsteps recorded steps.  tape, count, nsteps and
+ * dt as given to rhd_step_record (the same dt; <= 0: rhd_default_dt); the
+ * context's rho and kappa must be those the steps ran with.  ybar: device
+ * buffer of 8*ncell doubles (slots as in the tape) holding dL/dy(nsteps) on
+ * entry and dL/dy(0) on return.  kappa_bar: device buffer of ncell doubles
+ * to which dL/dkappa is added.  Both caller-owned.  The transport part is
+ * the transpose of the PLM/HLL fluxes (Sec. 3.3, Sec. 4.3) on the active
+ * branch of every limiter, maximum and clip; the implicit part applies the
+ * implicit-function theorem to the converged local solve of eq.
+ * (egupdate)-(fupdate).  The first call allocates 8*ncell + 18*(faces)
+ * doubles of scratch that the context keeps.  Returns RHD_ERR_NEWTON if the
+ * Jacobian of a converged solve is singular.  Synchronises. */
+rhd_status rhd_adjoint(rhd_ctx* ctx, const double* tape, int64_t count, int nsteps,
+                       double dt, double* ybar, double* kappa_bar);
+
 /* Number of kernels this context has launched since rhd_init. */
 int64_t rhd_launch_count(const rhd_ctx* ctx);
 

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <vector>
 
+#include "rhd_adjoint.cuh"
 #include "rhd_internal.cuh"
 
 using namespace rhd;
@@ -63,6 +64,8 @@ struct rhd_ctx {
   bool prof = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  double* adj_q = nullptr;   // adjoint scratch, allocated by the first rhd_adjoint
+  double* adj_fp = nullptr;
 };
 
 static rhd_status fail(rhd_ctx* c, rhd_status s, const char* fmt, ...) {
@@ -259,6 +262,8 @@ static void release(rhd_ctx* c) {
   cudaFree(c->d_partials);
   cudaFree(c->d_tot);
   cudaFree(c->d_flag);
+  cudaFree(c->adj_q);
+  cudaFree(c->adj_fp);
   cudaFreeHost(c->h_status);
   cudaFreeHost(c->h_tot);
   cudaFreeHost(c->h_flag);
@@ -670,6 +675,152 @@ rhd_status rhd_profile_read(rhd_ctx* c, int64_t launches[3], double ms[3]) {
     launches[r.kind] += 1;
     ms[r.kind] += (double)t;
   }
+  return RHD_OK;
+}
+
+// ------------------------------------------------------------ differentiation
+
+static void fill_info_status(rhd_ctx* c, const DevStatus& st, int n, double dt,
+                             rhd_step_info* info, rhd_status code, int done, int64_t cell) {
+  if (!info) return;
+  info->status = code;
+  info->steps_done = done;
+  info->fail_cell = cell;
+  info->fail_step = code == RHD_OK ? -1 : st.fail_step;
+  info->fail_stage = code == RHD_OK ? 0 : st.fail_stage;
+  info->max_newton = st.max_newton;
+  info->max_outer = st.max_outer;
+  info->sum_newton = (int64_t)st.sum_newton;
+  info->n_solves = (int64_t)st.n_solves;
+  info->sum_outer = (int64_t)st.sum_outer;
+  info->t = c->t;
+  info->dt = dt;
+  (void)n;
+}
+
+rhd_status rhd_step_record(rhd_ctx* c, int nsteps, double dt, double* tape, int64_t count,
+                           rhd_step_info* info) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->fail_cell = -1;
+    info->fail_step = -1;
+  }
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
+  if (!tape) return fail(c, RHD_ERR_ARG, "tape is NULL");
+  const size_t N = (size_t)c->ncell;
+  const size_t S = NY * N;  // doubles per recorded state
+  if (count != (int64_t)((2 * (size_t)nsteps + 1) * S))
+    return fail(c, RHD_ERR_ARG, "tape count must be (2*nsteps+1)*8*ncell");
+  if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
+  if (!std::isfinite(dt)) return fail(c, RHD_ERR_ARG, "dt is not finite");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+  c->launches += 1;
+  if (c->p.hll_mode == RHD_HLL_TAU && c->eps_dirty) {
+    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->eps, c->stream));
+    c->launches += 1;
+    c->eps_dirty = false;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(tape, c->ybuf[c->cur], sizeof(double) * S,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  StageArgs A;
+  A.cell_base = 0;
+  for (int d = 0; d < 3; ++d) A.eps[d] = c->eps[d];
+  A.g = c->g;
+  A.ph = c->ph;
+  A.dt = dt;
+  A.rho = c->rho;
+  A.kappa = c->kappa;
+  A.st = c->d_status;
+  const int n = c->ncell;
+  for (int s = 0; s < nsteps; ++s) {
+    double* yn = tape + (size_t)(2 * s) * S;
+    double* yh = yn + S;
+    double* y1 = yh + S;
+    A.step = s;
+    slots_of<const double*>(A.yt, yn, n);
+    slots_of<const double*>(A.yn, yn, n);
+    slots_of<double*>(A.yo, yh, n);
+    CUDA_TRY(c, launch_recorded(c, 0, 1, A));
+    slots_of<const double*>(A.yt, yh, n);
+    slots_of<double*>(A.yo, y1, n);
+    CUDA_TRY(c, launch_recorded(c, 1, 2, A));
+    c->launches += 2;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const DevStatus& st = *c->h_status;
+  if (st.fail_key != ~0ull) {
+    rhd_status code = (rhd_status)(st.fail_key & 0xffull);
+    int64_t cell = (int64_t)(st.fail_key >> 8);
+    fill_info_status(c, st, nsteps, dt, info, code, st.fail_step, cell);
+    return fail(c, code, "recorded step %d stage %d failed at cell %lld (status %d)",
+                st.fail_step, st.fail_stage, (long long)cell, (int)code);
+  }
+  // the context continues from y(nsteps)
+  CUDA_TRY(c, cudaMemcpyAsync(c->ybuf[c->cur], tape + (size_t)(2 * nsteps) * S,
+                              sizeof(double) * S, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->t += nsteps * dt;
+  fill_info_status(c, st, nsteps, dt, info, RHD_OK, nsteps, -1);
+  return RHD_OK;
+}
+
+rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps, double dt,
+                       double* ybar, double* kappa_bar) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if ((c->fields_set & ((1u << RHD_F_RHO) | (1u << RHD_F_KAPPA))) !=
+      ((1u << RHD_F_RHO) | (1u << RHD_F_KAPPA)))
+    return fail(c, RHD_ERR_STATE, "rho and kappa must be set");
+  if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
+  if (!tape || !ybar || !kappa_bar) return fail(c, RHD_ERR_ARG, "a buffer is NULL");
+  const size_t N = (size_t)c->ncell;
+  const size_t S = NY * N;
+  if (count != (int64_t)((2 * (size_t)nsteps + 1) * S))
+    return fail(c, RHD_ERR_ARG, "tape count must be (2*nsteps+1)*8*ncell");
+  if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
+  if (!std::isfinite(dt)) return fail(c, RHD_ERR_ARG, "dt is not finite");
+  if (nsteps == 0) return RHD_OK;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (!c->adj_q) {
+    CUDA_TRY(c, cudaMalloc(&c->adj_q, sizeof(double) * S));
+    CUDA_TRY(c, cudaMalloc(&c->adj_fp, sizeof(double) * adjoint_scratch_doubles(c->g)));
+  }
+  CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+  AdjointStep A;
+  A.g = c->g;
+  A.ph = c->ph;
+  A.dt = dt;
+  A.rho = c->rho;
+  A.kappa = c->kappa;
+  A.ybar = ybar;
+  A.q = c->adj_q;
+  A.fp = c->adj_fp;
+  A.kbar = kappa_bar;
+  A.st = c->d_status;
+  for (int k = nsteps - 1; k >= 0; --k) {
+    A.step = k;
+    A.yn = tape + (size_t)(2 * k) * S;
+    A.yh = A.yn + S;
+    A.y1 = A.yh + S;
+    A.pending_fp = k < nsteps - 1;
+    CUDA_TRY(c, launch_adjoint_step(A, c->stream));
+  }
+  CUDA_TRY(c, launch_adjoint_finish(A, c->stream));
+  c->launches += 1 + 4 * (int64_t)nsteps + 1;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->h_status->fail_key != ~0ull)
+    return fail(c, RHD_ERR_NEWTON,
+                "adjoint step %d: singular local-solve Jacobian at cell %lld",
+                c->h_status->fail_step, (long long)(c->h_status->fail_key >> 8));
   return RHD_OK;
 }
 

@@ -114,6 +114,9 @@ SIGNATURES = {
     "rhd_time": (ctypes.c_double, [_V]),
     "rhd_last_error": (ctypes.c_char_p, [_V]),
     "rhd_destroy": (None, [_V]),
+    "rhd_step_record": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double, _V, _I64,
+                                       ctypes.POINTER(rhd_step_info)]),
+    "rhd_adjoint": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int, ctypes.c_double, _V, _V]),
     "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
                                         ctypes.POINTER(rhd_step_info)]),
     "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
@@ -339,6 +342,31 @@ class RHDContext:
         ms = (ctypes.c_double * 3)()
         _check(self.lib.rhd_profile_read(self.h, launches, ms), self.h)
         return list(launches), list(ms)
+
+    def step_record(self, nsteps: int, dt: float, tape) -> dict:
+        """rhd_step_record: nsteps steps that also write the tape (a device
+        tensor of (2*nsteps+1)*8*ncell float64)."""
+        ptr, dev = _ptr(tape)
+        if not dev:
+            raise ValueError("the tape must be a device tensor")
+        info = rhd_step_info()
+        _check(self.lib.rhd_step_record(self.h, int(nsteps), float(dt), ctypes.c_void_p(ptr),
+                                        int(tape.numel()), ctypes.byref(info)), self.h)
+        return info.as_dict()
+
+    def adjoint(self, tape, nsteps: int, dt: float, ybar, kappa_bar):
+        """rhd_adjoint: ybar (device, 8*ncell) from dL/dy(nsteps) to dL/dy(0) in
+        place; dL/dkappa added to kappa_bar (device, ncell)."""
+        tp, td = _ptr(tape)
+        yp, yd = _ptr(ybar)
+        kp, kd = _ptr(kappa_bar)
+        if not (td and yd and kd):
+            raise ValueError("tape, ybar and kappa_bar must be device tensors")
+        if ybar.numel() != 8 * self.ncell or kappa_bar.numel() != self.ncell:
+            raise ValueError("ybar must hold 8*ncell and kappa_bar ncell values")
+        _check(self.lib.rhd_adjoint(self.h, ctypes.c_void_p(tp), int(tape.numel()),
+                                    int(nsteps), float(dt), ctypes.c_void_p(yp),
+                                    ctypes.c_void_p(kp)), self.h)
 
     def launch_count(self) -> int:
         return int(self.lib.rhd_launch_count(self.h))
