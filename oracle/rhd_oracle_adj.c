@@ -196,9 +196,21 @@ static int face_vjp(const orc_params* p, int d, const double* cell[4], double ep
   return ORC_OK;
 }
 
-/* d/dtau of the optical-depth factor (1 - exp(-tau))/tau */
+/* d/dtau of the optical-depth factor (1 - exp(-tau))/tau,
+ * (tau exp(-tau) - (1 - exp(-tau)))/tau^2.  For small tau the two terms of
+ * the numerator cancel; there the Taylor series of the derivative,
+ * sum over k >= 1 of (-1)^k k tau^(k-1) / (k+1)!, is summed to k = 8. */
 static double tau_factor_d(double tau) {
-  if (tau < 1e-4) return -0.5 + tau / 3.0 - tau * tau / 8.0;
+  if (tau < 0.05) {
+    double s = 0.0, term_fact = 2.0; /* (k+1)! */
+    double tpow = 1.0;               /* tau^(k-1) */
+    for (int k = 1; k <= 8; ++k) {
+      s += ((k & 1) ? -1.0 : 1.0) * k * tpow / term_fact;
+      tpow *= tau;
+      term_fact *= (double)(k + 2);
+    }
+    return s;
+  }
   double e = exp(-tau);
   return (tau * e + expm1(-tau)) / (tau * tau);
 }

@@ -7,9 +7,9 @@ derivative of the local solve's energy quartic.
 
 Finite differences use per-cell relative perturbations.  The step is only
 piecewise smooth (the slope limiter, the max in the HLL speed and the flux
-rescale have kinks), so a difference step that straddles a kink is off by the
-jump; the steps used here are small enough that the seeded cases straddle
-none.
+rescale have kinks), so a difference step that straddles a kink is off by a
+term proportional to the step; single steps use a step small enough that the
+seeded cases straddle none, trajectories the best of a short ladder.
 """
 import numpy as np
 import pytest
@@ -267,3 +267,33 @@ def test_trajectory_gradient_matches_central_differences(oracle_mod):
                       loss(T0 - h * vec_T, lk - h * vec_k)) / (2 * h)
                 errs.append(abs(lin - fd) / abs(fd))
             assert min(errs) <= 1e-6, errs
+
+
+
+@pytest.mark.parametrize("tau_cell", [1e-4, 1e-3, 0.03, 0.049, 0.051, 0.3])
+def test_opacity_gradient_across_the_tau_series_switch(oracle_mod, tau_cell):
+    """TAU mode with optical depths on both sides of the switch between the
+    series and the closed form of d eps/d tau (R18): dL/dkappa of one step
+    equals central differences in kappa, cell by cell."""
+    O = oracle_mod
+    n = 12
+    prob = I.base_problem(1, (n,), (1.0 / n,), c=1e3, chat=1e3, hll_mode="tau")
+    U = I.random_state(prob, seed=31, tau_range=(tau_cell, tau_cell * 1.0001))
+    dt = O.dt(prob)
+    tape = O.step_tape(prob, U.copy(), dt)
+    rng = np.random.default_rng(5)
+    W = np.zeros_like(tape[2])
+    W[4] = rng.standard_normal(W[4].shape) / np.abs(U[I.F_ERAD]).max()
+    kbar = np.zeros_like(U[0])
+    O.step_adjoint(prob, U[I.F_RHO], U[I.F_KAPPA], tape, W, kbar, dt)
+    for i in range(0, n, 3):
+        h = 1e-4 * U[I.F_KAPPA].flat[i]  # smooth in kappa; larger step, less rounding
+        vals = []
+        for sgn in (1.0, -1.0):
+            V = U.copy()
+            V[I.F_KAPPA].flat[i] += sgn * h
+            O.step(prob, V, 1, dt)
+            vals.append((W[4] * V[I.F_ERAD]).sum())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(kbar.flat[i] - fd) <= 1e-6 * abs(fd) + 1e-12 * np.abs(kbar).max(), \
+            (i, kbar.flat[i], fd)
