@@ -297,6 +297,15 @@ rhd_status rhd_batch_locate(const rhd_batch* b, int64_t pooled_cell, int* prob,
 const char* rhd_batch_last_error(const rhd_batch* b);
 void rhd_batch_destroy(rhd_batch* b);
 
+/* Diagnostic: the reciprocal and reciprocal square root that the FP64
+ * kernels use in place of IEEE division and square root (Newton-Raphson
+ * steps from a single-precision seed), for n positive values.  x, rcp and
+ * rsqrt are device buffers of n doubles owned by the caller; results go to
+ * rcp[i] = 1/x[i] and rsqrt[i] = 1/sqrt(x[i]).  Lets tests bound their error
+ * against IEEE results.  Runs on the legacy default stream and synchronises
+ * the device.  Messages: rhd_last_error(NULL). */
+rhd_status rhd_eval_recip(const double* x, int64_t n, double* rcp, double* rsqrt);
+
 /* Largest grid, in cells, that rhd_step_noalloc accepts. */
 #define RHD_NOALLOC_MAX_CELLS 262144
 

@@ -77,6 +77,67 @@ inline void slots_of(P* out, P base, int n) {
   for (int q = 0; q < NY; ++q) out[q] = base + (size_t)q * n;
 }
 
+// ------------------------------------------------- FP64 off the FP64 pipe
+// On this GPU the FP64 pipe, which limits the FP64 step, also executes double
+// compares, minima and conversions (about one FMA slot each), and division
+// and square root take about ten.  The helpers below give the same answers
+// with the integer pipe doing what it can:
+//  * non-negative, non-NaN doubles order like their IEEE bit patterns as
+//    signed 64-bit integers, so their compares and minima are integer ops;
+//  * rcp_pos / rsqrt_pos: 1/x and 1/sqrt(x) for x > 0 by Newton-Raphson
+//    iteration (r <- r + r (1 - x r); y <- y + y (1/2 - x y^2 / 2), each step
+//    doubling the correct bits; e.g. P. Markstein, IBM J. Res. Dev. 34 (1990))
+//    from a single-precision seed whose exponent is rebiased with integer
+//    arithmetic: two steps from a 2^-22 seed leave ~1 ulp (the IEEE operation
+//    is used outside the single-precision exponent range).
+constexpr long long kMag = 0x7fffffffffffffffll;
+constexpr long long kInfBits = 0x7ff0000000000000ll;
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > 0 and finite (false for NaN)
+__device__ __forceinline__ bool pos_finite(double x) {
+  long long b = dbits(x);
+  return b > 0 && b < kInfBits;
+}
+__device__ __forceinline__ bool finite_bits(double x) { return (dbits(x) & kMag) < kInfBits; }
+// |x|, and a < b / a <= b / max(a, b) for a, b >= 0 (not NaN)
+__device__ __forceinline__ long long abs_bits(double x) { return dbits(x) & kMag; }
+__device__ __forceinline__ bool lt_nn(double a, double b) { return dbits(a) < dbits(b); }
+__device__ __forceinline__ bool le_nn(double a, double b) { return dbits(a) <= dbits(b); }
+__device__ __forceinline__ double max_nn(double a, double b) {
+  return __longlong_as_double(max(dbits(a), dbits(b)));
+}
+
+__device__ __forceinline__ bool seed_range(double x) {
+  int e = (int)(dbits(x) >> 52);  // biased exponent of x > 0
+  return e > 1023 - 120 && e < 1023 + 120;
+}
+// x as a float with the mantissa truncated (x > 0 within seed_range)
+__device__ __forceinline__ float seed_float(double x) {
+  return __int_as_float((int)((dbits(x) >> 29) - (896ll << 23)));
+}
+// a positive normal float widened exactly
+__device__ __forceinline__ double seed_double(float f) {
+  return __longlong_as_double(((long long)__float_as_int(f) + (896ll << 23)) << 29);
+}
+__device__ __forceinline__ double rcp_pos(double x) {
+  if (!seed_range(x)) return 1.0 / x;
+  double r = seed_double(__fdividef(1.0f, seed_float(x)));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt_pos(double x) {
+  if (!seed_range(x)) return 1.0 / sqrt(x);
+  double y = seed_double(rsqrtf(seed_float(x)));
+  double h = 0.5 * x;
+  double e = fma(-h * y, y, 0.5);
+  y = fma(y, e, y);
+  e = fma(-h * y, y, 0.5);
+  return fma(y, e, y);
+}
+
 // ---------------------------------------------------------------- limiter
 // Half of the PLM slope with the monotonised-central limiter:
 // (1/2) minmod(2 d-, (d- + d+)/2, 2 d+) = sgn * min(|d-|, |d+|, |d- + d+|/4),
@@ -87,6 +148,20 @@ __device__ __forceinline__ R half_slope(R um, R u0, R up) {
   R dp = up - u0;
   R m = fmin(fmin(fabs(dm), fabs(dp)), R(0.25) * fabs(dm + dp));
   return (dm > R(0) && dp > R(0)) ? m : ((dm < R(0) && dp < R(0)) ? -m : R(0));
+}
+
+// double: the same value with the sign tests and the minimum on the integer
+// pipe (0.25 |d- + d+| = |0.25 (d- + d+)| exactly)
+template <>
+__device__ __forceinline__ double half_slope<double>(double um, double u0, double up) {
+  double dm = u0 - um;
+  double dp = up - u0;
+  double q = 0.25 * (dm + dp);
+  long long bm = dbits(dm), bp = dbits(dp);
+  long long am = bm & kMag, ap = bp & kMag;
+  long long m = min(min(am, ap), abs_bits(q));
+  bool take = ((bm ^ bp) >= 0) & (am != 0) & (ap != 0);  // same sign, both nonzero
+  return __longlong_as_double(take ? (m | (bm & ~kMag)) : 0ll);
 }
 
 // ---------------------------------------------------------------- closure
@@ -110,6 +185,22 @@ __device__ __forceinline__ void m1_coeffs(R E, const R Ft[3], R& ha, R& hb) {
     R s = sqrt(R(4) * E2 - R(3) * F2);
     ha = (s - E) * (R(1) / R(3));
     hb = R(3) / (R(2) * E + s);
+  }
+}
+
+template <>
+__device__ __forceinline__ void m1_coeffs<double>(double E, const double Ft[3], double& ha,
+                                                  double& hb) {
+  double F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
+  double E2 = E * E;
+  if (lt_nn(E2, F2)) {
+    ha = 0.0;
+    hb = E * rcp_pos(F2);
+  } else {
+    double x = 4.0 * E2 - 3.0 * F2;
+    double s = x * rsqrt_pos(x);
+    ha = (s - E) * (1.0 / 3.0);
+    hb = 3.0 * rcp_pos(2.0 * E + s);
   }
 }
 
@@ -137,33 +228,52 @@ __device__ __forceinline__ void m1_row(int d, R E, const R Ft[3], int closure, R
 //   Phi = (Phi_L + Phi_R)/2 - S (U_R - U_L)/2,
 // with the optical-depth factor eps on the energy part (1 for HLL NONE).
 // Returns false for a face state with E <= 0 (or NaN).
+// a > 0 and a < b for a, b >= 0 in the transport precision (integer pipe for
+// double, plain compares for float)
+template <typename R>
+__device__ __forceinline__ bool positive(R a) {
+  if constexpr (sizeof(R) == 8) return dbits(a) > 0 && dbits(a) < kInfBits;
+  else return a > R(0);
+}
+template <typename R>
+__device__ __forceinline__ bool less_nn(R a, R b) {
+  if constexpr (sizeof(R) == 8) return lt_nn(a, b);
+  else return a < b;
+}
+
 template <typename R>
 __device__ __forceinline__ bool hll_states(int d, R L[4], R Rr[4], R eps, R chat,
                                            int closure, R out[4]) {
-  if (!(L[0] > R(0)) || !(Rr[0] > R(0))) {
+  if (!positive(L[0]) || !positive(Rr[0])) {
     out[0] = out[1] = out[2] = out[3] = R(0);
     return false;
   }
   {
     R n2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
-    if (n2 > L[0] * L[0]) {
-      R sc = L[0] / sqrt(n2);
+    if (less_nn(L[0] * L[0], n2)) {
+      R sc;
+      if constexpr (sizeof(R) == 8) sc = L[0] * rsqrt_pos(n2);
+      else sc = L[0] / sqrt(n2);
       L[1] *= sc; L[2] *= sc; L[3] *= sc;
     }
     n2 = Rr[1] * Rr[1] + Rr[2] * Rr[2] + Rr[3] * Rr[3];
-    if (n2 > Rr[0] * Rr[0]) {
-      R sc = Rr[0] / sqrt(n2);
+    if (less_nn(Rr[0] * Rr[0], n2)) {
+      R sc;
+      if constexpr (sizeof(R) == 8) sc = Rr[0] * rsqrt_pos(n2);
+      else sc = Rr[0] / sqrt(n2);
       Rr[1] *= sc; Rr[2] *= sc; Rr[3] *= sc;
     }
   }
   R PL[3], PR[3];
   m1_row(d, L[0], &L[1], closure, PL);
   m1_row(d, Rr[0], &Rr[1], closure, PR);
-  // largest of D_dd,L, D_dd,R and 1/3 without dividing each
+  // largest of D_dd,L, D_dd,R and 1/3 without dividing each (P_dd >= 0)
   R num = PL[d], den = L[0];
-  if (PR[d] * L[0] > PL[d] * Rr[0]) { num = PR[d]; den = Rr[0]; }
-  if (R(3) * num < den) { num = R(1); den = R(3); }
-  R S = chat * sqrt(num / den);
+  if (less_nn(PL[d] * Rr[0], PR[d] * L[0])) { num = PR[d]; den = Rr[0]; }
+  if (less_nn(R(3) * num, den)) { num = R(1); den = R(3); }
+  R S;
+  if constexpr (sizeof(R) == 8) S = chat * num * rsqrt_pos(num * den);  // sqrt(num/den)
+  else S = chat * sqrt(num / den);
   R hc = R(0.5) * chat;
   R hS = R(0.5) * S;
   out[0] = hc * (L[1 + d] + Rr[1 + d]) - eps * hS * (Rr[0] - L[0]);
@@ -237,8 +347,8 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
   no = 0;
   if (chi == 0.0) return RHD_OK;
   const double Cv = rho * ph.cv_spec;
-  const double inv_Cv = 1.0 / Cv;
-  const double inv_rho = 1.0 / rho;
+  const double inv_Cv = rcp_pos(Cv);
+  const double inv_rho = rcp_pos(rho);
   const double cr = ph.c_over_chat;
   const double a = ph.a_rad;
   const double Eg0 = y[0], E0 = y[4];
@@ -259,13 +369,13 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
 
   {
     double T0 = (Eg0 - Ekin) * inv_Cv;
-    if (T0 > 0.0) {
+    if (pos_finite(T0)) {
       double kg = k * g;
-      double inv1 = 1.0 / (1.0 + kg);
+      double inv1 = rcp_pos(1.0 + kg);
       double a4 = cr * kg * a * inv1 * inv_Cv;
       double rhs = T0 + cr * k * (g * E0 - w) * inv1 * inv_Cv;
       double Tg;
-      if (rhs > 0.0 && quartic_start(a4, rhs, T0, Tg)) {
+      if (pos_finite(rhs) && quartic_start(a4, rhs, T0, Tg)) {
         Eg = Cv * Tg + Ekin;
         R = -ph.chat_over_c * (Eg - Eg0);
       }
@@ -276,24 +386,27 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
     no = outer + 1;
     const double kg = k * g;
     const double kw = k * w;
+    const double c4 = 4.0 * kg * a * inv_Cv;  // J10 / T^3
+    const double gpk = g * (1.0 + k);
+    const double tolRg = tolR * g;
 
     bool conv = false;
+    double aT4 = 0.0;
     for (int it = 0;; ++it) {
       double T = (Eg - Ekin) * inv_Cv;
-      if (!(T > 0.0) || !isfinite(T) || !isfinite(R)) return RHD_ERR_NONPHYSICAL;
+      if (!pos_finite(T) || !finite_bits(R)) return RHD_ERR_NONPHYSICAL;
       double T2 = T * T;
-      double aT4 = a * T2 * T2;
+      aT4 = a * T2 * T2;
       double r0 = (Eg - Eg0) + cr * R;
       double r1 = kg * (aT4 - E0 - R) + (kw - R);
-      if (fabs(r0) < tolG && cr * fabs(r1) <= tolR * g) {
+      if (lt_nn(fabs(r0), tolG) && le_nn(cr * fabs(r1), tolRg)) {
         conv = true;
         break;
       }
       if (it >= ph.newton_max) break;
-      double J10 = 4.0 * kg * a * T2 * T * inv_Cv;
-      double gpk = g * (1.0 + k);
-      double det = -gpk - cr * J10;
-      double inv_det = MIXED ? (double)(1.0f / (float)det) : 1.0 / det;
+      double J10 = c4 * T2 * T;
+      double det = -gpk - cr * J10;  // < 0
+      double inv_det = MIXED ? (double)(1.0f / (float)det) : -rcp_pos(-det);
       double dEg = (r0 * gpk + cr * r1) * inv_det;
       double dR = (r0 * J10 - r1) * inv_det;
       Eg += dEg;
@@ -302,10 +415,8 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
     }
     if (!conv) return RHD_ERR_NEWTON;
 
+    // energy closure; aT4 is that of the converged Egas
     E = E0 - ph.chat_over_c * (Eg - Eg0);
-    double T = (Eg - Ekin) * inv_Cv;
-    double T2 = T * T;
-    double aT4 = a * T2 * T2;
 
     // v_j P_ji of the closure at (E, F): P = ha I + hb Ft Ft^T
     double vP[3];
@@ -322,7 +433,7 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
         for (int i = 0; i < 3; ++i) vP[i] = ha * v[i] + t * Ft[i];
       }
     }
-    double inv_den = 1.0 / (1.0 + kg);
+    double inv_den = rcp_pos(1.0 + kg);
     double Fn[3], mn[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -349,15 +460,15 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
     g = gn;
     w = wn;
     Ekin = 0.5 * (m[0] * v[0] + m[1] * v[1] + m[2] * v[2]);
+    // |dQ| <= rtol max(|Q_old|, |R|, Q_scale): the three tests of the outer stop
     double dQ = fabs(Q_new - Q_old);
-    if (dQ <= ph.outer_rtol * fabs(Q_old) || dQ <= ph.outer_rtol * fabs(R) ||
-        dQ <= ph.outer_rtol * Q_scale) {
+    double big = max_nn(max_nn(fabs(Q_old), fabs(R)), Q_scale);
+    if (le_nn(dQ, ph.outer_rtol * big)) {
       y[0] = Eg;
       y[1] = m[0]; y[2] = m[1]; y[3] = m[2];
       y[4] = E;
       y[5] = F[0]; y[6] = F[1]; y[7] = F[2];
-      if (!(E > 0.0) || !isfinite(E) || !isfinite(F[0]) || !isfinite(F[1]) ||
-          !isfinite(F[2]))
+      if (!pos_finite(E) || !finite_bits(F[0]) || !finite_bits(F[1]) || !finite_bits(F[2]))
         return RHD_ERR_NONPHYSICAL;
       return RHD_OK;
     }

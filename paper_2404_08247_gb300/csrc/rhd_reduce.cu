@@ -111,3 +111,31 @@ cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
 }
 
 }  // namespace rhd
+
+// ---------------------------------------------------------------- diagnostic
+namespace {
+__global__ void eval_recip_kernel(const double* __restrict__ x, long long n,
+                                  double* __restrict__ r, double* __restrict__ q) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = x[i];
+  r[i] = rhd::rcp_pos(v);
+  q[i] = rhd::rsqrt_pos(v);
+}
+}  // namespace
+
+extern "C" rhd_status rhd_eval_recip(const double* x, int64_t n, double* rcp, double* rsqrt) {
+  if (n < 0 || (n > 0 && (!x || !rcp || !rsqrt))) {
+    rhd::set_global_error("rhd_eval_recip: bad arguments");
+    return RHD_ERR_ARG;
+  }
+  if (n == 0) return RHD_OK;
+  eval_recip_kernel<<<(unsigned)((n + 255) / 256), 256>>>(x, (long long)n, rcp, rsqrt);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    rhd::set_global_error(cudaGetErrorString(e));
+    return RHD_ERR_CUDA;
+  }
+  return RHD_OK;
+}

@@ -117,6 +117,7 @@ SIGNATURES = {
     "rhd_step_record": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double, _V, _I64,
                                        ctypes.POINTER(rhd_step_info)]),
     "rhd_adjoint": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int, ctypes.c_double, _V, _V]),
+    "rhd_eval_recip": (ctypes.c_int, [_V, _I64, _V, _V]),
     "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
                                         ctypes.POINTER(rhd_step_info)]),
     "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
@@ -219,6 +220,20 @@ def _ptr(x):
     if str(x.dtype) != "torch.float64" or not x.is_contiguous():
         raise ValueError("expected a contiguous float64 tensor")
     return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+def eval_recip(x):
+    """rhd_eval_recip on a float64 CUDA tensor: (1/x, 1/sqrt(x)) as computed by
+    the FP64 kernels."""
+    import torch
+    if not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    r = torch.empty_like(x)
+    q = torch.empty_like(x)
+    torch.cuda.synchronize()
+    _check(load().rhd_eval_recip(ctypes.c_void_p(x.data_ptr()), int(x.numel()),
+                                 ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(q.data_ptr())))
+    return r, q
 
 
 class RHDContext:
