@@ -45,15 +45,17 @@ __device__ __forceinline__ long long face_index(const Geometry& g, int d, int x,
 }
 
 // Half PLM slope (monotonised-central limiter) and its gradient with respect to
-// (u_-, u_0, u_+) on the active branch; zero at an extremum.
+// (u_-, u_0, u_+) on the active branch; zero at an extremum.  Signs and the
+// minimum are taken on the integer pipe, as in the forward half_slope.
 __device__ __forceinline__ double half_slope_vjp(double um, double u0, double up, double& gm,
                                                  double& g0, double& gp) {
   double dm = u0 - um, dp = up - u0;
+  double q = 0.25 * (dm + dp);
+  long long bm = dbits(dm), bp = dbits(dp);
+  long long am = bm & kMag, ap = bp & kMag, aq = abs_bits(q);
   gm = g0 = gp = 0.0;
-  bool pos = dm > 0.0 && dp > 0.0, neg = dm < 0.0 && dp < 0.0;
-  if (!pos && !neg) return 0.0;
-  double am = fabs(dm), ap = fabs(dp), aq = 0.25 * fabs(dm + dp);
-  double m = fmin(fmin(am, ap), aq);
+  if (!(((bm ^ bp) >= 0) & (am != 0) & (ap != 0))) return 0.0;
+  long long m = min(min(am, ap), aq);
   // the selected candidate, as a signed linear form in (um, u0, up)
   if (m == am) {
     gm = -1.0; g0 = 1.0;
@@ -62,7 +64,7 @@ __device__ __forceinline__ double half_slope_vjp(double um, double u0, double up
   } else {
     gm = -0.25; gp = 0.25;
   }
-  return pos ? m : -m;
+  return __longlong_as_double(m | (bm & ~kMag));
 }
 
 // One face state after the free-streaming rescale, with the closure
@@ -79,8 +81,8 @@ __device__ __forceinline__ void face_state(int d, int closure, double E, const d
                                            FaceState& s) {
   s.E = E;
   s.n2 = Fin[0] * Fin[0] + Fin[1] * Fin[1] + Fin[2] * Fin[2];
-  s.resc = s.n2 > E * E;
-  double sc = s.resc ? E / sqrt(s.n2) : 1.0;
+  s.resc = lt_nn(E * E, s.n2);
+  double sc = s.resc ? E * rsqrt_pos(s.n2) : 1.0;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     s.Fin[j] = Fin[j];
@@ -93,8 +95,8 @@ __device__ __forceinline__ void face_state(int d, int closure, double E, const d
     s.ha_F2 = s.hb_E = s.hb_F2 = 0.0;
   } else {
     double F2 = s.F[0] * s.F[0] + s.F[1] * s.F[1] + s.F[2] * s.F[2];
-    if (F2 > E * E) {  // only through rounding of the rescale
-      double iF2 = 1.0 / F2;
+    if (lt_nn(E * E, F2)) {  // only through rounding of the rescale
+      double iF2 = rcp_pos(F2);
       s.ha = 0.0;
       s.hb = E * iF2;
       s.ha_E = s.ha_F2 = 0.0;
@@ -102,10 +104,11 @@ __device__ __forceinline__ void face_state(int d, int closure, double E, const d
       s.hb_F2 = -E * iF2 * iF2;
     } else {
       // s = sqrt(4E^2 - 3F2), ha = (s - E)/3, hb = 3/(2E + s)
-      double r = sqrt(4.0 * E * E - 3.0 * F2);
-      double ir = 1.0 / r;
+      double x = 4.0 * E * E - 3.0 * F2;
+      double ir = rsqrt_pos(x);
+      double r = x * ir;
       s.ha = (r - E) * (1.0 / 3.0);
-      s.hb = 3.0 / (2.0 * E + r);
+      s.hb = 3.0 * rcp_pos(2.0 * E + r);
       double r_E = 4.0 * E * ir, r_F2 = -1.5 * ir;
       s.ha_E = (r_E - 1.0) * (1.0 / 3.0);
       s.ha_F2 = r_F2 * (1.0 / 3.0);
@@ -137,7 +140,7 @@ __device__ __forceinline__ void face_state_vjp(int d, const FaceState& s, const 
   for (int j = 0; j < 3; ++j) gF[j] += gF2 * s.F[j];
   if (s.resc) {
     // F = Fin E / |Fin|
-    double in = 1.0 / sqrt(s.n2);
+    double in = rsqrt_pos(s.n2);
     double fg = s.Fin[0] * gF[0] + s.Fin[1] * gF[1] + s.Fin[2] * gF[2];
     gE += fg * in;
     double a = s.E * in, b = fg * in * in;
@@ -231,14 +234,16 @@ __device__ __forceinline__ void face_vjp(const FaceArgs& A, long long fidx) {
   face_state(d, A.ph.closure, R[0], &R[1], sr);
   double num = sl.P[d], den = sl.E;
   int side = 0;
-  if (sr.P[d] * sl.E > sl.P[d] * sr.E) {
+  if (lt_nn(sl.P[d] * sr.E, sr.P[d] * sl.E)) {
     num = sr.P[d];
     den = sr.E;
     side = 1;
   }
-  if (3.0 * num < den) side = -1;
+  if (lt_nn(3.0 * num, den)) side = -1;
   const double chat = A.ph.chat;
-  double S = side < 0 ? chat * sqrt(1.0 / 3.0) : chat * sqrt(num / den);
+  // S = chat sqrt(num/den) = chat num / sqrt(num den)
+  double rq = side < 0 ? 0.0 : rsqrt_pos(num * den);
+  double S = side < 0 ? chat * sqrt(1.0 / 3.0) : chat * num * rq;
   double eps = 1.0, tau = 0.0;
   bool tau_mode = A.ph.hll_mode == RHD_HLL_TAU;
   if (tau_mode) {
@@ -265,9 +270,10 @@ __device__ __forceinline__ void face_vjp(const FaceArgs& A, long long fidx) {
     ghS -= (sr.F[j] - sl.F[j]) * ob[1 + j];
   }
   if (side >= 0) {
-    // S = chat sqrt(num/den): dS/d(num/den) = chat^2 / (2 S)
-    double gx = 0.5 * ghS * chat * chat / (2.0 * S);
-    double gnum = gx / den, gden = -gx * num / (den * den);
+    // S = chat sqrt(num/den): dS/d(num/den) = chat^2 / (2 S), 1/S = den rq / chat
+    double gx = 0.25 * ghS * chat * den * rq;
+    double iden = rcp_pos(den);
+    double gnum = gx * iden, gden = -gx * num * iden * iden;
     if (side == 0) {
       gPL[d] += gnum;
       gEL += gden;
@@ -379,12 +385,13 @@ __device__ __forceinline__ void gather_axis(const Geometry& g, const double* fp,
 // Solve M x = b for a 5 x 5 M (row-major, destroyed) by Gaussian elimination
 // with partial pivoting; rows are swapped with compile-time indices only.
 __device__ __forceinline__ bool solve5(double M[5][5], double b[5]) {
+  double ipiv[5];
 #pragma unroll
   for (int col = 0; col < 5; ++col) {
     // pivot: the largest |M[r][col]|, r >= col, moved into row col
 #pragma unroll
     for (int r = col + 1; r < 5; ++r) {
-      if (fabs(M[r][col]) > fabs(M[col][col])) {
+      if (abs_bits(M[col][col]) < abs_bits(M[r][col])) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
           double t = M[col][k];
@@ -396,8 +403,12 @@ __device__ __forceinline__ bool solve5(double M[5][5], double b[5]) {
         b[r] = t;
       }
     }
-    if (M[col][col] == 0.0 || !isfinite(M[col][col])) return false;
-    double inv = 1.0 / M[col][col];
+    const long long pb = dbits(M[col][col]);
+    if ((pb & kMag) == 0 || (pb & kMag) >= kInfBits) return false;
+    // 1/pivot with the pivot's sign
+    const double inv = __longlong_as_double(
+        dbits(rcp_pos(__longlong_as_double(pb & kMag))) | (pb & ~kMag));
+    ipiv[col] = inv;
 #pragma unroll
     for (int r = col + 1; r < 5; ++r) {
       double f = M[r][col] * inv;
@@ -411,7 +422,7 @@ __device__ __forceinline__ bool solve5(double M[5][5], double b[5]) {
     double s = b[i];
 #pragma unroll
     for (int k = i + 1; k < 5; ++k) s -= M[i][k] * b[k];
-    b[i] = s / M[i][i];
+    b[i] = s * ipiv[i];
   }
   return true;
 }
@@ -424,8 +435,8 @@ __device__ bool ls_adjoint(const Physics& ph, double tdt, double rho, double chi
                            const double y[8], const double ybar[8], double yin[8],
                            double& chibar) {
   const double cr = ph.c_over_chat, icc = ph.inv_cchat, ic2 = ph.inv_c2;
-  const double irho = 1.0 / rho;
-  const double Cv = rho * ph.cv_spec, iCv = 1.0 / Cv;
+  const double irho = rcp_pos(rho);
+  const double Cv = rho * ph.cv_spec, iCv = rcp_pos(Cv);
   const bool o2 = ph.vc_order == 2;
   const double Eg = y[0], E = y[4];
   const double m[3] = {y[1], y[2], y[3]}, F[3] = {y[5], y[6], y[7]};
@@ -452,16 +463,17 @@ __device__ bool ls_adjoint(const Physics& ph, double tdt, double rho, double chi
     ha_E = 1.0 / 3.0;
   } else {
     double F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
-    if (F2 > E * E) {
-      double iF2 = 1.0 / F2;
+    if (lt_nn(E * E, F2)) {
+      double iF2 = rcp_pos(F2);
       ha = 0.0;
       hb = E * iF2;
       hb_E = iF2;
       hb_F2 = -E * iF2 * iF2;
     } else {
-      double r = sqrt(4.0 * E * E - 3.0 * F2), ir = 1.0 / r;
+      double x = 4.0 * E * E - 3.0 * F2;
+      double ir = rsqrt_pos(x), r = x * ir;
       ha = (r - E) * (1.0 / 3.0);
-      hb = 3.0 / (2.0 * E + r);
+      hb = 3.0 * rcp_pos(2.0 * E + r);
       double r_E = 4.0 * E * ir, r_F2 = -1.5 * ir;
       ha_E = (r_E - 1.0) * (1.0 / 3.0);
       ha_F2 = r_F2 * (1.0 / 3.0);

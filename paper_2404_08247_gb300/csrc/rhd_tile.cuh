@@ -29,8 +29,11 @@ struct TileT {
 
 template <int NDIM>
 struct DefaultTileOf;
+// 3-D: 8 planes per block.  Longer z-chunks load fewer halo planes, but the
+// per-block cost varies with the local physics (iteration counts), and short
+// chunks balance the SMs better (256^3: 8 planes 2.6 % faster than 32).
 template <>
-struct DefaultTileOf<3> { using type = TileT<3, 32, 8, 32>; };
+struct DefaultTileOf<3> { using type = TileT<3, 32, 8, 8>; };
 template <>
 struct DefaultTileOf<2> { using type = TileT<2, 32, 8, 1>; };
 template <>
