@@ -86,6 +86,22 @@ def dist_env():
     return ws, rank, local
 
 
+def stage_traffic_record():
+    """DRAM bytes per cell of the stage kernels from the committed ncu summary
+    (profiles/stage_kernel_traffic.json), or None if the kernel sources have
+    changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec if h.hexdigest()[:16] == rec["sources_sha256_16"] else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -446,17 +462,24 @@ def run_ours(args):
     avg_ms = kms[dom] / max(klaunch[dom], 1)
     achieved = ALG_BYTES[dom] * N / (avg_ms * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    rec = stage_traffic_record() if args.precision == "fp64" else None
+    traffic = rec["dram_bytes_per_cell"][KERNEL_NAMES[dom]] * N if rec else None
     roofline = {
         "bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
-        "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+        "traffic_source": ("ncu dram__bytes_read+write per cell at 128^3 x cells "
+                           "(profiles/stage_kernel_traffic.json)") if rec else None,
+        "fp64_pipe_busy": ({"while_active": rec["fp64_pipe_busy_active"][KERNEL_NAMES[dom]],
+                            "of_elapsed_128": rec["fp64_pipe_busy_elapsed"][KERNEL_NAMES[dom]]}
+                           if rec else None),
         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
         if peak_src == "measured" else "fallback",
         "alg_bytes_per_cell": ALG_BYTES[dom],
         "avg_launch_ms": avg_ms,
         "kernel_ms": {KERNEL_NAMES[k]: kms[k] / max(klaunch[k], 1) for k in (0, 1)},
         "step_alg_bytes_per_cell_min": 144,
-        "note": "the FP64 stage kernels are bound by the FP64 pipe (ncu: ~85 % busy), "
-                "not by HBM; see profiles/",
+        "note": "the FP64 stage kernels are bound by the FP64 pipe (ncu: 85 % busy "
+                "while active), not by HBM; see profiles/stage_kernel_fp64_turbulent_box.md",
     }
 
     # end to end through the public API with pinned host buffers
