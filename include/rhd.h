@@ -55,7 +55,17 @@ typedef enum {
   RHD_ERR_STATE = 7         /* call out of order (e.g. step before all fields set) */
 } rhd_status;
 
-typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_REFLECT = 1 } rhd_bc;
+/* Boundaries of the radiation transport.  PERIODIC: wrap; REFLECT: mirror
+ * the cells, negating the normal flux; INFLOW: ghost cells hold the fixed
+ * radiation state bc_state of that face (e.g. an isotropic source of
+ * temperature T_s: E = a_rad T_s^4, F = 0). */
+typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_REFLECT = 1, RHD_BC_INFLOW = 2 } rhd_bc;
+/* Time integration.  IMEX_PDARS: the paper's scheme (eq. imex1/imex2), the
+ * local exchange solved in both stages.  RK2_SSP: the comparison scheme of
+ * Sec. 4.2, transport alone in the first stage and the exchange solved once,
+ * with the full step, after the second -- kept as a negative control for the
+ * asymptotic diffusion limit, which it does not preserve. */
+typedef enum { RHD_SCHEME_IMEX_PDARS = 0, RHD_SCHEME_RK2_SSP = 1 } rhd_scheme;
 typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_EDDINGTON = 1 } rhd_closure;
 /* HLL energy-flux dissipation (Sec. 4.3): TAU scales it by
  * (1 - exp(-tau))/tau, tau = chi dx of the face; NONE is the paper's own
@@ -94,6 +104,16 @@ typedef struct {
   double outer_rtol;   /* outer convergence tolerance (Sec. 3.3: 1e-13) */
   int newton_max_iter; /* bound on Newton updates per inner solve */
   int outer_max_iter;  /* bound on outer passes per local solve */
+  /* -- added after the fields above; rhd_params_default sets them -- */
+  int scheme;          /* rhd_scheme (default IMEX_PDARS) */
+  /* temperature-dependent opacity chi = kappa rho (T/kappa_T_ref)^kappa_T_exp
+   * in the local solve, evaluated at the current Newton iterate and held
+   * fixed in the Jacobian (Sec. 3.3); the default 0 keeps chi = kappa rho.
+   * A non-zero exponent needs hll_mode NONE (the optical-depth factor is
+   * computed from the static kappa and rho). */
+  double kappa_T_exp;
+  double kappa_T_ref;  /* reference temperature (> 0, default 1) */
+  double bc_state[3][2][4]; /* INFLOW faces: ghost E, Fx, Fy, Fz (E > 0) */
 } rhd_params;
 
 typedef struct {
@@ -113,8 +133,10 @@ typedef struct {
 
 /* Fill p with the library defaults: periodic, gamma 5/3, c = chat = 1,
  * a_rad = kB_over_mu = 1, CFL 0.4, M1, v/c order 2, HLL TAU, FP64,
- * tolerances 1e-13, 64 Newton updates, 32 outer passes.  The grid fields are
- * zeroed; the caller sets ndim, n and dx. */
+ * tolerances 1e-13, 64 Newton updates, 32 outer passes, IMEX PD-ARS,
+ * temperature-independent opacity (kappa_T_exp 0, kappa_T_ref 1), inflow
+ * states E = 1, F = 0.  The grid fields are zeroed; the caller sets ndim, n
+ * and dx. */
 void rhd_params_default(rhd_params* p);
 
 /* Check p without touching the GPU.  Returns RHD_OK or RHD_ERR_ARG; on error

@@ -30,7 +30,8 @@ NFIELD = 10
 FIELDS = ("rho", "mx", "my", "mz", "egas", "erad", "fx", "fy", "fz", "kappa")
 STATUS = {0: "ok", 1: "arg", 3: "newton", 4: "outer", 5: "nonphysical"}
 
-_BC = {"periodic": 0, "reflect": 1}
+_BC = {"periodic": 0, "reflect": 1, "inflow": 2}
+_SCHEME = {"imex": 0, "rk2ssp": 1}
 _CLOSURE = {"m1": 0, "eddington": 1}
 _HLL = {"tau": 0, "none": 1}
 
@@ -70,6 +71,10 @@ class OrcParams(ctypes.Structure):
         ("outer_rtol", ctypes.c_double),
         ("newton_max_iter", ctypes.c_int),
         ("outer_max_iter", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("kappa_T_exp", ctypes.c_double),
+        ("kappa_T_ref", ctypes.c_double),
+        ("bc_state", ((ctypes.c_double * 4) * 2) * 3),
     ]
 
 
@@ -149,6 +154,16 @@ def make_params(prob: dict) -> OrcParams:
     p.outer_rtol = float(prob.get("outer_rtol", 1e-13))
     p.newton_max_iter = int(prob.get("newton_max_iter", 64))
     p.outer_max_iter = int(prob.get("outer_max_iter", 32))
+    p.scheme = _SCHEME[prob.get("scheme", "imex")]
+    p.kappa_T_exp = float(prob.get("kappa_T_exp", 0.0))
+    p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
+    # bc_state[d][side] = (E, Fx, Fy, Fz) of inflow faces; default E = 1, F = 0
+    st = prob.get("bc_state", {})
+    for d in range(3):
+        for side in range(2):
+            v = st.get((d, side), (1.0, 0.0, 0.0, 0.0)) if isinstance(st, dict) else st[d][side]
+            for q in range(4):
+                p.bc_state[d][side][q] = float(v[q])
     return p
 
 

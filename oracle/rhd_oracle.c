@@ -84,11 +84,12 @@ static rad_cell fetch(const orc_params* p, const double* U, const long long ic[3
   long long q[3] = {ic[0], ic[1], ic[2]};
   long long nd = p->n[d];
   long long x = q[d] + off;
-  int flip = 0;
+  int flip = 0, inflow = -1; /* inflow: side (0 low, 1 high) of an inflow ghost */
   if (x < 0) {
     if (p->bc[d][0] == ORC_BC_PERIODIC) {
       x = ((x % nd) + nd) % nd;
     } else {
+      if (p->bc[d][0] == ORC_BC_INFLOW) inflow = 0;
       x = -1 - x;
       flip = 1;
     }
@@ -96,6 +97,7 @@ static rad_cell fetch(const orc_params* p, const double* U, const long long ic[3
     if (p->bc[d][1] == ORC_BC_PERIODIC) {
       x = x % nd;
     } else {
+      if (p->bc[d][1] == ORC_BC_INFLOW) inflow = 1;
       x = 2 * nd - 1 - x;
       flip = 1;
     }
@@ -110,6 +112,12 @@ static rad_cell fetch(const orc_params* p, const double* U, const long long ic[3
   r.F[2] = U[ORC_FZ * N + idx];
   if (flip) r.F[d] = -r.F[d];
   r.chi = U[ORC_KAPPA * N + idx] * U[ORC_RHO * N + idx];
+  if (inflow >= 0) {
+    /* reading: an inflow ghost holds the face's fixed radiation state; its
+     * opacity (used only by the TAU factor) is that of the mirrored cell */
+    r.E = p->bc_state[d][inflow][0];
+    for (int j = 0; j < 3; ++j) r.F[j] = p->bc_state[d][inflow][1 + j];
+  }
   return r;
 }
 
@@ -217,8 +225,16 @@ int orc_transport(const orc_params* p, const double* U, double* rate,
  * with the paper's Jacobian (beta^2 terms dropped).  Outer stage: eq. (numF1)
  * or (numF2) for F, the momentum update, then a repeat of the inner stage with
  * the new v and F until the v- and F-terms of R settle. */
+/* Opacity at gas temperature T: chi0 = kappa rho, times (T/T_ref)^exp when the
+ * opacity depends on temperature (the paper's chi carry the superscript
+ * (t+1) of the iterate, Sec. 3.3). */
+static double chi_at(const orc_params* p, double chi0, double T) {
+  if (p->kappa_T_exp == 0.0) return chi0;
+  return chi0 * pow(T / p->kappa_T_ref, p->kappa_T_exp);
+}
+
 int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
-                    double chi, double y[8], int* n_newton, int* n_outer) {
+                    double chi0, double y[8], int* n_newton, int* n_outer) {
   const double c = p->c, chat = p->chat, a = p->a_rad;
   const double Cv = rho * p->kB_over_mu / (p->gamma - 1.0); /* C_v = rho c_v */
   const double Eg0 = y[0];
@@ -229,7 +245,7 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
   *n_outer = 0;
 
   /* With chi = 0 every exchange term of eq. (egupdate)-(fupdate) vanishes. */
-  if (chi == 0.0) return ORC_OK;
+  if (chi0 == 0.0) return ORC_OK;
 
   /* reading: E_tot = Egas^(t) + (c/chat) E^(t), the energy the source terms
    * conserve (the printed chat/c factor is read as a typo; both agree when
@@ -258,6 +274,7 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
       double T = (Eg - Ekin) / Cv;
       if (!(T > 0.0) || !isfinite(T) || !isfinite(R)) return ORC_ERR_NONPHYSICAL;
       double aT4 = a * T * T * T * T; /* 4 pi B / c */
+      double chi = chi_at(p, chi0, T); /* held fixed in the Jacobian below */
       /* E as a function of (Egas, R): eq. (Rnew) solved for E */
       double Ex = aT4 + (vF / (c * c)) / g - R / (chat * chi * tdt * g);
       double FG = Eg - Eg0 + (c / chat) * R;
@@ -289,6 +306,7 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
     /* ---- outer stage: flux and momentum ---- */
     double T = (Eg - Ekin) / Cv;
     double aT4 = a * T * T * T * T;
+    double chi = chi_at(p, chi0, T); /* the updated gas temperature's opacity */
     double D[3][3];
     orc_eddington_tensor(p, E, F, D); /* reading: P from the new E and the
                                          flux of the previous outer pass */
@@ -397,7 +415,12 @@ static const int RAD_FIELD[4] = {ORC_ERAD, ORC_FX, ORC_FY, ORC_FZ};
  *   y(n+1)   = y(n) + dt [s(y(n)) + s(y(n+1/2))]/2
  *                   + dt [f(y(n+1/2)) + f(y(n+1))]/2
  * The stage-1 relation fixes dt f(y(n+1/2)) = y(n+1/2) - y*, y* the explicit
- * state of stage 1; stage 2 uses it as such.  On failure U is left at y(n). */
+ * state of stage 1; stage 2 uses it as such.  On failure U is left at y(n).
+ * RK2-SSP (Sec. 4.2, the comparison scheme):
+ *   y(n+1/2) = y(n) + dt s(y(n))
+ *   y(n+1)   = y(n) + dt [s(y(n)) + s(y(n+1/2))]/2 + dt f(y(n+1)),
+ * the same code with the first implicit stage skipped (y(n+1/2) = y*, so the
+ * (y(n+1/2) - y*)/2 term vanishes) and theta = 1 in the second. */
 int orc_step(const orc_params* p, double* U, double dt, orc_info* info) {
   const long long N = ncell_of(p);
   const size_t bytes = sizeof(double) * ORC_NFIELD * (size_t)N;
@@ -431,8 +454,11 @@ int orc_step(const orc_params* p, double* U, double dt, orc_info* info) {
     for (long long i = 0; i < N; ++i)
       Uh[RAD_FIELD[r] * N + i] = Un[RAD_FIELD[r] * N + i] + dt * s0[r * N + i];
   memcpy(Ystar, Uh, bytes);
-  st = implicit_all(p, Uh, 1.0, dt, info);
-  if (st != ORC_OK) goto done;
+  /* RK2-SSP (Sec. 4.2): no exchange in the first stage, y(n+1/2) = y* */
+  if (p->scheme != ORC_SCHEME_RK2_SSP) {
+    st = implicit_all(p, Uh, 1.0, dt, info);
+    if (st != ORC_OK) goto done;
+  }
 
   /* ---- stage 2: explicit part of eq. (imex2), then implicit, theta = 1/2 ---- */
   st = orc_transport(p, Uh, s1, &fc);
@@ -463,7 +489,8 @@ int orc_step(const orc_params* p, double* U, double dt, orc_info* info) {
       U2[ORC_RHO * N + i] = Un[ORC_RHO * N + i];
       U2[ORC_KAPPA * N + i] = Un[ORC_KAPPA * N + i];
     }
-    st = implicit_all(p, U2, 0.5, dt, info);
+    /* IMEX: (dt/2) f(y(n+1)) in eq. (imex2); RK2-SSP: dt f(y(n+1)) */
+    st = implicit_all(p, U2, p->scheme == ORC_SCHEME_RK2_SSP ? 1.0 : 0.5, dt, info);
     if (st != ORC_OK) goto done;
     memcpy(U, U2, bytes);
   }

@@ -31,7 +31,8 @@ extern "C" {
 enum { ORC_RHO = 0, ORC_MX, ORC_MY, ORC_MZ, ORC_EGAS, ORC_ERAD, ORC_FX, ORC_FY,
        ORC_FZ, ORC_KAPPA, ORC_NFIELD };
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_REFLECT = 1 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_REFLECT = 1, ORC_BC_INFLOW = 2 };
+enum { ORC_SCHEME_IMEX = 0, ORC_SCHEME_RK2_SSP = 1 };
 enum { ORC_CLOSURE_M1 = 0, ORC_CLOSURE_EDDINGTON = 1 };
 enum { ORC_HLL_TAU = 0, ORC_HLL_NONE = 1 };
 
@@ -56,6 +57,10 @@ typedef struct {
   double outer_rtol;      /* tolerance of the outer iteration */
   int newton_max_iter;
   int outer_max_iter;
+  int scheme;             /* ORC_SCHEME_*: eq. imex1/imex2, or RK2-SSP (Sec. 4.2) */
+  double kappa_T_exp;     /* chi = kappa rho (T / kappa_T_ref)^kappa_T_exp */
+  double kappa_T_ref;
+  double bc_state[3][2][4]; /* ghost E, Fx, Fy, Fz of ORC_BC_INFLOW faces */
 } orc_params;
 
 typedef struct {
@@ -82,7 +87,9 @@ int orc_transport(const orc_params* p, const double* U, double* rate,
 
 /* Implicit local solve of one cell, eq. (egupdate)-(fupdate), with the
  * stage weight theta.  y = {Egas, mx, my, mz, E, Fx, Fy, Fz} holds the state
- * after the explicit terms on input and the solution on output. */
+ * after the explicit terms on input and the solution on output.  chi is
+ * kappa rho; with kappa_T_exp != 0 the opacity is chi (T/kappa_T_ref)^exp at
+ * the current gas temperature. */
 int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
                     double chi, double y[8], int* n_newton, int* n_outer);
 

@@ -134,6 +134,14 @@ void rhd_params_default(rhd_params* p) {
   p->outer_rtol = 1e-13;
   p->newton_max_iter = 64;
   p->outer_max_iter = 32;
+  p->scheme = RHD_SCHEME_IMEX_PDARS;
+  p->kappa_T_exp = 0.0;
+  p->kappa_T_ref = 1.0;
+  for (int d = 0; d < 3; ++d)
+    for (int s = 0; s < 2; ++s) {
+      p->bc_state[d][s][0] = 1.0;
+      p->bc_state[d][s][1] = p->bc_state[d][s][2] = p->bc_state[d][s][3] = 0.0;
+    }
 }
 
 static int bad(char* msg, int len, const char* fmt, ...) {
@@ -159,10 +167,19 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
       if (!(p->dx[d] > 0.0) || !std::isfinite(p->dx[d]))
         return bad(msg, msglen, "dx[%d] must be positive and finite", d), RHD_ERR_ARG;
       for (int s = 0; s < 2; ++s) {
-        if (p->bc[d][s] != RHD_BC_PERIODIC && p->bc[d][s] != RHD_BC_REFLECT)
+        if (p->bc[d][s] != RHD_BC_PERIODIC && p->bc[d][s] != RHD_BC_REFLECT &&
+            p->bc[d][s] != RHD_BC_INFLOW)
           return bad(msg, msglen, "bc[%d][%d] is not an rhd_bc", d, s), RHD_ERR_ARG;
-        if (p->bc[d][s] == RHD_BC_REFLECT && p->n[d] < 2)
-          return bad(msg, msglen, "reflecting axis %d needs n >= 2", d), RHD_ERR_ARG;
+        if (p->bc[d][s] != RHD_BC_PERIODIC && p->n[d] < 2)
+          return bad(msg, msglen, "a reflecting or inflow axis %d needs n >= 2", d),
+                 RHD_ERR_ARG;
+        if (p->bc[d][s] == RHD_BC_INFLOW) {
+          const double* st = p->bc_state[d][s];
+          if (!(st[0] > 0.0) || !std::isfinite(st[0]) || !std::isfinite(st[1]) ||
+              !std::isfinite(st[2]) || !std::isfinite(st[3]))
+            return bad(msg, msglen, "bc_state[%d][%d] needs E > 0 and finite F", d, s),
+                   RHD_ERR_ARG;
+        }
       }
       if ((p->bc[d][0] == RHD_BC_PERIODIC) != (p->bc[d][1] == RHD_BC_PERIODIC))
         return bad(msg, msglen, "axis %d: periodic must apply to both faces", d),
@@ -198,6 +215,14 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
     return bad(msg, msglen, "tolerances must be positive"), RHD_ERR_ARG;
   if (p->newton_max_iter < 1 || p->outer_max_iter < 1)
     return bad(msg, msglen, "iteration bounds must be >= 1"), RHD_ERR_ARG;
+  if (p->scheme != RHD_SCHEME_IMEX_PDARS && p->scheme != RHD_SCHEME_RK2_SSP)
+    return bad(msg, msglen, "scheme is not an rhd_scheme"), RHD_ERR_ARG;
+  if (!std::isfinite(p->kappa_T_exp) || !(p->kappa_T_ref > 0.0) ||
+      !std::isfinite(p->kappa_T_ref))
+    return bad(msg, msglen, "kappa_T_exp must be finite and kappa_T_ref > 0"), RHD_ERR_ARG;
+  if (p->kappa_T_exp != 0.0 && p->hll_mode != RHD_HLL_NONE)
+    return bad(msg, msglen, "a temperature-dependent opacity needs hll_mode NONE"),
+           RHD_ERR_ARG;
   return RHD_OK;
 }
 
@@ -210,7 +235,9 @@ double rhd_default_dt(const rhd_params* p) {
 
 }  // extern "C"
 
-static void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
+// Device-side geometry and physics of validated params (shared by the
+// single-grid, batched and no-allocation paths).
+void rhd::fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
   memset(&g, 0, sizeof(g));
   g.ndim = p->ndim;
   int stride = 1;
@@ -222,6 +249,8 @@ static void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
     g.inv_dx[d] = 1.0 / p->dx[d];
     g.bc[d][0] = p->bc[d][0];
     g.bc[d][1] = p->bc[d][1];
+    for (int s = 0; s < 2; ++s)
+      for (int q = 0; q < 4; ++q) g.bc_state[d][s][q] = p->bc_state[d][s][q];
   }
   g.ncell = stride;
   memset(&ph, 0, sizeof(ph));
@@ -241,6 +270,9 @@ static void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
   ph.outer_rtol = p->outer_rtol;
   ph.newton_max = p->newton_max_iter;
   ph.outer_max = p->outer_max_iter;
+  ph.scheme = p->scheme;
+  ph.kappa_T_exp = p->kappa_T_exp;
+  ph.inv_kappa_T_ref = 1.0 / p->kappa_T_ref;
 }
 
 static void release(rhd_ctx* c) {
@@ -780,6 +812,12 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
     return fail(c, RHD_ERR_STATE, "rho and kappa must be set");
   if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
   if (!tape || !ybar || !kappa_bar) return fail(c, RHD_ERR_ARG, "a buffer is NULL");
+  if (c->p.scheme != RHD_SCHEME_IMEX_PDARS || c->p.kappa_T_exp != 0.0)
+    return fail(c, RHD_ERR_ARG,
+                "the adjoint covers the IMEX scheme with a temperature-independent opacity");
+  for (int d = 0; d < c->p.ndim; ++d)
+    if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
+      return fail(c, RHD_ERR_ARG, "the adjoint covers periodic and reflecting boundaries");
   const size_t N = (size_t)c->ncell;
   const size_t S = NY * N;
   if (count != (int64_t)((2 * (size_t)nsteps + 1) * S))

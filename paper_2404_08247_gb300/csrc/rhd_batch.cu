@@ -55,7 +55,7 @@ using Tile2b = TileT<2, 64, 4, 1>;
 using Tile2c = TileT<2, 16, 16, 1>;
 constexpr int kBatchThreads = 256;
 
-template <int STAGE, class T2, typename R>
+template <int STAGE, class T2, typename R, bool GEN>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item, s_skip;
@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
 #pragma unroll
     for (int q = 0; q < 4; ++q) A.rate[q] = nullptr;
     if (w.kind == 0)
-      stage_tile<STAGE, Tile1, R>(A, w.x0, 0, 0, smem_raw, ts);
+      stage_tile<STAGE, Tile1, R, GEN>(A, w.x0, 0, 0, smem_raw, ts);
     else
-      stage_tile<STAGE, T2, R>(A, w.x0, w.y0, 0, smem_raw, ts);
+      stage_tile<STAGE, T2, R, GEN>(A, w.x0, w.y0, 0, smem_raw, ts);
   }
   flush_stats<kBatchThreads>(B.st, ts);
 }
@@ -106,32 +106,40 @@ size_t batch_smem() {
   return a > b ? a : b;
 }
 
-template <int STAGE, class T2, typename R>
+template <int STAGE, class T2, typename R, bool GEN>
 cudaError_t launch_batch_t(const BatchArgs& B, int grid, cudaStream_t s) {
   size_t sm = batch_smem<T2, R>();
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<STAGE, T2, R>,
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<STAGE, T2, R, GEN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  batch_kernel<STAGE, T2, R><<<grid, kBatchThreads, sm, s>>>(B);
+  batch_kernel<STAGE, T2, R, GEN><<<grid, kBatchThreads, sm, s>>>(B);
   return cudaGetLastError();
 }
 
-template <int STAGE, typename R>
+template <int STAGE, typename R, bool GEN>
 cudaError_t launch_batch_r(int tile2d, const BatchArgs& B, int grid, cudaStream_t s) {
   switch (tile2d) {
-    case 1: return launch_batch_t<STAGE, Tile2b, R>(B, grid, s);
-    case 2: return launch_batch_t<STAGE, Tile2c, R>(B, grid, s);
-    default: return launch_batch_t<STAGE, Tile2a, R>(B, grid, s);
+    case 1: return launch_batch_t<STAGE, Tile2b, R, GEN>(B, grid, s);
+    case 2: return launch_batch_t<STAGE, Tile2c, R, GEN>(B, grid, s);
+    default: return launch_batch_t<STAGE, Tile2a, R, GEN>(B, grid, s);
   }
 }
 
-cudaError_t launch_batch(int stage, int precision, int tile2d, const BatchArgs& B, int grid,
-                         cudaStream_t s) {
+template <typename R, bool GEN>
+cudaError_t launch_batch_p(int stage, int tile2d, const BatchArgs& B, int grid,
+                           cudaStream_t s) {
+  return stage == 1 ? launch_batch_r<1, R, GEN>(tile2d, B, grid, s)
+                    : launch_batch_r<2, R, GEN>(tile2d, B, grid, s);
+}
+
+// general: some problem of the batch needs the general kernels
+cudaError_t launch_batch(int stage, int precision, bool general, int tile2d,
+                         const BatchArgs& B, int grid, cudaStream_t s) {
   if (precision == RHD_PREC_MIXED)
-    return stage == 1 ? launch_batch_r<1, float>(tile2d, B, grid, s)
-                      : launch_batch_r<2, float>(tile2d, B, grid, s);
-  return stage == 1 ? launch_batch_r<1, double>(tile2d, B, grid, s)
-                    : launch_batch_r<2, double>(tile2d, B, grid, s);
+    return general ? launch_batch_p<float, true>(stage, tile2d, B, grid, s)
+                   : launch_batch_p<float, false>(stage, tile2d, B, grid, s);
+  return general ? launch_batch_p<double, true>(stage, tile2d, B, grid, s)
+                 : launch_batch_p<double, false>(stage, tile2d, B, grid, s);
 }
 
 const int kTileX[3] = {32, 64, 16};
@@ -139,36 +147,7 @@ const int kTileY[3] = {8, 4, 16};
 
 void fill_desc(const rhd_params* p, ProblemDesc& d) {
   memset(&d, 0, sizeof(d));
-  Geometry& g = d.g;
-  g.ndim = p->ndim;
-  int stride = 1;
-  for (int k = 0; k < 3; ++k) {
-    g.n[k] = (int)p->n[k];
-    g.stride[k] = stride;
-    stride *= g.n[k];
-    g.dx[k] = p->dx[k];
-    g.inv_dx[k] = 1.0 / p->dx[k];
-    g.bc[k][0] = p->bc[k][0];
-    g.bc[k][1] = p->bc[k][1];
-  }
-  g.ncell = stride;
-  Physics& ph = d.ph;
-  ph.c = p->c;
-  ph.chat = p->chat;
-  ph.a_rad = p->a_rad;
-  ph.cv_spec = p->kB_over_mu / (p->gamma - 1.0);
-  ph.inv_c = 1.0 / p->c;
-  ph.c_over_chat = p->c / p->chat;
-  ph.chat_over_c = p->chat / p->c;
-  ph.inv_c2 = 1.0 / (p->c * p->c);
-  ph.inv_cchat = 1.0 / (p->c * p->chat);
-  ph.closure = p->closure;
-  ph.vc_order = p->vc_order;
-  ph.hll_mode = p->hll_mode;
-  ph.newton_rtol = p->newton_rtol;
-  ph.outer_rtol = p->outer_rtol;
-  ph.newton_max = p->newton_max_iter;
-  ph.outer_max = p->outer_max_iter;
+  rhd::fill_geometry(p, d.g, d.ph);
   d.dt = rhd_default_dt(p);
 }
 
@@ -202,6 +181,7 @@ struct rhd_batch {
   std::vector<char> eps_dirty;
   int tile2d = 0;
   int blocks_per_sm = 2;
+  bool general = false;  // some problem needs the general kernels
   int items_tile = -1;  // tile shape the work list was built for
   struct Graph {
     int nsteps, cur0, tile2d, bps;
@@ -309,6 +289,7 @@ rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out) {
   bool any_tau = false;
   for (int p = 0; p < nprob; ++p) {
     fill_desc(&probs[p], b->desc[p]);
+    b->general = b->general || needs_general(b->desc[p].g, b->desc[p].ph);
     b->desc[p].offset = off;
     b->offsets[p] = off;
     off += b->desc[p].g.ncell;
@@ -481,11 +462,11 @@ static rhd_status capture(rhd_batch* b, int nsteps, int cur0, cudaGraphExec_t* e
     B.yn = b->ybuf[cur];
     B.yo = b->yhalf;
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
-    if (e == cudaSuccess) e = launch_batch(1, b->precision, b->tile2d, B, grid, cs);
+    if (e == cudaSuccess) e = launch_batch(1, b->precision, b->general, b->tile2d, B, grid, cs);
     B.yt = b->yhalf;
     B.yo = b->ybuf[cur ^ 1];
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
-    if (e == cudaSuccess) e = launch_batch(2, b->precision, b->tile2d, B, grid, cs);
+    if (e == cudaSuccess) e = launch_batch(2, b->precision, b->general, b->tile2d, B, grid, cs);
     cur ^= 1;
   }
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

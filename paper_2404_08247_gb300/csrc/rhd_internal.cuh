@@ -39,6 +39,7 @@ struct Geometry {
   int bc[3][2];
   double dx[3];
   double inv_dx[3];
+  double bc_state[3][2][4];  // ghost E, Fx, Fy, Fz of RHD_BC_INFLOW faces
 };
 
 struct Physics {
@@ -52,6 +53,9 @@ struct Physics {
   int closure, vc_order, hll_mode;
   double newton_rtol, outer_rtol;
   int newton_max, outer_max;
+  int scheme;              // rhd_scheme
+  double kappa_T_exp;      // chi = kappa rho (T / T_ref)^kappa_T_exp
+  double inv_kappa_T_ref;  // 1 / T_ref
 };
 
 struct StageArgs {
@@ -340,7 +344,9 @@ __device__ __forceinline__ bool quartic_start(double a4, double rhs, double T0, 
 // factor); residuals, the state, the closure of the exchange term v.P and
 // every update stay double, so the solve meets the double-precision
 // convergence tests (inner and outer) and conserves to rounding.
-template <bool MIXED>
+// GEN: compiled with the temperature-dependent opacity; the default physics
+// (constant chi) uses the GEN = false copy, free of that branch.
+template <bool MIXED, bool GEN>
 __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double rho,
                                            double chi, double y[8], int& nn, int& no) {
   nn = 0;
@@ -353,9 +359,13 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
   const double a = ph.a_rad;
   const double Eg0 = y[0], E0 = y[4];
   const double Etot = Eg0 + cr * E0;
-  const double k = ph.chat * chi * tdt;
+  // k = chat chi theta dt; with a temperature-dependent opacity chi is taken
+  // at the current Newton iterate (the paper's chi carry the superscript
+  // (t+1)) and held fixed in the Jacobian
+  const bool vary = GEN && ph.kappa_T_exp != 0.0;
+  const double k0 = ph.chat * chi * tdt;
+  double k = k0;
   const double tolG = ph.newton_rtol * Etot;
-  const double tolR = tolG * k;
   double Eg = Eg0, R = 0.0, E = E0;
   double m[3] = {y[1], y[2], y[3]};
   double F[3] = {y[5], y[6], y[7]};
@@ -370,6 +380,7 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
   {
     double T0 = (Eg0 - Ekin) * inv_Cv;
     if (pos_finite(T0)) {
+      if (vary) k = k0 * pow(T0 * ph.inv_kappa_T_ref, ph.kappa_T_exp);
       double kg = k * g;
       double inv1 = rcp_pos(1.0 + kg);
       double a4 = cr * kg * a * inv1 * inv_Cv;
@@ -384,17 +395,25 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
 
   for (int outer = 0; outer < ph.outer_max; ++outer) {
     no = outer + 1;
-    const double kg = k * g;
-    const double kw = k * w;
-    const double c4 = 4.0 * kg * a * inv_Cv;  // J10 / T^3
-    const double gpk = g * (1.0 + k);
-    const double tolRg = tolR * g;
+    double kg = k * g;
+    double kw = k * w;
+    double c4 = 4.0 * kg * a * inv_Cv;  // J10 / T^3
+    double gpk = g * (1.0 + k);
+    double tolRg = tolG * k * g;
 
     bool conv = false;
     double aT4 = 0.0;
     for (int it = 0;; ++it) {
       double T = (Eg - Ekin) * inv_Cv;
       if (!pos_finite(T) || !finite_bits(R)) return RHD_ERR_NONPHYSICAL;
+      if (vary) {
+        k = k0 * pow(T * ph.inv_kappa_T_ref, ph.kappa_T_exp);
+        kg = k * g;
+        kw = k * w;
+        c4 = 4.0 * kg * a * inv_Cv;
+        gpk = g * (1.0 + k);
+        tolRg = tolG * k * g;
+      }
       double T2 = T * T;
       aT4 = a * T2 * T2;
       double r0 = (Eg - Eg0) + cr * R;
@@ -489,5 +508,15 @@ cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
                                cudaStream_t s);
 // message returned by rhd_last_error(NULL) on this thread
 void set_global_error(const char* msg);
+// device-side geometry and physics of validated params
+void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph);
+// whether a grid needs the general kernels (RK2-SSP, a temperature-dependent
+// opacity or an inflow face) rather than the lean default ones
+inline bool needs_general(const Geometry& g, const Physics& ph) {
+  if (ph.scheme != RHD_SCHEME_IMEX_PDARS || ph.kappa_T_exp != 0.0) return true;
+  for (int d = 0; d < g.ndim; ++d)
+    if (g.bc[d][0] == RHD_BC_INFLOW || g.bc[d][1] == RHD_BC_INFLOW) return true;
+  return false;
+}
 
 }  // namespace rhd

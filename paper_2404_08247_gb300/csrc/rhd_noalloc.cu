@@ -64,38 +64,7 @@ rhd_status resolve_symbols(int dev, DeviceSymbols*& out) {
   return RHD_OK;
 }
 
-void fill(const rhd_params* p, Geometry& g, Physics& ph) {
-  memset(&g, 0, sizeof(g));
-  g.ndim = p->ndim;
-  int stride = 1;
-  for (int d = 0; d < 3; ++d) {
-    g.n[d] = (int)p->n[d];
-    g.stride[d] = stride;
-    stride *= g.n[d];
-    g.dx[d] = p->dx[d];
-    g.inv_dx[d] = 1.0 / p->dx[d];
-    g.bc[d][0] = p->bc[d][0];
-    g.bc[d][1] = p->bc[d][1];
-  }
-  g.ncell = stride;
-  memset(&ph, 0, sizeof(ph));
-  ph.c = p->c;
-  ph.chat = p->chat;
-  ph.a_rad = p->a_rad;
-  ph.cv_spec = p->kB_over_mu / (p->gamma - 1.0);
-  ph.inv_c = 1.0 / p->c;
-  ph.c_over_chat = p->c / p->chat;
-  ph.chat_over_c = p->chat / p->c;
-  ph.inv_c2 = 1.0 / (p->c * p->c);
-  ph.inv_cchat = 1.0 / (p->c * p->chat);
-  ph.closure = p->closure;
-  ph.vc_order = p->vc_order;
-  ph.hll_mode = p->hll_mode;
-  ph.newton_rtol = p->newton_rtol;
-  ph.outer_rtol = p->outer_rtol;
-  ph.newton_max = p->newton_max_iter;
-  ph.outer_max = p->outer_max_iter;
-}
+void fill(const rhd_params* p, Geometry& g, Physics& ph) { rhd::fill_geometry(p, g, ph); }
 
 // ABI field -> evolved slot (the ABI orders rho, m, Egas, E, F, kappa)
 const int kSlotField[NY] = {RHD_F_EGAS, RHD_F_MX, RHD_F_MY, RHD_F_MZ,

@@ -10,7 +10,7 @@
 
 namespace rhd {
 
-template <int STAGE, int NDIM, typename R>
+template <int STAGE, int NDIM, typename R, bool GEN>
 __global__ void __launch_bounds__(Tile<NDIM>::NT, 2) stage_kernel(const StageArgs A) {
   using T = Tile<NDIM>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(Tile<NDIM>::NT, 2) stage_kernel(const StageArg
   __syncthreads();
   if (s_skip) return;  // a previous launch of this batch failed
   TileStats ts;
-  stage_tile<STAGE, T, R>(A, blockIdx.x * T::TX, blockIdx.y * T::TY, blockIdx.z * T::LZ,
+  stage_tile<STAGE, T, R, GEN>(A, blockIdx.x * T::TX, blockIdx.y * T::TY, blockIdx.z * T::LZ,
                           smem_raw, ts);
   flush_stats<T::NT>(A.st, ts);
 }
@@ -71,34 +71,38 @@ cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* k
   return cudaGetLastError();
 }
 
-template <int STAGE, int NDIM, typename R>
+template <int STAGE, int NDIM, typename R, bool GEN>
 static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s) {
   using T = Tile<NDIM>;
   using S = SmemT<T, R>;
   // opt in to more than 48 KiB of dynamic shared memory (idempotent)
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<STAGE, NDIM, R>,
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<STAGE, NDIM, R, GEN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)S::BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid((A.g.n[0] + T::TX - 1) / T::TX, (A.g.n[1] + T::TY - 1) / T::TY,
             (A.g.n[2] + T::LZ - 1) / T::LZ);
-  stage_kernel<STAGE, NDIM, R><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
+  stage_kernel<STAGE, NDIM, R, GEN><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
   return cudaGetLastError();
 }
 
-template <int STAGE, typename R>
+template <int STAGE, typename R, bool GEN>
 static cudaError_t launch_prec(const StageArgs& A, cudaStream_t s) {
   switch (A.g.ndim) {
-    case 1: return launch_nd<STAGE, 1, R>(A, s);
-    case 2: return launch_nd<STAGE, 2, R>(A, s);
-    default: return launch_nd<STAGE, 3, R>(A, s);
+    case 1: return launch_nd<STAGE, 1, R, GEN>(A, s);
+    case 2: return launch_nd<STAGE, 2, R, GEN>(A, s);
+    default: return launch_nd<STAGE, 3, R, GEN>(A, s);
   }
 }
 
+// The lean kernels (GEN = false) serve the default physics; RK2-SSP, a
+// temperature-dependent opacity or an inflow face select the general ones.
 template <int STAGE>
 static cudaError_t launch_stage_t(int precision, const StageArgs& A, cudaStream_t s) {
-  return precision == RHD_PREC_MIXED ? launch_prec<STAGE, float>(A, s)
-                                     : launch_prec<STAGE, double>(A, s);
+  const bool gen = needs_general(A.g, A.ph);
+  if (precision == RHD_PREC_MIXED)
+    return gen ? launch_prec<STAGE, float, true>(A, s) : launch_prec<STAGE, float, false>(A, s);
+  return gen ? launch_prec<STAGE, double, true>(A, s) : launch_prec<STAGE, double, false>(A, s);
 }
 
 cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s) {

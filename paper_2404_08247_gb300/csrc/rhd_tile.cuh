@@ -75,6 +75,14 @@ __device__ __forceinline__ int fold(int x, int n, int bclo, int bchi, bool& flip
   return x;
 }
 
+// Side (0 low, 1 high) of an inflow ghost at coordinate x along axis d, or -1
+// for an interior cell or a ghost of another boundary kind.
+__device__ __forceinline__ int inflow_side(const Geometry& g, int d, int x) {
+  if (x < 0) return g.bc[d][0] == RHD_BC_INFLOW ? 0 : -1;
+  if (x >= g.n[d]) return g.bc[d][1] == RHD_BC_INFLOW ? 1 : -1;
+  return -1;
+}
+
 __device__ __forceinline__ double eps_direct(const StageArgs& A, int ia, int ib, int d) {
   double tau = 0.5 * (A.kappa[ia] * A.rho[ia] + A.kappa[ib] * A.rho[ib]) * A.g.dx[d];
   return tau_factor(tau);
@@ -103,7 +111,7 @@ __device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, in
 
 // load plane zg (global z, may be a ghost plane) into ring slot `slot`,
 // converting to the transport precision R
-template <class T, typename R>
+template <class T, typename R, bool GEN>
 __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot, int zg,
                                            int x0, int y0) {
   constexpr int NDIM = T::NDIM;
@@ -112,6 +120,7 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
   const R inv_c = (R)A.ph.inv_c;
   bool fz = false;
   int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz) : 0;
+  const int zin = GEN && NDIM == 3 ? inflow_side(g, 2, zg) : -1;
   R* pl = ring + slot * 4 * S::PS;
   for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
     int ii = c % S::PW, jj = c / S::PW;
@@ -123,10 +132,30 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
     R Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
     R Fy = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
     R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+    Fx = fx ? -Fx : Fx;
+    Fy = fy ? -Fy : Fy;
+    Fz = fz ? -Fz : Fz;
+    // ghost cells of an inflow face hold its fixed radiation state
+    int ax = zin >= 0 ? 2 : -1, side = zin;
+    if (GEN && ax < 0) {
+      side = inflow_side(g, 0, x0 + ii - T::HX);
+      ax = side >= 0 ? 0 : -1;
+    }
+    if (GEN && ax < 0 && NDIM >= 2) {
+      side = inflow_side(g, 1, y0 + jj - T::HY);
+      ax = side >= 0 ? 1 : -1;
+    }
+    if (ax >= 0) {
+      const double* st = g.bc_state[ax][side];
+      E = (R)st[0];
+      Fx = (R)(st[1] * A.ph.inv_c);
+      Fy = (R)(st[2] * A.ph.inv_c);
+      Fz = (R)(st[3] * A.ph.inv_c);
+    }
     pl[0 * S::PS + c] = E;
-    pl[1 * S::PS + c] = fx ? -Fx : Fx;
-    pl[2 * S::PS + c] = fy ? -Fy : Fy;
-    pl[3 * S::PS + c] = fz ? -Fz : Fz;
+    pl[1 * S::PS + c] = Fx;
+    pl[2 * S::PS + c] = Fy;
+    pl[3 * S::PS + c] = Fz;
   }
 }
 
@@ -161,13 +190,15 @@ struct TileStats {
   unsigned long long nn_sum = 0, no_sum = 0, cnt = 0;
 };
 
-// One tile of one stage (STAGE 1, 2, or 0 = transport rates only): the block
+// One tile of one stage (STAGE 1, 2, or 0 = transport rates only; GEN: with
+// the general physics, RK2-SSP, a temperature-dependent opacity and inflow
+// faces, which the default physics compiles out): the block
 // of T::NT threads owns the cells x0 + [0, TX) x y0 + [0, TY) x planes
 // [kbeg, kbeg + LZ) of the grid described by A.  R: precision of
 // reconstruction, closure and HLL fluxes (double for FP64, float for MIXED);
 // the state, the flux differences, the updates and the local solve are double
 // in both.  Every thread of the block must call it (it synchronises).
-template <int STAGE, class T, typename R>
+template <int STAGE, class T, typename R, bool GEN>
 __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, int kbeg,
                                            unsigned char* smem_raw, TileStats& ts) {
   using S = SmemT<T, R>;
@@ -195,7 +226,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell
   if (NDIM == 3) {
     for (int o = -2; o <= 1; ++o)
-      load_plane<T, R>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
+      load_plane<T, R, GEN>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
     __syncthreads();
     R um[4], u0[4], up[4], upp[4];
     cell_of<T, R>(ring + ((kbeg - 2) & 3) * 4 * S::PS, own, um);
@@ -216,9 +247,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 
   for (int k = kbeg; k < kend; ++k) {
     if (NDIM == 3) {
-      load_plane<T, R>(A, ring, (k + 2) & 3, k + 2, x0, y0);
+      load_plane<T, R, GEN>(A, ring, (k + 2) & 3, k + 2, x0, y0);
     } else {
-      load_plane<T, R>(A, ring, 0, 0, x0, y0);
+      load_plane<T, R, GEN>(A, ring, 0, 0, x0, y0);
     }
     __syncthreads();
     const R* pl = ring + (NDIM == 3 ? (k & 3) : 0) * 4 * S::PS;
@@ -335,9 +366,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       const double chi = A.kappa[idx] * rho;
       int nn = 0, no = 0;
       int code = RHD_OK;
+      // RK2-SSP (Sec. 4.2): no exchange in stage 1, the full dt f(y(n+1)) in
+      // stage 2; IMEX PD-ARS: theta = 1, then theta = 1/2
+      const bool rk2 = GEN && ph.scheme == RHD_SCHEME_RK2_SSP;
       if (STAGE != 0) {
-        code = bad ? RHD_ERR_NONPHYSICAL
-                   : local_solve<MIXED>(ph, STAGE == 1 ? A.dt : 0.5 * A.dt, rho, chi, y, nn, no);
+        if (bad)
+          code = RHD_ERR_NONPHYSICAL;
+        else if (!(rk2 && STAGE == 1))
+          code = local_solve<MIXED, GEN>(ph, (STAGE == 1 || rk2) ? A.dt : 0.5 * A.dt, rho, chi, y,
+                                    nn, no);
 #pragma unroll
         for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
       }
@@ -350,7 +387,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       ts.no_max = max(ts.no_max, no);
       ts.nn_sum += nn;
       ts.no_sum += no;
-      ts.cnt += 1;
+      ts.cnt += (STAGE != 0 && rk2 && STAGE == 1) ? 0 : 1;
     }
     if (NDIM == 3) {
 #pragma unroll

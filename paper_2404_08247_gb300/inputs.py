@@ -305,3 +305,30 @@ def rest_state(prob: dict, T, log_kappa) -> np.ndarray:
     sh = T.shape
     return equilibrium_state(prob, np.ones(sh), T, np.zeros((3,) + sh),
                              np.exp(np.asarray(log_kappa, dtype=np.float64)))
+
+
+# Asymptotic Marshak wave (Sec. 5.2) in cgs with temperatures in keV.
+A_RAD_KEV = 7.5657e-15 * 1.160451812e7 ** 4  # radiation constant, erg cm^-3 keV^-4
+C_CGS = 2.99792458e10                         # cm s^-1
+
+
+def marshak_wave_1d(n: int = 60, L: float = 0.66, scheme: str = "imex", cfl: float = 0.9,
+                    T_source: float = 1.0, T0: float = 1e-3, **kw):
+    """Radiation from a T_source (keV) source entering a cold medium through the
+    x = 0 face: chi = 300 cm^-1 (T/keV)^-3, volumetric heat capacity
+    3e15 erg cm^-3 keV^-1 (rho = 1 g cm^-3, gamma = 5/3), T = T0 and
+    E = a T0^4 initially, gas at rest, chat = c, HLL NONE (the paper's IMEX
+    method), reflecting far wall.  The inflow face holds E = a T_source^4,
+    F = 0.  Returns (problem, state)."""
+    dx = L / n
+    cv = 3e15
+    prob = base_problem(
+        1, [n], [dx], c=C_CGS, chat=C_CGS, a_rad=A_RAD_KEV, kB_over_mu=cv * (2.0 / 3.0),
+        gamma=5.0 / 3.0, hll_mode="none", kappa_T_exp=-3.0, kappa_T_ref=1.0,
+        bc=[["inflow", "reflect"], ["periodic", "periodic"], ["periodic", "periodic"]],
+        bc_state={(0, 0): (A_RAD_KEV * T_source ** 4, 0.0, 0.0, 0.0)},
+        scheme=scheme, cfl=cfl, **kw)
+    sh = (1, 1, n)
+    U = equilibrium_state(prob, np.ones(sh), np.full(sh, T0), np.zeros((3,) + sh),
+                          np.full(sh, 300.0))
+    return prob, U

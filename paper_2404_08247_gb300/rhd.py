@@ -22,7 +22,8 @@ RHD_OK, RHD_ERR_ARG, RHD_ERR_CUDA, RHD_ERR_NEWTON, RHD_ERR_OUTER, \
     RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE = range(8)
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "newton", 4: "outer",
                 5: "nonphysical", 6: "timeout", 7: "state"}
-RHD_BC_PERIODIC, RHD_BC_REFLECT = 0, 1
+RHD_BC_PERIODIC, RHD_BC_REFLECT, RHD_BC_INFLOW = 0, 1, 2
+RHD_SCHEME_IMEX_PDARS, RHD_SCHEME_RK2_SSP = 0, 1
 RHD_CLOSURE_M1, RHD_CLOSURE_EDDINGTON = 0, 1
 RHD_HLL_TAU, RHD_HLL_NONE = 0, 1
 RHD_PREC_FP64, RHD_PREC_MIXED = 0, 1
@@ -30,7 +31,8 @@ RHD_NFIELDS = 10
 (RHD_F_RHO, RHD_F_MX, RHD_F_MY, RHD_F_MZ, RHD_F_EGAS, RHD_F_ERAD, RHD_F_FX,
  RHD_F_FY, RHD_F_FZ, RHD_F_KAPPA) = range(10)
 
-_BC = {"periodic": RHD_BC_PERIODIC, "reflect": RHD_BC_REFLECT}
+_BC = {"periodic": RHD_BC_PERIODIC, "reflect": RHD_BC_REFLECT, "inflow": RHD_BC_INFLOW}
+_SCHEME = {"imex": RHD_SCHEME_IMEX_PDARS, "rk2ssp": RHD_SCHEME_RK2_SSP}
 _CLOSURE = {"m1": RHD_CLOSURE_M1, "eddington": RHD_CLOSURE_EDDINGTON}
 _HLL = {"tau": RHD_HLL_TAU, "none": RHD_HLL_NONE}
 _PREC = {"fp64": RHD_PREC_FP64, "mixed": RHD_PREC_MIXED}
@@ -62,6 +64,10 @@ class rhd_params(ctypes.Structure):
         ("outer_rtol", ctypes.c_double),
         ("newton_max_iter", ctypes.c_int),
         ("outer_max_iter", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("kappa_T_exp", ctypes.c_double),
+        ("kappa_T_ref", ctypes.c_double),
+        ("bc_state", ((ctypes.c_double * 4) * 2) * 3),
     ]
 
 
@@ -207,6 +213,15 @@ def params_from_problem(prob: dict, precision: str | int = "fp64") -> rhd_params
     p.outer_rtol = float(prob.get("outer_rtol", 1e-13))
     p.newton_max_iter = int(prob.get("newton_max_iter", 64))
     p.outer_max_iter = int(prob.get("outer_max_iter", 32))
+    p.scheme = _SCHEME[prob.get("scheme", "imex")]
+    p.kappa_T_exp = float(prob.get("kappa_T_exp", 0.0))
+    p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
+    st = prob.get("bc_state", {})
+    for d in range(3):
+        for side in range(2):
+            v = st.get((d, side), (1.0, 0.0, 0.0, 0.0)) if isinstance(st, dict) else st[d][side]
+            for q in range(4):
+                p.bc_state[d][side][q] = float(v[q])
     return p
 
 
