@@ -441,10 +441,15 @@ def run_ours(args):
 
     forms = [args.precision] + [f for f in ("fp64", "mixed") if f != args.precision
                                 and not args.single_form]
+    if not args.single_form:
+        forms.append("fp64-rk2ssp")  # the paper's comparison scheme (Sec. 4.2)
     results = {}
     ctx = None
     for form in forms:
-        c, r = time_form(args, rhd, torch, prob, Ud, form, barrier, stream, local)
+        fprob, fprec = prob, form
+        if form == "fp64-rk2ssp":
+            fprob, fprec = dict(prob, scheme="rk2ssp"), "fp64"
+        c, r = time_form(args, rhd, torch, fprob, Ud, fprec, barrier, stream, local)
         r["ms"] = max_over_ranks(r["ms"])
         results[form] = r
         if form == args.precision:
