@@ -114,6 +114,11 @@ typedef struct {
   double kappa_T_exp;
   double kappa_T_ref;  /* reference temperature (> 0, default 1) */
   double bc_state[3][2][4]; /* INFLOW faces: ghost E, Fx, Fy, Fz (E > 0) */
+  /* non-grey material (eq. G0/G1): chi_0E = kappa rho (times the T factor
+   * above), chi_0P = kappa_P_ratio chi_0E, chi_0F = kappa_F_ratio chi_0E;
+   * both 1 (the default) is grey.  The TAU factor then uses chi_0F. */
+  double kappa_P_ratio;
+  double kappa_F_ratio;
 } rhd_params;
 
 typedef struct {
@@ -134,9 +139,9 @@ typedef struct {
 /* Fill p with the library defaults: periodic, gamma 5/3, c = chat = 1,
  * a_rad = kB_over_mu = 1, CFL 0.4, M1, v/c order 2, HLL TAU, FP64,
  * tolerances 1e-13, 64 Newton updates, 32 outer passes, IMEX PD-ARS,
- * temperature-independent opacity (kappa_T_exp 0, kappa_T_ref 1), inflow
- * states E = 1, F = 0.  The grid fields are zeroed; the caller sets ndim, n
- * and dx. */
+ * temperature-independent grey opacity (kappa_T_exp 0, kappa_T_ref 1,
+ * kappa_P_ratio = kappa_F_ratio = 1), inflow states E = 1, F = 0.  The grid
+ * fields are zeroed; the caller sets ndim, n and dx. */
 void rhd_params_default(rhd_params* p);
 
 /* Check p without touching the GPU.  Returns RHD_OK or RHD_ERR_ARG; on error

@@ -75,6 +75,8 @@ class OrcParams(ctypes.Structure):
         ("kappa_T_exp", ctypes.c_double),
         ("kappa_T_ref", ctypes.c_double),
         ("bc_state", ((ctypes.c_double * 4) * 2) * 3),
+        ("kappa_P_ratio", ctypes.c_double),
+        ("kappa_F_ratio", ctypes.c_double),
     ]
 
 
@@ -157,6 +159,8 @@ def make_params(prob: dict) -> OrcParams:
     p.scheme = _SCHEME[prob.get("scheme", "imex")]
     p.kappa_T_exp = float(prob.get("kappa_T_exp", 0.0))
     p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
+    p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
+    p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
     # bc_state[d][side] = (E, Fx, Fy, Fz) of inflow faces; default E = 1, F = 0
     st = prob.get("bc_state", {})
     for d in range(3):

@@ -165,7 +165,9 @@ static int hll_face(const orc_params* p, int d, const rad_cell* am,
    * width at the face, which is 1 when thin and 1/tau when thick. */
   double eps = 1.0;
   if (p->hll_mode == ORC_HLL_TAU) {
-    double tau = 0.5 * (a->chi + b->chi) * p->dx[d];
+    /* reading: the optical depth of the face is that of the flux-mean
+     * opacity chi_0F (= chi for grey material) */
+    double tau = 0.5 * (a->chi + b->chi) * p->dx[d] * p->kappa_F_ratio;
     if (tau > 0.0) eps = -expm1(-tau) / tau;
   }
   double phiL = (chat / c) * FL[d];
@@ -241,6 +243,8 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
   const double m0[3] = {y[1], y[2], y[3]};
   const double E0 = y[4];
   const double F0[3] = {y[5], y[6], y[7]};
+  const int order2 = p->vc_order == 2;
+  const double rP = p->kappa_P_ratio, rF = p->kappa_F_ratio;
   *n_newton = 0;
   *n_outer = 0;
 
@@ -258,15 +262,24 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
   double m[3] = {m0[0], m0[1], m0[2]};
   double F[3] = {F0[0], F0[1], F0[2]};
   double E = E0;
+  /* reading: the closure tensor D = P/E of the (v.v.P) term of eq. (Rnew) is
+   * frozen with v and F in the inner stage: that of the explicit state in
+   * the first pass, then the one of the previous pass's flux update */
+  double D[3][3];
+  orc_eddington_tensor(p, E0, F0, D);
 
   for (int outer = 0; outer < p->outer_max_iter; ++outer) {
     *n_outer = outer + 1;
-    /* v and F frozen for the inner stage */
+    /* v, F and D frozen for the inner stage */
     double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
     double beta2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / (c * c);
-    double g = (p->vc_order == 2) ? 1.0 + 0.5 * beta2 : 1.0;
+    double g = order2 ? 1.0 + 0.5 * beta2 : 1.0;
     double vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
     double Ekin = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho;
+    double vDv = 0.0; /* v_i D_ij v_j / c^2 */
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) vDv += v[i] * D[i][j] * v[j];
+    vDv /= c * c;
 
     /* ---- inner Newton-Raphson on (Egas, R) ---- */
     int converged = 0;
@@ -274,9 +287,14 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
       double T = (Eg - Ekin) / Cv;
       if (!(T > 0.0) || !isfinite(T) || !isfinite(R)) return ORC_ERR_NONPHYSICAL;
       double aT4 = a * T * T * T * T; /* 4 pi B / c */
-      double chi = chi_at(p, chi0, T); /* held fixed in the Jacobian below */
-      /* E as a function of (Egas, R): eq. (Rnew) solved for E */
-      double Ex = aT4 + (vF / (c * c)) / g - R / (chat * chi * tdt * g);
+      /* eq. (G0): chi_0E = chi, chi_0P = rP chi, chi_0F = rF chi, all at the
+       * current temperature and held fixed in the Jacobian below */
+      double chiE = chi_at(p, chi0, T), chiP = rP * chiE, chiF = rF * chiE;
+      /* E as a function of (Egas, R): eq. (Rnew) solved for E, with
+       * P = D E; order 1 keeps the O(v/c) terms only */
+      double num = chiP * aT4 * g + (2.0 * chiE - chiF) * vF / (c * c) - R / (chat * tdt);
+      double den = chiE * g - (order2 ? (chiF - chiE) * (beta2 + vDv) : 0.0);
+      double Ex = num / den;
       double FG = Eg - Eg0 + (c / chat) * R;
       double FR = Ex - E0 - R;
       if (fabs(FG / Etot) < eps && fabs((c / chat) * FR / Etot) < eps) {
@@ -284,11 +302,11 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
         break;
       }
       if (it >= p->newton_max_iter) break;
-      /* Jacobian of eq. (linear) */
+      /* Jacobian of eq. (linear), the paper's simplified form */
       double J00 = 1.0;
       double J01 = c / chat;
-      double J10 = 4.0 * a * T * T * T / Cv; /* (1/C_v) d(aT^4)/dT */
-      double J11 = -1.0 / (chat * chi * tdt) - 1.0;
+      double J10 = (chiP / chiE) * 4.0 * a * T * T * T / Cv; /* (1/C_v) d(chiP/chiE aT^4)/dT */
+      double J11 = -1.0 / (chat * chiE * tdt) - 1.0;
       double det = J00 * J11 - J01 * J10;
       double dEg = (-FG * J11 + FR * J01) / det;
       double dR = (-FR * J00 + FG * J10) / det;
@@ -306,38 +324,58 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
     /* ---- outer stage: flux and momentum ---- */
     double T = (Eg - Ekin) / Cv;
     double aT4 = a * T * T * T * T;
-    double chi = chi_at(p, chi0, T); /* the updated gas temperature's opacity */
-    double D[3][3];
+    double chiE = chi_at(p, chi0, T), chiP = rP * chiE, chiF = rF * chiE;
     orc_eddington_tensor(p, E, F, D); /* reading: P from the new E and the
                                          flux of the previous outer pass */
-    double Fn[3], mn[3];
+    double rhs[3];
     for (int i = 0; i < 3; ++i) {
       double vP = 0.0;
       for (int j = 0; j < 3; ++j) vP += v[j] * D[j][i] * E; /* v_j P_ji */
-      double num = F0[i] + chat * tdt * (chi * aT4 * v[i] + chi * vP);
-      double den = (p->vc_order == 2)
-                       ? 1.0 + chat * chi * (1.0 + beta2 / 2.0) * tdt /* (numF2) */
-                       : 1.0 + chat * chi * tdt;                      /* (numF1) */
-      Fn[i] = num / den;
-      mn[i] = m0[i] - (Fn[i] - F0[i]) / (c * chat); /* momentum update */
+      rhs[i] = F0[i] + chat * tdt * (chiP * aT4 * v[i] + chiF * vP + (chiF - chiE) * E * v[i]);
     }
+    double Fn[3], mn[3];
+    if (order2) {
+      /* eq. (fupdate) with eq. (G1) to O(v^2/c^2):
+       *   [(1 + chat theta dt chiF g) I + b v v^T] F = rhs,
+       *   b = 2 chat theta dt (chiF - chiE)/c^2 (zero for grey material,
+       *   eq. numF2), solved by the Sherman-Morrison formula */
+      double aa = 1.0 + chat * chiF * g * tdt;
+      double b = 2.0 * chat * tdt * (chiF - chiE) / (c * c);
+      double vr = v[0] * rhs[0] + v[1] * rhs[1] + v[2] * rhs[2];
+      double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+      double corr = b * vr / (aa + b * v2);
+      for (int i = 0; i < 3; ++i) Fn[i] = (rhs[i] - corr * v[i]) / aa;
+    } else {
+      for (int i = 0; i < 3; ++i) Fn[i] = rhs[i] / (1.0 + chat * chiF * tdt); /* (numF1) */
+    }
+    for (int i = 0; i < 3; ++i) mn[i] = m0[i] - (Fn[i] - F0[i]) / (c * chat); /* momentum */
 
-    /* reading: the "terms proportional to v and F in R" are
-     * Q = theta dt chat chi [(g - 1)(aT^4 - E) + v.F/c^2]; compare the Q the
-     * inner stage used with the Q of the updated v and F.  The relative change
-     * is also measured against the magnitude of those terms,
-     * Qs = theta dt chat chi [|(g - 1)(aT^4 - E)| + sum_i |v_i F_i|/c^2], so
-     * that a Q which is a cancelling sum cannot cycle at its rounding level. */
-    double Q_old = chat * chi * tdt * ((g - 1.0) * (aT4 - E) + vF / (c * c));
+    /* reading: the "terms proportional to v and F in R" of eq. (Rnew) are
+     *   Q = theta dt chat [(chiP aT^4 - chiE E)(g - 1) + (2 chiE - chiF) v.F/c^2
+     *                      + (chiF - chiE)(beta^2 + v.D.v/c^2) E]
+     * (order 1: the v.F term alone); compare the Q the inner stage used with
+     * the Q of the updated v and F (and the closure the next pass freezes).
+     * The change is also measured against the magnitude of the terms, Qs,
+     * so that a Q which is a cancelling sum cannot cycle at its rounding
+     * level. */
     double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
     double beta2n = (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]) / (c * c);
-    double gn = (p->vc_order == 2) ? 1.0 + 0.5 * beta2n : 1.0;
+    double gn = order2 ? 1.0 + 0.5 * beta2n : 1.0;
     double vFn = vn[0] * Fn[0] + vn[1] * Fn[1] + vn[2] * Fn[2];
-    double Q_new = chat * chi * tdt * ((gn - 1.0) * (aT4 - E) + vFn / (c * c));
-    double Q_scale = chat * chi * tdt *
-                     (fabs((gn - 1.0) * (aT4 - E)) +
-                      (fabs(vn[0] * Fn[0]) + fabs(vn[1] * Fn[1]) + fabs(vn[2] * Fn[2])) /
-                          (c * c));
+    double vDvn = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) vDvn += vn[i] * D[i][j] * vn[j];
+    vDvn /= c * c;
+    double k = chat * tdt;
+    double Q_old = k * ((chiP * aT4 - chiE * E) * (g - 1.0) + (2.0 * chiE - chiF) * vF / (c * c) +
+                        (order2 ? (chiF - chiE) * (beta2 + vDv) * E : 0.0));
+    double Q_new = k * ((chiP * aT4 - chiE * E) * (gn - 1.0) + (2.0 * chiE - chiF) * vFn / (c * c) +
+                        (order2 ? (chiF - chiE) * (beta2n + vDvn) * E : 0.0));
+    double Q_scale =
+        k * (fabs((chiP * aT4 - chiE * E) * (gn - 1.0)) +
+             fabs(2.0 * chiE - chiF) *
+                 (fabs(vn[0] * Fn[0]) + fabs(vn[1] * Fn[1]) + fabs(vn[2] * Fn[2])) / (c * c) +
+             (order2 ? fabs(chiF - chiE) * (beta2n + fabs(vDvn)) * E : 0.0));
 
     for (int i = 0; i < 3; ++i) {
       F[i] = Fn[i];

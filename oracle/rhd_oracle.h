@@ -61,6 +61,8 @@ typedef struct {
   double kappa_T_exp;     /* chi = kappa rho (T / kappa_T_ref)^kappa_T_exp */
   double kappa_T_ref;
   double bc_state[3][2][4]; /* ghost E, Fx, Fy, Fz of ORC_BC_INFLOW faces */
+  double kappa_P_ratio;   /* chi_0P / chi_0E (1: grey) */
+  double kappa_F_ratio;   /* chi_0F / chi_0E (1: grey) */
 } orc_params;
 
 typedef struct {

@@ -137,6 +137,8 @@ void rhd_params_default(rhd_params* p) {
   p->scheme = RHD_SCHEME_IMEX_PDARS;
   p->kappa_T_exp = 0.0;
   p->kappa_T_ref = 1.0;
+  p->kappa_P_ratio = 1.0;
+  p->kappa_F_ratio = 1.0;
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) {
       p->bc_state[d][s][0] = 1.0;
@@ -220,6 +222,10 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
   if (!std::isfinite(p->kappa_T_exp) || !(p->kappa_T_ref > 0.0) ||
       !std::isfinite(p->kappa_T_ref))
     return bad(msg, msglen, "kappa_T_exp must be finite and kappa_T_ref > 0"), RHD_ERR_ARG;
+  if (!(p->kappa_P_ratio > 0.0) || !std::isfinite(p->kappa_P_ratio) ||
+      !(p->kappa_F_ratio > 0.0) || !std::isfinite(p->kappa_F_ratio))
+    return bad(msg, msglen, "kappa_P_ratio and kappa_F_ratio must be positive"),
+           RHD_ERR_ARG;
   if (p->kappa_T_exp != 0.0 && p->hll_mode != RHD_HLL_NONE)
     return bad(msg, msglen, "a temperature-dependent opacity needs hll_mode NONE"),
            RHD_ERR_ARG;
@@ -273,6 +279,8 @@ void rhd::fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
   ph.scheme = p->scheme;
   ph.kappa_T_exp = p->kappa_T_exp;
   ph.inv_kappa_T_ref = 1.0 / p->kappa_T_ref;
+  ph.kappa_P_ratio = p->kappa_P_ratio;
+  ph.kappa_F_ratio = p->kappa_F_ratio;
 }
 
 static void release(rhd_ctx* c) {
@@ -522,7 +530,7 @@ rhd_status rhd_step_async(rhd_ctx* c, int nsteps, double dt) {
   CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
   c->launches += 1;
   if (c->p.hll_mode == RHD_HLL_TAU && c->eps_dirty) {
-    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->eps, c->stream));
+    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps, c->stream));
     c->launches += 1;
     c->eps_dirty = false;
   }
@@ -624,7 +632,7 @@ rhd_status rhd_transport(rhd_ctx* c, double* rates, int64_t count, int dst_on_de
   if (!dst_on_device) out = c->ybuf[c->cur ^ 1];  // the idle ping-pong buffer as staging
   CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
   if (c->p.hll_mode == RHD_HLL_TAU && c->eps_dirty) {
-    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->eps, c->stream));
+    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps, c->stream));
     c->launches += 1;
     c->eps_dirty = false;
   }
@@ -753,7 +761,7 @@ rhd_status rhd_step_record(rhd_ctx* c, int nsteps, double dt, double* tape, int6
   CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
   c->launches += 1;
   if (c->p.hll_mode == RHD_HLL_TAU && c->eps_dirty) {
-    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->eps, c->stream));
+    CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps, c->stream));
     c->launches += 1;
     c->eps_dirty = false;
   }
@@ -812,9 +820,11 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
     return fail(c, RHD_ERR_STATE, "rho and kappa must be set");
   if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
   if (!tape || !ybar || !kappa_bar) return fail(c, RHD_ERR_ARG, "a buffer is NULL");
-  if (c->p.scheme != RHD_SCHEME_IMEX_PDARS || c->p.kappa_T_exp != 0.0)
+  if (c->p.scheme != RHD_SCHEME_IMEX_PDARS || c->p.kappa_T_exp != 0.0 ||
+      c->p.kappa_P_ratio != 1.0 || c->p.kappa_F_ratio != 1.0)
     return fail(c, RHD_ERR_ARG,
-                "the adjoint covers the IMEX scheme with a temperature-independent opacity");
+                "the adjoint covers the IMEX scheme with a grey, temperature-independent "
+                "opacity");
   for (int d = 0; d < c->p.ndim; ++d)
     if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
       return fail(c, RHD_ERR_ARG, "the adjoint covers periodic and reflecting boundaries");

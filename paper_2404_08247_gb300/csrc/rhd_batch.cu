@@ -408,7 +408,8 @@ rhd_status rhd_batch_state_set(rhd_batch* b, int prob, const double* src, int64_
   if (b->desc[prob].ph.hll_mode == RHD_HLL_TAU) {
     double* eps[3] = {b->eps[0] + b->offsets[prob], b->eps[1] + b->offsets[prob], nullptr};
     BTRY(b, launch_tau_eps(b->desc[prob].g, batch_field(b, prob, RHD_F_RHO),
-                           batch_field(b, prob, RHD_F_KAPPA), eps, b->stream));
+                           batch_field(b, prob, RHD_F_KAPPA), b->desc[prob].ph.kappa_F_ratio,
+                           eps, b->stream));
   }
   BTRY(b, cudaMemcpyAsync(b->h_flag, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
                           b->stream));

@@ -56,6 +56,8 @@ struct Physics {
   int scheme;              // rhd_scheme
   double kappa_T_exp;      // chi = kappa rho (T / T_ref)^kappa_T_exp
   double inv_kappa_T_ref;  // 1 / T_ref
+  double kappa_P_ratio;    // chi_0P / chi_0E
+  double kappa_F_ratio;    // chi_0F / chi_0E
 };
 
 struct StageArgs {
@@ -495,6 +497,187 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
   return RHD_ERR_OUTER;
 }
 
+// Closure tensor D = P/E = dA I + dB Ft Ft^T of a state (E, Ft = F/c).
+__device__ __forceinline__ void closure_D(const Physics& ph, double E, const double Ft[3],
+                                          double& dA, double& dB) {
+  if (ph.closure == RHD_CLOSURE_EDDINGTON) {
+    dA = 1.0 / 3.0;
+    dB = 0.0;
+    return;
+  }
+  double ha, hb;
+  m1_coeffs(E, Ft, ha, hb);
+  const double iE = 1.0 / E;
+  dA = ha * iE;
+  dB = hb * iE;
+}
+
+// Implicit stage of one cell for non-grey material (general kernels only):
+// chi_0E = chi (times the T factor), chi_0P = rP chi_0E, chi_0F = rF chi_0E in
+// eq. (G0)/(G1).  The same inner/outer iteration as local_solve, with
+//   R = k [(rP a T^4 - E) g + (2 - rF) v.F/c^2 + (rF - 1)(beta^2 + v.D.v/c^2) E]
+// (k = chat chi_0E theta dt; the last term at order 2 only, with the closure
+// tensor D frozen like v and F: that of the explicit state, then the one of
+// the previous flux update), the R-row scaled by k' = k g - (kF - k)(beta^2 +
+// v.D.v/c^2), the paper's Jacobian ((chi_0P/chi_0E) 4aT^3/C_v, -1/k - 1), and
+// the flux from eq. (fupdate) with eq. (G1): at order 2
+//   [(1 + kF g) I + 2 (kF - k)/c^2 v v^T] F = F(t) + kP a T^4 v + kF v.P + (kF - k) E v,
+// solved by the Sherman-Morrison formula; at order 1 eq. (numF1).
+template <bool MIXED>
+__device__ int local_solve_nongrey(const Physics& ph, double tdt, double rho, double chi,
+                                   double y[8], int& nn, int& no) {
+  nn = 0;
+  no = 0;
+  if (chi == 0.0) return RHD_OK;
+  const double Cv = rho * ph.cv_spec;
+  const double inv_Cv = 1.0 / Cv, inv_rho = 1.0 / rho;
+  const double cr = ph.c_over_chat, a = ph.a_rad, ic2 = ph.inv_c2;
+  const double Eg0 = y[0], E0 = y[4];
+  const double tolG = ph.newton_rtol * (Eg0 + cr * E0);
+  const bool o2 = ph.vc_order == 2;
+  const bool vary = ph.kappa_T_exp != 0.0;
+  const double rP = ph.kappa_P_ratio, rF = ph.kappa_F_ratio;
+  const double k0 = ph.chat * chi * tdt;
+  double Eg = Eg0, R = 0.0, E = E0;
+  double m[3] = {y[1], y[2], y[3]};
+  double F[3] = {y[5], y[6], y[7]};
+  double v[3] = {m[0] * inv_rho, m[1] * inv_rho, m[2] * inv_rho};
+  double beta2 = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * ic2;
+  double g = o2 ? 1.0 + 0.5 * beta2 : 1.0;
+  double w = (v[0] * F[0] + v[1] * F[1] + v[2] * F[2]) * ic2;
+  double Ekin = 0.5 * (m[0] * v[0] + m[1] * v[1] + m[2] * v[2]);
+  double dA, dB, Fd[3] = {F[0] * ph.inv_c, F[1] * ph.inv_c, F[2] * ph.inv_c};
+  closure_D(ph, E0, Fd, dA, dB);
+  auto vdv_of = [&](const double vv[3]) {
+    double vf = vv[0] * Fd[0] + vv[1] * Fd[1] + vv[2] * Fd[2];
+    return (dA * (vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]) + dB * vf * vf) * ic2;
+  };
+  double vDv = vdv_of(v);
+  double kE = k0, kP = rP * k0, kF = rF * k0;
+  auto set_k = [&](double T) {
+    kE = vary ? k0 * pow(T * ph.inv_kappa_T_ref, ph.kappa_T_exp) : k0;
+    kP = rP * kE;
+    kF = rF * kE;
+  };
+  auto kprime = [&]() { return kE * g - (o2 ? (kF - kE) * (beta2 + vDv) : 0.0); };
+
+  {  // start from the frozen-opacity quartic A T^4 + C_v T = C (see quartic_start)
+    const double T0 = (Eg0 - Ekin) * inv_Cv;
+    if (pos_finite(T0)) {
+      set_k(T0);
+      const double kp = kprime();
+      if (kp > 0.0) {
+        const double inv1 = 1.0 / (1.0 + kp);
+        const double a4 = cr * kP * g * a * inv1 * inv_Cv;
+        const double rhs = T0 + cr * (kp * E0 - (2.0 * kE - kF) * w) * inv1 * inv_Cv;
+        double Tg;
+        if (pos_finite(rhs) && a4 > 0.0 && quartic_start(a4, rhs, T0, Tg)) {
+          Eg = Cv * Tg + Ekin;
+          R = -ph.chat_over_c * (Eg - Eg0);
+        }
+      }
+    }
+  }
+
+  for (int outer = 0; outer < ph.outer_max; ++outer) {
+    no = outer + 1;
+    bool conv = false;
+    double aT4 = 0.0, kp = 0.0;
+    for (int it = 0;; ++it) {
+      const double T = (Eg - Ekin) * inv_Cv;
+      if (!pos_finite(T) || !finite_bits(R)) return RHD_ERR_NONPHYSICAL;
+      set_k(T);
+      kp = kprime();
+      if (!(kp > 0.0)) return RHD_ERR_NONPHYSICAL;
+      const double T2 = T * T;
+      aT4 = a * T2 * T2;
+      const double Se = kP * aT4 * g + (2.0 * kE - kF) * w;
+      const double r0 = (Eg - Eg0) + cr * R;
+      const double r1 = Se - R - kp * (E0 + R);
+      if (fabs(r0) < tolG && cr * fabs(r1) <= tolG * kp) {
+        conv = true;
+        break;
+      }
+      if (it >= ph.newton_max) break;
+      const double J10 = kp * rP * 4.0 * a * T2 * T * inv_Cv;
+      const double gpk = kp / kE + kp;
+      const double det = -gpk - cr * J10;
+      const double inv_det = MIXED ? (double)(1.0f / (float)det) : 1.0 / det;
+      Eg += (r0 * gpk + cr * r1) * inv_det;
+      R += (r0 * J10 - r1) * inv_det;
+      ++nn;
+    }
+    if (!conv) return RHD_ERR_NEWTON;
+
+    E = E0 - ph.chat_over_c * (Eg - Eg0);  // energy closure
+    // closure at (E, F of the previous pass): P v for eq. (G1) and the tensor
+    // the next inner stage freezes
+    double Ft[3] = {F[0] * ph.inv_c, F[1] * ph.inv_c, F[2] * ph.inv_c};
+    closure_D(ph, E, Ft, dA, dB);
+    Fd[0] = Ft[0]; Fd[1] = Ft[1]; Fd[2] = Ft[2];
+    const double vFt = v[0] * Ft[0] + v[1] * Ft[1] + v[2] * Ft[2];
+    double rhs[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double vP = (dA * v[i] + dB * vFt * Ft[i]) * E;
+      rhs[i] = y[5 + i] + kP * aT4 * v[i] + kF * vP + (kF - kE) * E * v[i];
+    }
+    double Fn[3], mn[3];
+    if (o2) {
+      const double aa = 1.0 + kF * g;
+      const double b = 2.0 * (kF - kE) * ic2;
+      const double vr = v[0] * rhs[0] + v[1] * rhs[1] + v[2] * rhs[2];
+      const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+      const double corr = b * vr / (aa + b * v2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Fn[i] = (rhs[i] - corr * v[i]) / aa;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Fn[i] = rhs[i] / (1.0 + kF);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) mn[i] = y[1 + i] - (Fn[i] - y[5 + i]) * ph.inv_cchat;
+
+    const double Q_old = (kP * aT4 - kE * E) * (g - 1.0) + (2.0 * kE - kF) * w +
+                         (o2 ? (kF - kE) * (beta2 + vDv) * E : 0.0);
+    double vn[3] = {mn[0] * inv_rho, mn[1] * inv_rho, mn[2] * inv_rho};
+    const double beta2n = (vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]) * ic2;
+    const double gn = o2 ? 1.0 + 0.5 * beta2n : 1.0;
+    const double wn = (vn[0] * Fn[0] + vn[1] * Fn[1] + vn[2] * Fn[2]) * ic2;
+    const double vDvn = vdv_of(vn);
+    const double Q_new = (kP * aT4 - kE * E) * (gn - 1.0) + (2.0 * kE - kF) * wn +
+                         (o2 ? (kF - kE) * (beta2n + vDvn) * E : 0.0);
+    const double Q_scale =
+        fabs((kP * aT4 - kE * E) * (gn - 1.0)) +
+        fabs(2.0 * kE - kF) * (fabs(vn[0] * Fn[0]) + fabs(vn[1] * Fn[1]) + fabs(vn[2] * Fn[2])) *
+            ic2 +
+        (o2 ? fabs(kF - kE) * (beta2n + fabs(vDvn)) * E : 0.0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      F[i] = Fn[i];
+      m[i] = mn[i];
+      v[i] = vn[i];
+    }
+    beta2 = beta2n;
+    g = gn;
+    w = wn;
+    vDv = vDvn;
+    Ekin = 0.5 * (m[0] * v[0] + m[1] * v[1] + m[2] * v[2]);
+    const double dQ = fabs(Q_new - Q_old);
+    if (dQ <= ph.outer_rtol * fabs(Q_old) || dQ <= ph.outer_rtol * fabs(R) ||
+        dQ <= ph.outer_rtol * Q_scale) {
+      y[0] = Eg;
+      y[1] = m[0]; y[2] = m[1]; y[3] = m[2];
+      y[4] = E;
+      y[5] = F[0]; y[6] = F[1]; y[7] = F[2];
+      if (!pos_finite(E) || !finite_bits(F[0]) || !finite_bits(F[1]) || !finite_bits(F[2]))
+        return RHD_ERR_NONPHYSICAL;
+      return RHD_OK;
+    }
+  }
+  return RHD_ERR_OUTER;
+}
+
 // ------------------------------------------------------------ launchers
 // (host side, defined in the .cu files)
 cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s);
@@ -503,7 +686,7 @@ cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
                           double* partials, int npart, double* out4, cudaStream_t s);
 int totals_partials_needed();
 cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
-                           double* const eps[3], cudaStream_t s);
+                           double tau_scale, double* const eps[3], cudaStream_t s);
 cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
                                cudaStream_t s);
 // message returned by rhd_last_error(NULL) on this thread
@@ -513,7 +696,9 @@ void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph);
 // whether a grid needs the general kernels (RK2-SSP, a temperature-dependent
 // opacity or an inflow face) rather than the lean default ones
 inline bool needs_general(const Geometry& g, const Physics& ph) {
-  if (ph.scheme != RHD_SCHEME_IMEX_PDARS || ph.kappa_T_exp != 0.0) return true;
+  if (ph.scheme != RHD_SCHEME_IMEX_PDARS || ph.kappa_T_exp != 0.0 ||
+      ph.kappa_P_ratio != 1.0 || ph.kappa_F_ratio != 1.0)
+    return true;
   for (int d = 0; d < g.ndim; ++d)
     if (g.bc[d][0] == RHD_BC_INFLOW || g.bc[d][1] == RHD_BC_INFLOW) return true;
   return false;

@@ -42,10 +42,11 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
 
 // Optical-depth factors of every face (TAU mode): eps_d[i] belongs to the face
 // between cell i and its +d neighbour (periodic wrap, or the mirror of cell i
-// at a reflecting wall).  Depends on the static rho and kappa only.
+// at a reflecting wall).  Depends on the static rho and kappa only; tau_scale
+// is chi_0F / chi_0E (the face depth is that of the flux-mean opacity).
 __global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
-                               const double* __restrict__ kappa, double* e0, double* e1,
-                               double* e2) {
+                               const double* __restrict__ kappa, double tau_scale, double* e0,
+                               double* e1, double* e2) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell) return;
   int c[3];
@@ -60,14 +61,14 @@ __global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
     int xb = fold(c[d] + 1, g.n[d], g.bc[d][0], g.bc[d][1], flip);
     int nb = idx + (xb - c[d]) * g.stride[d];
     double tau = 0.5 * (chi_a + kappa[nb] * rho[nb]) * g.dx[d];
-    out[d][idx] = tau_factor(tau);
+    out[d][idx] = tau_factor(tau * tau_scale);
   }
 }
 
 cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
-                           double* const eps[3], cudaStream_t s) {
+                           double tau_scale, double* const eps[3], cudaStream_t s) {
   int blocks = (g.ncell + 255) / 256;
-  tau_eps_kernel<<<blocks, 256, 0, s>>>(g, rho, kappa, eps[0], eps[1], eps[2]);
+  tau_eps_kernel<<<blocks, 256, 0, s>>>(g, rho, kappa, tau_scale, eps[0], eps[1], eps[2]);
   return cudaGetLastError();
 }
 

@@ -83,9 +83,10 @@ __device__ __forceinline__ int inflow_side(const Geometry& g, int d, int x) {
   return -1;
 }
 
+// optical depth of the face from the flux-mean opacity chi_0F
 __device__ __forceinline__ double eps_direct(const StageArgs& A, int ia, int ib, int d) {
   double tau = 0.5 * (A.kappa[ia] * A.rho[ia] + A.kappa[ib] * A.rho[ib]) * A.g.dx[d];
-  return tau_factor(tau);
+  return tau_factor(tau * A.ph.kappa_F_ratio);
 }
 
 // Optical-depth factor of the face on the +d side of the cell c (c[d] may be
@@ -372,9 +373,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       if (STAGE != 0) {
         if (bad)
           code = RHD_ERR_NONPHYSICAL;
-        else if (!(rk2 && STAGE == 1))
-          code = local_solve<MIXED, GEN>(ph, (STAGE == 1 || rk2) ? A.dt : 0.5 * A.dt, rho, chi, y,
-                                    nn, no);
+        else if (!(rk2 && STAGE == 1)) {
+          const double tdt = (STAGE == 1 || rk2) ? A.dt : 0.5 * A.dt;
+          if (GEN && (ph.kappa_P_ratio != 1.0 || ph.kappa_F_ratio != 1.0))
+            code = local_solve_nongrey<MIXED>(ph, tdt, rho, chi, y, nn, no);
+          else
+            code = local_solve<MIXED, GEN>(ph, tdt, rho, chi, y, nn, no);
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
       }

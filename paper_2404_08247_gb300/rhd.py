@@ -68,6 +68,8 @@ class rhd_params(ctypes.Structure):
         ("kappa_T_exp", ctypes.c_double),
         ("kappa_T_ref", ctypes.c_double),
         ("bc_state", ((ctypes.c_double * 4) * 2) * 3),
+        ("kappa_P_ratio", ctypes.c_double),
+        ("kappa_F_ratio", ctypes.c_double),
     ]
 
 
@@ -216,6 +218,8 @@ def params_from_problem(prob: dict, precision: str | int = "fp64") -> rhd_params
     p.scheme = _SCHEME[prob.get("scheme", "imex")]
     p.kappa_T_exp = float(prob.get("kappa_T_exp", 0.0))
     p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
+    p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
+    p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
     st = prob.get("bc_state", {})
     for d in range(3):
         for side in range(2):

@@ -85,6 +85,34 @@ def test_schemes_opacity_and_inflow_match_oracle(R, oracle_mod, ndim, n, scheme,
     assert_parity(Ug, Uo, TOL, str(kw))
 
 
+NONGREY = [
+    # ndim, n, (rP, rF), order, hll, kappa_T_exp
+    (1, (200,), (0.5, 0.3), 2, "tau", 0.0),
+    (2, (30, 17), (3.0, 1.5), 2, "none", 0.0),
+    (3, (10, 9, 8), (1.0, 4.0), 2, "tau", 0.0),
+    (2, (24, 20), (0.5, 0.3), 1, "tau", 0.0),
+    (3, (9, 8, 7), (3.0, 1.5), 1, "none", -3.0),
+    (1, (130,), (2.0, 0.7), 2, "none", -3.0),
+]
+
+
+@pytest.mark.parametrize("ndim,n,ratios,order,hll,pexp", NONGREY)
+def test_nongrey_opacities_match_oracle(R, oracle_mod, ndim, n, ratios, order, hll, pexp):
+    """chi_0P = rP chi_0E, chi_0F = rF chi_0E (eq. G0/G1, the 3x3 flux update at
+    O(v^2/c^2)), with v up to 1e-2 c, against the oracle to 1e-11."""
+    ci = NONGREY.index((ndim, n, ratios, order, hll, pexp))
+    prob = I.base_problem(ndim, n, tuple(1.0 / v for v in n), c=1e3, chat=[1e3, 2e2][ci % 2],
+                          kappa_P_ratio=ratios[0], kappa_F_ratio=ratios[1], vc_order=order,
+                          hll_mode=hll, kappa_T_exp=pexp, kappa_T_ref=1.5,
+                          bc="reflect" if ci % 3 == 0 else "periodic",
+                          newton_max_iter=400, outer_max_iter=200)
+    U = I.random_state(prob, seed=700 + ci, tau_range=(1e-2, 1e2), beta_max=1e-2)
+    Ug, info = run_gpu(R, prob, U, 5)
+    Uo = run_oracle(oracle_mod, prob, U, 5)
+    assert info["steps_done"] == 5
+    assert_parity(Ug, Uo, TOL, str(ratios))
+
+
 def test_rk2ssp_solves_once_per_step(R):
     prob = I.base_problem(2, (20, 16), (1 / 20, 1 / 16), c=1e3, chat=1e2, scheme="rk2ssp")
     U = I.random_state(prob, seed=9)
