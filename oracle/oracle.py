@@ -77,6 +77,7 @@ class OrcParams(ctypes.Structure):
         ("bc_state", ((ctypes.c_double * 4) * 2) * 3),
         ("kappa_P_ratio", ctypes.c_double),
         ("kappa_F_ratio", ctypes.c_double),
+        ("reconstruction", ctypes.c_int),
     ]
 
 
@@ -161,6 +162,7 @@ def make_params(prob: dict) -> OrcParams:
     p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
     p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
     p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
+    p.reconstruction = {"plm": 0, "ppm": 1}[prob.get("reconstruction", "plm")]
     # bc_state[d][side] = (E, Fx, Fy, Fz) of inflow faces; default E = 1, F = 0
     st = prob.get("bc_state", {})
     for d in range(3):

@@ -102,6 +102,10 @@ static rad_cell fetch(const orc_params* p, const double* U, const long long ic[3
       flip = 1;
     }
   }
+  /* a mirror deeper than the axis (only for stencil cells that the
+   * reconstruction in use does not read, e.g. PLM's outermost pair) */
+  if (x < 0) x = 0;
+  if (x >= nd) x = nd - 1;
   q[d] = x;
   long long N = ncell_of(p);
   long long idx = q[0] + p->n[0] * (q[1] + p->n[1] * q[2]);
@@ -121,22 +125,76 @@ static rad_cell fetch(const orc_params* p, const double* U, const long long ic[3
   return r;
 }
 
-/* HLL flux through the face between cells a and b along axis d, for the RSLA
- * transport system of eq. (yrsla): conserved (E, F/(c chat)) with fluxes
- * ((chat/c) F_d, P_d.).  Face states: PLM from the 4-cell stencil
- * (am, a | b, bp).  out[0] = energy flux, out[1..3] = flux of F/(c chat). */
-static int hll_face(const orc_params* p, int d, const rad_cell* am,
-                    const rad_cell* a, const rad_cell* b, const rad_cell* bp,
-                    double out[4]) {
-  const double c = p->c, chat = p->chat;
-  /* left state: cell a + half its slope; right state: cell b - half its slope */
-  double EL = a->E + 0.5 * mc_slope(am->E, a->E, b->E);
-  double ER = b->E - 0.5 * mc_slope(a->E, b->E, bp->E);
-  double FL[3], FR[3];
+/* PPM interface value between cells j and j+1 (Colella & Woodward 1984,
+ * uniform zones): (u_j + u_{j+1})/2 - (dm_{j+1} - dm_j)/6 with dm the
+ * MC-limited slopes; from u_{j-1} .. u_{j+2}. */
+static double ppm_interface(double um, double u0, double up, double upp) {
+  return 0.5 * (u0 + up) - (mc_slope(u0, up, upp) - mc_slope(um, u0, up)) / 6.0;
+}
+
+/* PPM edge values (aL, aR) of cell j from u_{j-2} .. u_{j+2}, made monotone
+ * (Colella & Woodward 1984): a cell at an extremum is flat, and an edge value
+ * that would put an extremum of the parabola inside the cell is moved. */
+static void ppm_edges(const double u[5], double* aL, double* aR) {
+  double l = ppm_interface(u[0], u[1], u[2], u[3]);
+  double r = ppm_interface(u[1], u[2], u[3], u[4]);
+  double u0 = u[2];
+  if ((r - u0) * (u0 - l) <= 0.0) {
+    l = r = u0;
+  } else {
+    double dd = r - l, m6 = 6.0 * (u0 - 0.5 * (l + r));
+    if (dd * m6 > dd * dd)
+      l = 3.0 * u0 - 2.0 * r;
+    else if (-dd * dd > dd * m6)
+      r = 3.0 * u0 - 2.0 * l;
+  }
+  *aL = l;
+  *aR = r;
+}
+
+/* Face states of the face between s[2] and s[3] along axis d from the
+ * stencil s[0..5] (cells i-2 .. i+3): E and F.
+ *   PLM (reading: Sec. 3.3 uses PPM; PLM with the monotonised-central
+ *   limiter is the default): cell a + half its slope | cell b - half its
+ *   slope, from s[1..4];
+ *   PPM: the right edge value of s[2] | the left edge value of s[3]. */
+static void face_states(const orc_params* p, const rad_cell* s, double* EL, double FL[3],
+                        double* ER, double FR[3]) {
+  if (p->reconstruction == ORC_RECON_PPM) {
+    double u[6], l, r;
+    for (int q = 0; q < 4; ++q) {
+      for (int k = 0; k < 6; ++k) u[k] = q == 0 ? s[k].E : s[k].F[q - 1];
+      ppm_edges(u, &l, &r);       /* cell s[2] */
+      double left = r;
+      ppm_edges(u + 1, &l, &r);   /* cell s[3] */
+      if (q == 0) {
+        *EL = left;
+        *ER = l;
+      } else {
+        FL[q - 1] = left;
+        FR[q - 1] = l;
+      }
+    }
+    return;
+  }
+  const rad_cell *am = &s[1], *a = &s[2], *b = &s[3], *bp = &s[4];
+  *EL = a->E + 0.5 * mc_slope(am->E, a->E, b->E);
+  *ER = b->E - 0.5 * mc_slope(a->E, b->E, bp->E);
   for (int j = 0; j < 3; ++j) {
     FL[j] = a->F[j] + 0.5 * mc_slope(am->F[j], a->F[j], b->F[j]);
     FR[j] = b->F[j] - 0.5 * mc_slope(a->F[j], b->F[j], bp->F[j]);
   }
+}
+
+/* HLL flux through the face between cells s[2] and s[3] along axis d, for
+ * the RSLA transport system of eq. (yrsla): conserved (E, F/(c chat)) with
+ * fluxes ((chat/c) F_d, P_d.).  out[0] = energy flux, out[1..3] = flux of
+ * F/(c chat). */
+static int hll_face(const orc_params* p, int d, const rad_cell* s, double out[4]) {
+  const double c = p->c, chat = p->chat;
+  const rad_cell *a = &s[2], *b = &s[3];
+  double EL = 0.0, ER = 0.0, FL[3], FR[3];
+  face_states(p, s, &EL, FL, &ER, FR);
   if (!(EL > 0.0) || !(ER > 0.0)) return ORC_ERR_NONPHYSICAL;
   /* reading: a reconstructed face flux above the free-streaming limit
    * |F| <= c E is scaled back onto that limit. */
@@ -196,12 +254,11 @@ int orc_transport(const orc_params* p, const double* U, double* rate,
         for (long long i0 = 0; i0 < p->n[0]; ++i0) {
           long long ic[3] = {i0, i1, i2};
           long long idx = i0 + p->n[0] * (i1 + p->n[1] * i2);
-          rad_cell s[5];
-          for (int o = -2; o <= 2; ++o) s[o + 2] = fetch(p, U, ic, d, o);
+          rad_cell s[7];
+          for (int o = -3; o <= 3; ++o) s[o + 3] = fetch(p, U, ic, d, o);
           double lo[4], hi[4];
-          /* face i-1/2: cells (i-2, i-1 | i, i+1); face i+1/2: (i-1, i | i+1, i+2) */
-          if (hll_face(p, d, &s[0], &s[1], &s[2], &s[3], lo) != ORC_OK ||
-              hll_face(p, d, &s[1], &s[2], &s[3], &s[4], hi) != ORC_OK) {
+          /* face i-1/2: stencil cells i-3 .. i+2; face i+1/2: i-2 .. i+3 */
+          if (hll_face(p, d, &s[0], lo) != ORC_OK || hll_face(p, d, &s[1], hi) != ORC_OK) {
             if (fail_cell) *fail_cell = idx;
             return ORC_ERR_NONPHYSICAL;
           }

@@ -33,6 +33,7 @@ enum { ORC_RHO = 0, ORC_MX, ORC_MY, ORC_MZ, ORC_EGAS, ORC_ERAD, ORC_FX, ORC_FY,
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_REFLECT = 1, ORC_BC_INFLOW = 2 };
 enum { ORC_SCHEME_IMEX = 0, ORC_SCHEME_RK2_SSP = 1 };
+enum { ORC_RECON_PLM = 0, ORC_RECON_PPM = 1 };
 enum { ORC_CLOSURE_M1 = 0, ORC_CLOSURE_EDDINGTON = 1 };
 enum { ORC_HLL_TAU = 0, ORC_HLL_NONE = 1 };
 
@@ -63,6 +64,7 @@ typedef struct {
   double bc_state[3][2][4]; /* ghost E, Fx, Fy, Fz of ORC_BC_INFLOW faces */
   double kappa_P_ratio;   /* chi_0P / chi_0E (1: grey) */
   double kappa_F_ratio;   /* chi_0F / chi_0E (1: grey) */
+  int reconstruction;     /* ORC_RECON_*: face states of the transport */
 } orc_params;
 
 typedef struct {
