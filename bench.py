@@ -443,12 +443,15 @@ def run_ours(args):
                                 and not args.single_form]
     if not args.single_form:
         forms.append("fp64-rk2ssp")  # the paper's comparison scheme (Sec. 4.2)
+        forms += ["fp64-ppm", "mixed-ppm"]  # the paper's PPM faces (Sec. 3.3)
     results = {}
     ctx = None
     for form in forms:
         fprob, fprec = prob, form
         if form == "fp64-rk2ssp":
             fprob, fprec = dict(prob, scheme="rk2ssp"), "fp64"
+        elif form.endswith("-ppm"):
+            fprob, fprec = dict(prob, reconstruction="ppm"), form[:-4]
         c, r = time_form(args, rhd, torch, fprob, Ud, fprec, barrier, stream, local)
         r["ms"] = max_over_ranks(r["ms"])
         results[form] = r

@@ -67,6 +67,15 @@ typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_REFLECT = 1, RHD_BC_INFLOW = 2 } rhd_
  * asymptotic diffusion limit, which it does not preserve. */
 typedef enum { RHD_SCHEME_IMEX_PDARS = 0, RHD_SCHEME_RK2_SSP = 1 } rhd_scheme;
 typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_EDDINGTON = 1 } rhd_closure;
+/* Face states of E and F (Sec. 3.3).  PLM: linear with the monotonised-
+ * central limiter (the default).  PPM: the paper's choice, the piecewise
+ * parabolic edge values of Colella & Woodward (1984) -- fourth-order
+ * interface values from limited slopes, then their monotonicity constraint
+ * per cell -- without contact steepening or flattening.  PPM reads three
+ * cells on each side of a face, so a reflecting or inflow axis needs n >= 3;
+ * a forward-Euler transport stage keeps E > 0 for CFL <= 1/3 with PPM (1/2
+ * with PLM).  The batched form and rhd_adjoint take PLM only. */
+typedef enum { RHD_RECON_PLM = 0, RHD_RECON_PPM = 1 } rhd_recon;
 /* HLL energy-flux dissipation (Sec. 4.3): TAU scales it by
  * (1 - exp(-tau))/tau, tau = chi dx of the face; NONE is the paper's own
  * uncorrected IMEX choice. */
@@ -119,6 +128,7 @@ typedef struct {
    * both 1 (the default) is grey.  The TAU factor then uses chi_0F. */
   double kappa_P_ratio;
   double kappa_F_ratio;
+  int reconstruction; /* rhd_recon */
 } rhd_params;
 
 typedef struct {
@@ -140,7 +150,7 @@ typedef struct {
  * a_rad = kB_over_mu = 1, CFL 0.4, M1, v/c order 2, HLL TAU, FP64,
  * tolerances 1e-13, 64 Newton updates, 32 outer passes, IMEX PD-ARS,
  * temperature-independent grey opacity (kappa_T_exp 0, kappa_T_ref 1,
- * kappa_P_ratio = kappa_F_ratio = 1), inflow states E = 1, F = 0.  The grid
+ * kappa_P_ratio = kappa_F_ratio = 1), inflow states E = 1, F = 0, PLM faces.  The grid
  * fields are zeroed; the caller sets ndim, n and dx. */
 void rhd_params_default(rhd_params* p);
 
@@ -257,8 +267,10 @@ rhd_status rhd_step_record(rhd_ctx* ctx, int nsteps, double dt, double* tape,
  * branch of every limiter, maximum and clip; the implicit part applies the
  * implicit-function theorem to the converged local solve of eq.
  * (egupdate)-(fupdate).  The first call allocates 8*ncell + 18*(faces)
- * doubles of scratch that the context keeps.  Returns RHD_ERR_NEWTON if the
- * Jacobian of a converged solve is singular.  Synchronises. */
+ * doubles of scratch that the context keeps.  Returns RHD_ERR_ARG for a
+ * context with RK2-SSP, a temperature-dependent or non-grey opacity, an
+ * inflow face or PPM faces, and RHD_ERR_NEWTON if the Jacobian of a
+ * converged solve is singular.  Synchronises. */
 rhd_status rhd_adjoint(rhd_ctx* ctx, const double* tape, int64_t count, int nsteps,
                        double dt, double* ybar, double* kappa_bar);
 
@@ -287,8 +299,8 @@ void rhd_destroy(rhd_ctx* ctx);
  * ------------------------------------------------------------------- */
 typedef struct rhd_batch rhd_batch;
 
-/* Validate and allocate nprob problems (probs[p].ndim must be 1 or 2, one
- * precision for all).  *out is NULL on error (message: rhd_last_error(NULL)). */
+/* Validate and allocate nprob problems (probs[p].ndim must be 1 or 2, PLM
+ * faces, one precision for all).  *out is NULL on error (message: rhd_last_error(NULL)). */
 rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out);
 
 /* Run on this CUDA stream (drops the captured graphs).  The legacy default

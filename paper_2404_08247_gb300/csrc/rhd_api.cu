@@ -139,6 +139,7 @@ void rhd_params_default(rhd_params* p) {
   p->kappa_T_ref = 1.0;
   p->kappa_P_ratio = 1.0;
   p->kappa_F_ratio = 1.0;
+  p->reconstruction = RHD_RECON_PLM;
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) {
       p->bc_state[d][s][0] = 1.0;
@@ -226,6 +227,13 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
       !(p->kappa_F_ratio > 0.0) || !std::isfinite(p->kappa_F_ratio))
     return bad(msg, msglen, "kappa_P_ratio and kappa_F_ratio must be positive"),
            RHD_ERR_ARG;
+  if (p->reconstruction != RHD_RECON_PLM && p->reconstruction != RHD_RECON_PPM)
+    return bad(msg, msglen, "reconstruction is not an rhd_recon"), RHD_ERR_ARG;
+  if (p->reconstruction == RHD_RECON_PPM)
+    for (int d = 0; d < p->ndim; ++d)
+      if (p->bc[d][0] != RHD_BC_PERIODIC && p->n[d] < 3)
+        return bad(msg, msglen, "PPM on a reflecting or inflow axis %d needs n >= 3", d),
+               RHD_ERR_ARG;
   if (p->kappa_T_exp != 0.0 && p->hll_mode != RHD_HLL_NONE)
     return bad(msg, msglen, "a temperature-dependent opacity needs hll_mode NONE"),
            RHD_ERR_ARG;
@@ -281,6 +289,7 @@ void rhd::fill_geometry(const rhd_params* p, Geometry& g, Physics& ph) {
   ph.inv_kappa_T_ref = 1.0 / p->kappa_T_ref;
   ph.kappa_P_ratio = p->kappa_P_ratio;
   ph.kappa_F_ratio = p->kappa_F_ratio;
+  ph.reconstruction = p->reconstruction;
 }
 
 static void release(rhd_ctx* c) {
@@ -828,6 +837,8 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
   for (int d = 0; d < c->p.ndim; ++d)
     if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
       return fail(c, RHD_ERR_ARG, "the adjoint covers periodic and reflecting boundaries");
+  if (c->p.reconstruction != RHD_RECON_PLM)
+    return fail(c, RHD_ERR_ARG, "the adjoint covers PLM faces");
   const size_t N = (size_t)c->ncell;
   const size_t S = NY * N;
   if (count != (int64_t)((2 * (size_t)nsteps + 1) * S))

@@ -277,6 +277,8 @@ rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out) {
       return bfail(nullptr, RHD_ERR_ARG, "problem %d: %s", p, msg);
     if (probs[p].ndim > 2)
       return bfail(nullptr, RHD_ERR_ARG, "problem %d: the batch takes 1-D and 2-D grids", p);
+    if (probs[p].reconstruction != RHD_RECON_PLM)
+      return bfail(nullptr, RHD_ERR_ARG, "problem %d: the batch takes PLM faces", p);
     if (probs[p].precision != probs[0].precision)
       return bfail(nullptr, RHD_ERR_ARG, "problem %d: all problems share one precision", p);
   }

@@ -58,6 +58,7 @@ struct Physics {
   double inv_kappa_T_ref;  // 1 / T_ref
   double kappa_P_ratio;    // chi_0P / chi_0E
   double kappa_F_ratio;    // chi_0F / chi_0E
+  int reconstruction;      // rhd_recon
 };
 
 struct StageArgs {
@@ -168,6 +169,68 @@ __device__ __forceinline__ double half_slope<double>(double um, double u0, doubl
   long long m = min(min(am, ap), abs_bits(q));
   bool take = ((bm ^ bp) >= 0) & (am != 0) & (ap != 0);  // same sign, both nonzero
   return __longlong_as_double(take ? (m | (bm & ~kMag)) : 0ll);
+}
+
+// ---------------------------------------------------------------- PPM
+// Piecewise parabolic face states (Colella & Woodward 1984, the paper's
+// reconstruction in Sec. 3.3) written with half slopes h = dm/2 of the
+// limiter above.  Interface value between cells u0 and up (their eq. 1.6 with
+// the limited slopes of eq. 1.8): (u0 + up)/2 - (dm(up) - dm(u0))/6
+// = (u0 + up)/2 - (h1 - h0)/3; it lies between u0 and up.
+template <typename R>
+__device__ __forceinline__ R ppm_interface(R u0, R up, R h0, R h1) {
+  return R(0.5) * (u0 + up) - (h1 - h0) * R(1.0 / 3.0);
+}
+
+// Their monotonicity constraint (eq. 1.10) on the edge values (l, r) of a
+// cell of mean u0.  With dl = u0 - l and dr = r - u0: at a local extremum
+// (dl dr <= 0) the cell is flat; otherwise the parabola is monotone in the
+// cell iff |dl| <= 2|dr| and |dr| <= 2|dl| (its two tests, dd m6 > dd^2 and
+// -dd^2 > dd m6 with dd = dl + dr and m6 = 3 (dl - dr), divided through by
+// dd), and an edge beyond that is moved onto it: |dl| <- min(|dl|, 2|dr|),
+// |dr| <- min(|dr|, 2|dl|), signs kept.  The constraint is continuous where
+// its branches meet, so a tie decided either way changes an edge by
+// rounding only.  Returned: the constrained left edge (LEFT) or right edge.
+template <bool LEFT, typename R>
+__device__ __forceinline__ R ppm_edge(R u0, R l, R r) {
+  const R dl = u0 - l, dr = r - u0;
+  if (!(dl * dr > R(0))) return u0;
+  const R a = LEFT ? dl : dr, b = LEFT ? dr : dl;  // the moved side, the other
+  const R m = fmin(fabs(a), R(2) * fabs(b));
+  return LEFT ? u0 - copysign(m, a) : u0 + copysign(m, a);
+}
+
+// double: the sign tests and minima on the integer pipe (non-negative doubles
+// order as their bit patterns; 2|b| = |b + b| exactly)
+template <bool LEFT>
+__device__ __forceinline__ double ppm_edge_d(double u0, double l, double r) {
+  const double dl = u0 - l, dr = r - u0;
+  const double a = LEFT ? dl : dr, b = LEFT ? dr : dl;
+  const long long ba = dbits(a), bb = dbits(b);
+  const long long ma = ba & kMag, mb = bb & kMag;
+  const bool mono = ((ba ^ bb) >= 0) & (ma != 0) & (mb != 0);
+  const long long m = min(ma, abs_bits(b + b));
+  const double s = __longlong_as_double(mono ? (m | (ba & ~kMag)) : 0ll);
+  return LEFT ? u0 - s : u0 + s;
+}
+
+// States of the face between u[2] and u[3] from cells u[0..5] (the face's
+// three cells on each side): the constrained right edge of u[2] | the
+// constrained left edge of u[3].
+template <typename R>
+__device__ __forceinline__ void ppm_face(const R u[6], R& L, R& Rr) {
+  const R h1 = half_slope(u[0], u[1], u[2]), h2 = half_slope(u[1], u[2], u[3]);
+  const R h3 = half_slope(u[2], u[3], u[4]), h4 = half_slope(u[3], u[4], u[5]);
+  const R a12 = ppm_interface(u[1], u[2], h1, h2);
+  const R a23 = ppm_interface(u[2], u[3], h2, h3);
+  const R a34 = ppm_interface(u[3], u[4], h3, h4);
+  if constexpr (sizeof(R) == sizeof(double)) {
+    L = ppm_edge_d<false>(u[2], a12, a23);
+    Rr = ppm_edge_d<true>(u[3], a23, a34);
+  } else {
+    L = ppm_edge<false>(u[2], a12, a23);
+    Rr = ppm_edge<true>(u[3], a23, a34);
+  }
 }
 
 // ---------------------------------------------------------------- closure
@@ -681,6 +744,7 @@ __device__ int local_solve_nongrey(const Physics& ph, double tdt, double rho, do
 // ------------------------------------------------------------ launchers
 // (host side, defined in the .cu files)
 cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s);
+cudaError_t launch_stage_ppm(int stage, int precision, const StageArgs& A, cudaStream_t s);
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
 cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
                           double* partials, int npart, double* out4, cudaStream_t s);
@@ -697,6 +761,7 @@ void fill_geometry(const rhd_params* p, Geometry& g, Physics& ph);
 // opacity or an inflow face) rather than the lean default ones
 inline bool needs_general(const Geometry& g, const Physics& ph) {
   if (ph.scheme != RHD_SCHEME_IMEX_PDARS || ph.kappa_T_exp != 0.0 ||
+      ph.reconstruction != RHD_RECON_PLM ||
       ph.kappa_P_ratio != 1.0 || ph.kappa_F_ratio != 1.0)
     return true;
   for (int d = 0; d < g.ndim; ++d)

@@ -5,24 +5,10 @@
 //                       y(n+1) = y** + (dt/2) f(y(n+1))
 // The stage-2 explicit state is eq. (imex2) with dt f(y(n+1/2)) replaced by
 // y(n+1/2) - y*, which eq. (imex1) makes exact.  One block per tile; the tile
-// body is stage_tile (rhd_tile.cuh).
-#include "rhd_tile.cuh"
+// body is stage_tile (rhd_tile.cuh), the kernel stage_kernel (rhd_stage.cuh).
+#include "rhd_stage.cuh"
 
 namespace rhd {
-
-template <int STAGE, int NDIM, typename R, bool GEN>
-__global__ void __launch_bounds__(Tile<NDIM>::NT, 2) stage_kernel(const StageArgs A) {
-  using T = Tile<NDIM>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = (A.st->fail_key != ~0ull) ? 1 : 0;
-  __syncthreads();
-  if (s_skip) return;  // a previous launch of this batch failed
-  TileStats ts;
-  stage_tile<STAGE, T, R, GEN>(A, blockIdx.x * T::TX, blockIdx.y * T::TY, blockIdx.z * T::LZ,
-                          smem_raw, ts);
-  flush_stats<T::NT>(A.st, ts);
-}
 
 __global__ void status_reset_kernel(DevStatus* st) {
   st->fail_key = ~0ull;
@@ -72,38 +58,18 @@ cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* k
   return cudaGetLastError();
 }
 
-template <int STAGE, int NDIM, typename R, bool GEN>
-static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s) {
-  using T = Tile<NDIM>;
-  using S = SmemT<T, R>;
-  // opt in to more than 48 KiB of dynamic shared memory (idempotent)
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<STAGE, NDIM, R, GEN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)S::BYTES);
-  if (e != cudaSuccess) return e;
-  dim3 grid((A.g.n[0] + T::TX - 1) / T::TX, (A.g.n[1] + T::TY - 1) / T::TY,
-            (A.g.n[2] + T::LZ - 1) / T::LZ);
-  stage_kernel<STAGE, NDIM, R, GEN><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
-  return cudaGetLastError();
-}
-
-template <int STAGE, typename R, bool GEN>
-static cudaError_t launch_prec(const StageArgs& A, cudaStream_t s) {
-  switch (A.g.ndim) {
-    case 1: return launch_nd<STAGE, 1, R, GEN>(A, s);
-    case 2: return launch_nd<STAGE, 2, R, GEN>(A, s);
-    default: return launch_nd<STAGE, 3, R, GEN>(A, s);
-  }
-}
-
 // The lean kernels (GEN = false) serve the default physics; RK2-SSP, a
-// temperature-dependent opacity or an inflow face select the general ones.
+// temperature-dependent or non-grey opacity or an inflow face select the
+// general ones; PPM faces the PPM unit's (general physics, wider halo).
 template <int STAGE>
 static cudaError_t launch_stage_t(int precision, const StageArgs& A, cudaStream_t s) {
+  if (A.ph.reconstruction == RHD_RECON_PPM) return launch_stage_ppm(STAGE, precision, A, s);
   const bool gen = needs_general(A.g, A.ph);
   if (precision == RHD_PREC_MIXED)
-    return gen ? launch_prec<STAGE, float, true>(A, s) : launch_prec<STAGE, float, false>(A, s);
-  return gen ? launch_prec<STAGE, double, true>(A, s) : launch_prec<STAGE, double, false>(A, s);
+    return gen ? launch_prec<STAGE, float, true, false>(A, s)
+               : launch_prec<STAGE, float, false, false>(A, s);
+  return gen ? launch_prec<STAGE, double, true, false>(A, s)
+             : launch_prec<STAGE, double, false, false>(A, s);
 }
 
 cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s) {

@@ -1,0 +1,19 @@
+// rhd_stage_ppm.cu -- the stage kernels with piecewise parabolic faces
+// (Sec. 3.3): the tile body of rhd_tile.cuh with a 3-cell halo and a 6-plane
+// z ring, the general physics selected at run time.
+#include "rhd_stage.cuh"
+
+namespace rhd {
+
+template <int STAGE>
+static cudaError_t launch_ppm_t(int precision, const StageArgs& A, cudaStream_t s) {
+  if (precision == RHD_PREC_MIXED) return launch_prec<STAGE, float, true, true>(A, s);
+  return launch_prec<STAGE, double, true, true>(A, s);
+}
+
+cudaError_t launch_stage_ppm(int stage, int precision, const StageArgs& A, cudaStream_t s) {
+  if (stage == 0) return launch_ppm_t<0>(precision, A, s);
+  return stage == 1 ? launch_ppm_t<1>(precision, A, s) : launch_ppm_t<2>(precision, A, s);
+}
+
+}  // namespace rhd

@@ -2,10 +2,10 @@
 // (rhd_stage.cu) and the batched persistent kernel (rhd_batch.cu).
 //
 // Work layout (3-D): a block owns a TX x TY column of cells and marches
-// through a chunk of z planes.  E and F/c of four consecutive planes sit in a
-// shared-memory ring, each plane with a 2-cell halo in x and y (ghost cells
-// folded in at load time: periodic wrap, or mirror with the normal flux
-// negated).  Every face flux is computed exactly once: x- and y-faces of the
+// through a chunk of z planes.  E and F/c of four consecutive planes (six
+// with PPM faces) sit in a shared-memory ring, each plane with a 2-cell halo
+// in x and y (3 with PPM; ghost cells folded in at load time: periodic wrap,
+// or mirror with the normal flux negated).  Every face flux is computed exactly once: x- and y-faces of the
 // current plane by one thread each (into shared memory), z-faces by the thread
 // that owns the column (kept in registers from one plane to the next,
 // together with the half z-slope of the current cell).  The thread then
@@ -19,11 +19,14 @@
 namespace rhd {
 
 // A tile: TX x TY threads (one per cell of a plane), LZ planes per block in
-// 3-D.  HX, HY: halo widths; NPL: planes kept in the shared-memory ring.
-template <int NDIM_, int TX_, int TY_, int LZ_>
+// 3-D.  PPM: piecewise parabolic faces (else PLM).  HX, HY: halo widths; NPL:
+// planes kept in the shared-memory ring.
+template <int NDIM_, int TX_, int TY_, int LZ_, bool PPM_ = false>
 struct TileT {
   static constexpr int NDIM = NDIM_, TX = TX_, TY = TY_, LZ = LZ_;
-  static constexpr int HX = 2, HY = NDIM >= 2 ? 2 : 0, NPL = NDIM == 3 ? 4 : 1;
+  static constexpr bool PPM = PPM_;
+  static constexpr int HX = PPM ? 3 : 2, HY = NDIM >= 2 ? HX : 0;
+  static constexpr int NPL = NDIM == 3 ? (PPM ? 6 : 4) : 1;
   static constexpr int NT = TX * TY;
 };
 
@@ -41,6 +44,18 @@ struct DefaultTileOf<1> { using type = TileT<1, 256, 1, 1>; };
 template <int NDIM>
 using Tile = typename DefaultTileOf<NDIM>::type;
 
+// PPM tiles: the same shapes with the wider halo (3-D, FP64: 120 KB of
+// shared memory, one block per SM).
+template <int NDIM>
+using TilePPM = TileT<NDIM, DefaultTileOf<NDIM>::type::TX, DefaultTileOf<NDIM>::type::TY,
+                      DefaultTileOf<NDIM>::type::LZ, true>;
+
+// ring slot of plane p (p >= -3)
+template <class T>
+__device__ __forceinline__ int ring_slot(int p) {
+  return T::NPL == 4 ? (p & 3) : (T::NPL == 6 ? (p + 6) % 6 : 0);
+}
+
 template <class T, typename R>
 struct SmemT {
   static constexpr int PW = T::TX + 2 * T::HX;
@@ -52,11 +67,13 @@ struct SmemT {
   static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY);
 };
 
-// Coordinate x >= -2 folded onto [0, n) by the boundary condition (padding
-// of a partial tile beyond n + 1 is clamped first); flip = mirror image.
-__device__ __forceinline__ int fold(int x, int n, int bclo, int bchi, bool& flip) {
+// Coordinate x >= -3 folded onto [0, n) by the boundary condition (padding
+// of a partial tile beyond n + hmax is clamped first; a mirror needs
+// n >= hmax + 1); flip = mirror image.
+__device__ __forceinline__ int fold(int x, int n, int bclo, int bchi, bool& flip,
+                                    int hmax = 1) {
   flip = false;
-  x = min(x, n + 1);
+  x = min(x, n + hmax);
   if (x < 0) {
     if (bclo == RHD_BC_PERIODIC) {
       x = ((x % n) + n) % n;
@@ -120,14 +137,15 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
   const Geometry& g = A.g;
   const R inv_c = (R)A.ph.inv_c;
   bool fz = false;
-  int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz) : 0;
+  int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz, T::HX - 1) : 0;
   const int zin = GEN && NDIM == 3 ? inflow_side(g, 2, zg) : -1;
   R* pl = ring + slot * 4 * S::PS;
   for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
     int ii = c % S::PW, jj = c / S::PW;
     bool fx = false, fy = false;
-    int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx);
-    int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy) : 0;
+    int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx, T::HX - 1);
+    int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy, T::HX - 1)
+                       : 0;
     int idx = xf + g.n[0] * (yf + g.n[1] * zf);
     R E = (R)__ldg(A.yt[Y_ERAD] + idx);
     R Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
@@ -167,22 +185,57 @@ __device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
   for (int q = 0; q < 4; ++q) u[q] = pl[q * S::PS + c];
 }
 
+// PPM states of the face between cells u[2] and u[3] of the six cells u
+template <typename R>
+__device__ __forceinline__ void ppm_states(const R u[6][4], R L[4], R Rr[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    R v[6];
+#pragma unroll
+    for (int o = 0; o < 6; ++o) v[o] = u[o][q];
+    ppm_face(v, L[q], Rr[q]);
+  }
+}
+
 // flux through the face between plane cells c - st and c (stride st)
 template <class T, typename R>
 __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R eps, R chat,
                                            int closure, R out[4]) {
-  R am[4], a[4], b[4], bp[4];
-  cell_of<T, R>(pl, c - 2 * st, am);
-  cell_of<T, R>(pl, c - st, a);
-  cell_of<T, R>(pl, c, b);
-  cell_of<T, R>(pl, c + st, bp);
   R L[4], Rr[4];
+  if constexpr (T::PPM) {
+    R u[6][4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    L[q] = a[q] + half_slope(am[q], a[q], b[q]);
-    Rr[q] = b[q] - half_slope(a[q], b[q], bp[q]);
+    for (int o = 0; o < 6; ++o) cell_of<T, R>(pl, c + (o - 3) * st, u[o]);
+    ppm_states(u, L, Rr);
+  } else {
+    R am[4], a[4], b[4], bp[4];
+    cell_of<T, R>(pl, c - 2 * st, am);
+    cell_of<T, R>(pl, c - st, a);
+    cell_of<T, R>(pl, c, b);
+    cell_of<T, R>(pl, c + st, bp);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      L[q] = a[q] + half_slope(am[q], a[q], b[q]);
+      Rr[q] = b[q] - half_slope(a[q], b[q], bp[q]);
+    }
   }
   return hll_states<R>(d, L, Rr, eps, chat, closure, out);
+}
+
+// PPM flux through the z-face between planes kf and kf + 1 of the own column
+// (planes kf - 2 .. kf + 3 in the ring)
+template <class T, typename R>
+__device__ __forceinline__ bool ppm_zface(const StageArgs& A, const R* ring, int own, int kf,
+                                          int cx, int cy, R out[4]) {
+  using S = SmemT<T, R>;
+  R u[6][4];
+#pragma unroll
+  for (int o = 0; o < 6; ++o)
+    cell_of<T, R>(ring + ring_slot<T>(kf - 2 + o) * 4 * S::PS, own, u[o]);
+  R L[4], Rr[4];
+  ppm_states(u, L, Rr);
+  R eps = (R)face_eps(A, 2, cx, cy, kf);
+  return hll_states<R>(2, L, Rr, eps, (R)A.ph.chat, A.ph.closure, out);
 }
 
 // Per-thread iteration statistics of the cells a thread has solved.
@@ -224,8 +277,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   bool zbad = false;
 
   R zlo[4] = {R(0), R(0), R(0), R(0)};  // z-face flux below the current cell
-  R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell
-  if (NDIM == 3) {
+  R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell (PLM)
+  if constexpr (NDIM == 3 && T::PPM) {
+    for (int o = -3; o <= 2; ++o)
+      load_plane<T, R, GEN>(A, ring, ring_slot<T>(kbeg + o), kbeg + o, x0, y0);
+    __syncthreads();
+    zbad = !ppm_zface<T, R>(A, ring, own, kbeg - 1, cx, cy, zlo);
+    __syncthreads();  // plane kbeg-3's slot is reloaded by the first iteration
+  } else if constexpr (NDIM == 3) {
     for (int o = -2; o <= 1; ++o)
       load_plane<T, R, GEN>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
     __syncthreads();
@@ -248,18 +307,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 
   for (int k = kbeg; k < kend; ++k) {
     if (NDIM == 3) {
-      load_plane<T, R, GEN>(A, ring, (k + 2) & 3, k + 2, x0, y0);
+      constexpr int AHEAD = T::PPM ? 3 : 2;
+      load_plane<T, R, GEN>(A, ring, ring_slot<T>(k + AHEAD), k + AHEAD, x0, y0);
     } else {
       load_plane<T, R, GEN>(A, ring, 0, 0, x0, y0);
     }
     __syncthreads();
-    const R* pl = ring + (NDIM == 3 ? (k & 3) : 0) * 4 * S::PS;
+    const R* pl = ring + (NDIM == 3 ? ring_slot<T>(k) : 0) * 4 * S::PS;
     bool bad = zbad;
 
     // ---- z-face k+1/2 of the own column
     R zhi[4] = {R(0), R(0), R(0), R(0)};
     R hz1[4] = {R(0), R(0), R(0), R(0)};
-    if (NDIM == 3) {
+    if constexpr (NDIM == 3 && T::PPM) {
+      zbad = !ppm_zface<T, R>(A, ring, own, k, cx, cy, zhi);
+      bad = bad || zbad;
+    } else if constexpr (NDIM == 3) {
       R u0[4], u1[4], u2[4];
       cell_of<T, R>(pl, own, u0);
       cell_of<T, R>(ring + ((k + 1) & 3) * 4 * S::PS, own, u1);

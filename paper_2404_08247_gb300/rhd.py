@@ -27,6 +27,7 @@ RHD_SCHEME_IMEX_PDARS, RHD_SCHEME_RK2_SSP = 0, 1
 RHD_CLOSURE_M1, RHD_CLOSURE_EDDINGTON = 0, 1
 RHD_HLL_TAU, RHD_HLL_NONE = 0, 1
 RHD_PREC_FP64, RHD_PREC_MIXED = 0, 1
+RHD_RECON_PLM, RHD_RECON_PPM = 0, 1
 RHD_NFIELDS = 10
 (RHD_F_RHO, RHD_F_MX, RHD_F_MY, RHD_F_MZ, RHD_F_EGAS, RHD_F_ERAD, RHD_F_FX,
  RHD_F_FY, RHD_F_FZ, RHD_F_KAPPA) = range(10)
@@ -36,6 +37,7 @@ _SCHEME = {"imex": RHD_SCHEME_IMEX_PDARS, "rk2ssp": RHD_SCHEME_RK2_SSP}
 _CLOSURE = {"m1": RHD_CLOSURE_M1, "eddington": RHD_CLOSURE_EDDINGTON}
 _HLL = {"tau": RHD_HLL_TAU, "none": RHD_HLL_NONE}
 _PREC = {"fp64": RHD_PREC_FP64, "mixed": RHD_PREC_MIXED}
+_RECON = {"plm": RHD_RECON_PLM, "ppm": RHD_RECON_PPM}
 
 
 class RHDError(RuntimeError):
@@ -70,6 +72,7 @@ class rhd_params(ctypes.Structure):
         ("bc_state", ((ctypes.c_double * 4) * 2) * 3),
         ("kappa_P_ratio", ctypes.c_double),
         ("kappa_F_ratio", ctypes.c_double),
+        ("reconstruction", ctypes.c_int),
     ]
 
 
@@ -220,6 +223,7 @@ def params_from_problem(prob: dict, precision: str | int = "fp64") -> rhd_params
     p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
     p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
     p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
+    p.reconstruction = _RECON[prob.get("reconstruction", "plm")]
     st = prob.get("bc_state", {})
     for d in range(3):
         for side in range(2):

@@ -131,3 +131,35 @@ def test_problem_mapping(rhd):
     assert p.precision == rhd.RHD_PREC_MIXED
     assert p.n[0] == 64 and p.n[1] == 1 and p.ndim == 1
     assert p.chat == prob["chat"] and p.c == prob["c"]
+
+
+def test_reconstruction_option_is_validated(rhd):
+    """PPM reads three cells on each side of a face: a reflecting or inflow
+    axis needs n >= 3 (a periodic one wraps); an unknown value is refused."""
+    def params(n, bc, recon):
+        q = rhd.rhd_params_default()
+        q.n[0] = n
+        q.bc[0][0] = q.bc[0][1] = bc
+        q.reconstruction = recon
+        return q
+
+    assert rhd.rhd_params_default().reconstruction == rhd.RHD_RECON_PLM
+    assert rhd.rhd_params_validate(params(2, rhd.RHD_BC_REFLECT, rhd.RHD_RECON_PLM))[0] == rhd.RHD_OK
+    st, msg = rhd.rhd_params_validate(params(2, rhd.RHD_BC_REFLECT, rhd.RHD_RECON_PPM))
+    assert st == rhd.RHD_ERR_ARG and "n >= 3" in msg
+    assert rhd.rhd_params_validate(params(3, rhd.RHD_BC_REFLECT, rhd.RHD_RECON_PPM))[0] == rhd.RHD_OK
+    assert rhd.rhd_params_validate(params(1, rhd.RHD_BC_PERIODIC, rhd.RHD_RECON_PPM))[0] == rhd.RHD_OK
+    assert rhd.rhd_params_validate(params(8, rhd.RHD_BC_PERIODIC, 2))[0] == rhd.RHD_ERR_ARG
+    p = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16], reconstruction="ppm"))
+    assert p.reconstruction == rhd.RHD_RECON_PPM
+
+
+def test_batch_refuses_ppm_before_touching_the_device(rhd):
+    probs = (rhd.rhd_params * 2)()
+    for i in range(2):
+        probs[i] = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16]))
+    probs[1].reconstruction = rhd.RHD_RECON_PPM
+    h = ctypes.c_void_p()
+    st = rhd.load().rhd_batch_init(probs, 2, ctypes.byref(h))
+    assert st == rhd.RHD_ERR_ARG and not h.value
+    assert b"PLM" in rhd.load().rhd_last_error(None)

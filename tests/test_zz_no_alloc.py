@@ -41,10 +41,12 @@ def noalloc_step(R, p, x_in, x_out, stream_handle, dt=0.0):
     return st, info
 
 
-def test_two_calls_in_a_row_match_rhd_step(R):
+@pytest.mark.parametrize("recon", ["plm", "ppm"])
+def test_two_calls_in_a_row_match_rhd_step(R, recon):
     """Two successive no-allocation steps (the second reads the first's output)
-    equal two rhd_step calls of a context on the same input."""
-    prob, U, _ = I.turbulent_box_3d(shape=(24, 20, 18))
+    equal two rhd_step calls of a context on the same input (PLM and PPM
+    faces)."""
+    prob, U, _ = I.turbulent_box_3d(shape=(24, 20, 18), reconstruction=recon)
     p = R.params_from_problem(prob)
     stream = torch.cuda.current_stream()
     want = []
