@@ -59,6 +59,8 @@ def parse(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--hll", default="tau", choices=["tau", "none"])
+    ap.add_argument("--reconstruction", default="plm", choices=["plm", "ppm"],
+                    help="face states of the headline form (Sec. 3.3)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96,
@@ -193,7 +195,7 @@ def workload(args, rank=0):
     from paper_2404_08247_gb300 import inputs as I
     prob, U, _ = I.turbulent_box_3d(n=args.n, seed_rho=3 + 100 * rank,
                                     seed_v=4 + 100 * rank, seed_T=5 + 100 * rank,
-                                    hll_mode=args.hll)
+                                    hll_mode=args.hll, reconstruction=args.reconstruction)
     return prob, U
 
 
@@ -206,6 +208,7 @@ def config_of(args, prob):
         "cells": int(args.n ** 3),
         "precision": args.precision,
         "hll_mode": args.hll,
+        "reconstruction": args.reconstruction,
         "closure": "m1",
         "vc_order": 2,
         "cfl": prob["cfl"],

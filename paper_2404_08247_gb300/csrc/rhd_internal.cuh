@@ -214,6 +214,14 @@ __device__ __forceinline__ double ppm_edge_d(double u0, double l, double r) {
   return LEFT ? u0 - s : u0 + s;
 }
 
+template <bool LEFT, typename R>
+__device__ __forceinline__ R ppm_edge_of(R u0, R l, R r) {
+  if constexpr (sizeof(R) == sizeof(double))
+    return ppm_edge_d<LEFT>(u0, l, r);
+  else
+    return ppm_edge<LEFT>(u0, l, r);
+}
+
 // States of the face between u[2] and u[3] from cells u[0..5] (the face's
 // three cells on each side): the constrained right edge of u[2] | the
 // constrained left edge of u[3].
@@ -224,13 +232,8 @@ __device__ __forceinline__ void ppm_face(const R u[6], R& L, R& Rr) {
   const R a12 = ppm_interface(u[1], u[2], h1, h2);
   const R a23 = ppm_interface(u[2], u[3], h2, h3);
   const R a34 = ppm_interface(u[3], u[4], h3, h4);
-  if constexpr (sizeof(R) == sizeof(double)) {
-    L = ppm_edge_d<false>(u[2], a12, a23);
-    Rr = ppm_edge_d<true>(u[3], a23, a34);
-  } else {
-    L = ppm_edge<false>(u[2], a12, a23);
-    Rr = ppm_edge<true>(u[3], a23, a34);
-  }
+  L = ppm_edge_of<false>(u[2], a12, a23);
+  Rr = ppm_edge_of<true>(u[3], a23, a34);
 }
 
 // ---------------------------------------------------------------- closure

@@ -1,6 +1,6 @@
 // rhd_stage_ppm.cu -- the stage kernels with piecewise parabolic faces
-// (Sec. 3.3): the tile body of rhd_tile.cuh with a 3-cell halo and a 6-plane
-// z ring, the general physics selected at run time.
+// (Sec. 3.3): the tile body of rhd_tile.cuh with a 3-cell halo and the z
+// edges carried along the column, the general physics selected at run time.
 #include "rhd_stage.cuh"
 
 namespace rhd {

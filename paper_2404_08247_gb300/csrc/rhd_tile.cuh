@@ -2,10 +2,10 @@
 // (rhd_stage.cu) and the batched persistent kernel (rhd_batch.cu).
 //
 // Work layout (3-D): a block owns a TX x TY column of cells and marches
-// through a chunk of z planes.  E and F/c of four consecutive planes (six
-// with PPM faces) sit in a shared-memory ring, each plane with a 2-cell halo
-// in x and y (3 with PPM; ghost cells folded in at load time: periodic wrap,
-// or mirror with the normal flux negated).  Every face flux is computed exactly once: x- and y-faces of the
+// through a chunk of z planes.  E and F/c of four consecutive planes sit in
+// a shared-memory ring, each plane with a 2-cell halo in x and y (3 with PPM
+// faces; ghost cells folded in at load time: periodic wrap, or mirror with
+// the normal flux negated).  Every face flux is computed exactly once: x- and y-faces of the
 // current plane by one thread each (into shared memory), z-faces by the thread
 // that owns the column (kept in registers from one plane to the next,
 // together with the half z-slope of the current cell).  The thread then
@@ -26,7 +26,7 @@ struct TileT {
   static constexpr int NDIM = NDIM_, TX = TX_, TY = TY_, LZ = LZ_;
   static constexpr bool PPM = PPM_;
   static constexpr int HX = PPM ? 3 : 2, HY = NDIM >= 2 ? HX : 0;
-  static constexpr int NPL = NDIM == 3 ? (PPM ? 6 : 4) : 1;
+  static constexpr int NPL = NDIM == 3 ? 4 : 1;
   static constexpr int NT = TX * TY;
 };
 
@@ -44,8 +44,8 @@ struct DefaultTileOf<1> { using type = TileT<1, 256, 1, 1>; };
 template <int NDIM>
 using Tile = typename DefaultTileOf<NDIM>::type;
 
-// PPM tiles: the same shapes with the wider halo (3-D, FP64: 120 KB of
-// shared memory, one block per SM).
+// PPM tiles: the same shapes with the wider halo (3-D, FP64: 86 KB of
+// shared memory, two blocks per SM).
 template <int NDIM>
 using TilePPM = TileT<NDIM, DefaultTileOf<NDIM>::type::TX, DefaultTileOf<NDIM>::type::TY,
                       DefaultTileOf<NDIM>::type::LZ, true>;
@@ -53,7 +53,7 @@ using TilePPM = TileT<NDIM, DefaultTileOf<NDIM>::type::TX, DefaultTileOf<NDIM>::
 // ring slot of plane p (p >= -3)
 template <class T>
 __device__ __forceinline__ int ring_slot(int p) {
-  return T::NPL == 4 ? (p & 3) : (T::NPL == 6 ? (p + 6) % 6 : 0);
+  return T::NPL == 4 ? (p & 3) : 0;
 }
 
 template <class T, typename R>
@@ -222,20 +222,30 @@ __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R 
   return hll_states<R>(d, L, Rr, eps, chat, closure, out);
 }
 
-// PPM flux through the z-face between planes kf and kf + 1 of the own column
-// (planes kf - 2 .. kf + 3 in the ring)
-template <class T, typename R>
-__device__ __forceinline__ bool ppm_zface(const StageArgs& A, const R* ring, int own, int kf,
-                                          int cx, int cy, R out[4]) {
-  using S = SmemT<T, R>;
-  R u[6][4];
-#pragma unroll
-  for (int o = 0; o < 6; ++o)
-    cell_of<T, R>(ring + ring_slot<T>(kf - 2 + o) * 4 * S::PS, own, u[o]);
-  R L[4], Rr[4];
-  ppm_states(u, L, Rr);
-  R eps = (R)face_eps(A, 2, cx, cy, kf);
-  return hll_states<R>(2, L, Rr, eps, (R)A.ph.chat, A.ph.closure, out);
+// One cell (E, F/c) of the own column (cx, cy inside the grid) at plane zg,
+// a ghost plane folded or taken from its inflow state exactly as load_plane
+// does.
+template <class T, typename R, bool GEN>
+__device__ __forceinline__ void column_cell(const StageArgs& A, int cx, int cy, int zg,
+                                            R u[4]) {
+  const Geometry& g = A.g;
+  const R inv_c = (R)A.ph.inv_c;
+  bool fz = false;
+  const int zf = fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz, T::HX - 1);
+  const int idx = cx + g.n[0] * (cy + g.n[1] * zf);
+  u[0] = (R)__ldg(A.yt[Y_ERAD] + idx);
+  u[1] = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
+  u[2] = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
+  const R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+  u[3] = fz ? -Fz : Fz;
+  const int side = GEN ? inflow_side(g, 2, zg) : -1;
+  if (side >= 0) {
+    const double* st = g.bc_state[2][side];
+    u[0] = (R)st[0];
+    u[1] = (R)(st[1] * A.ph.inv_c);
+    u[2] = (R)(st[2] * A.ph.inv_c);
+    u[3] = (R)(st[3] * A.ph.inv_c);
+  }
 }
 
 // Per-thread iteration statistics of the cells a thread has solved.
@@ -278,12 +288,34 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 
   R zlo[4] = {R(0), R(0), R(0), R(0)};  // z-face flux below the current cell
   R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell (PLM)
+  // PPM z march: the constrained right edge of the current cell and the
+  // interface value above it, carried from plane to plane, so each plane
+  // adds one cell's edges; the start reads the own column from memory
+  R rz[4] = {R(0), R(0), R(0), R(0)};
+  R az[4] = {R(0), R(0), R(0), R(0)};
   if constexpr (NDIM == 3 && T::PPM) {
-    for (int o = -3; o <= 2; ++o)
+    R u[6][4];
+#pragma unroll
+    for (int o = 0; o < 6; ++o) column_cell<T, R, GEN>(A, cx, cy, kbeg - 3 + o, u[o]);
+    R L[4], Rr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const R h1 = half_slope(u[0][q], u[1][q], u[2][q]);
+      const R h2 = half_slope(u[1][q], u[2][q], u[3][q]);
+      const R h3 = half_slope(u[2][q], u[3][q], u[4][q]);
+      const R h4 = half_slope(u[3][q], u[4][q], u[5][q]);
+      const R a12 = ppm_interface(u[1][q], u[2][q], h1, h2);
+      const R a23 = ppm_interface(u[2][q], u[3][q], h2, h3);
+      const R a34 = ppm_interface(u[3][q], u[4][q], h3, h4);
+      L[q] = ppm_edge_of<false>(u[2][q], a12, a23);
+      Rr[q] = ppm_edge_of<true>(u[3][q], a23, a34);
+      rz[q] = ppm_edge_of<false>(u[3][q], a23, a34);
+      az[q] = a34;
+    }
+    R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
+    zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
+    for (int o = 0; o <= 2; ++o)
       load_plane<T, R, GEN>(A, ring, ring_slot<T>(kbeg + o), kbeg + o, x0, y0);
-    __syncthreads();
-    zbad = !ppm_zface<T, R>(A, ring, own, kbeg - 1, cx, cy, zlo);
-    __syncthreads();  // plane kbeg-3's slot is reloaded by the first iteration
   } else if constexpr (NDIM == 3) {
     for (int o = -2; o <= 1; ++o)
       load_plane<T, R, GEN>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
@@ -320,7 +352,26 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
     R zhi[4] = {R(0), R(0), R(0), R(0)};
     R hz1[4] = {R(0), R(0), R(0), R(0)};
     if constexpr (NDIM == 3 && T::PPM) {
-      zbad = !ppm_zface<T, R>(A, ring, own, k, cx, cy, zhi);
+      // face k+1/2: the carried right edge of cell k | the left edge of
+      // cell k+1, whose edges come from a(k+1/2) and a new a(k+3/2)
+      R v0[4], v1[4], v2[4], v3[4];
+      cell_of<T, R>(pl, own, v0);
+      cell_of<T, R>(ring + ring_slot<T>(k + 1) * 4 * S::PS, own, v1);
+      cell_of<T, R>(ring + ring_slot<T>(k + 2) * 4 * S::PS, own, v2);
+      cell_of<T, R>(ring + ring_slot<T>(k + 3) * 4 * S::PS, own, v3);
+      R L[4], Rr[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R ha = half_slope(v0[q], v1[q], v2[q]);
+        const R hb = half_slope(v1[q], v2[q], v3[q]);
+        const R an = ppm_interface(v1[q], v2[q], ha, hb);
+        L[q] = rz[q];
+        Rr[q] = ppm_edge_of<true>(v1[q], az[q], an);
+        rz[q] = ppm_edge_of<false>(v1[q], az[q], an);
+        az[q] = an;
+      }
+      R eps = (R)face_eps(A, 2, cx, cy, k);
+      zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
       bad = bad || zbad;
     } else if constexpr (NDIM == 3) {
       R u0[4], u1[4], u2[4];
