@@ -1,5 +1,6 @@
-"""Python access to the serial FP64 CPU oracle in ``rhd_oracle.c`` and its
-adjoint in ``rhd_oracle_adj.c``.
+"""Python access to the serial FP64 CPU oracle in ``rhd_oracle.c``, its
+adjoint in ``rhd_oracle_adj.c`` and the hydrodynamic subsystem with the
+operator split in ``rhd_oracle_hydro.c``.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only callers.  The library never imports
@@ -22,6 +23,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "rhd_oracle.c")
 SRC_ADJ = os.path.join(HERE, "rhd_oracle_adj.c")
+SRC_HYD = os.path.join(HERE, "rhd_oracle_hydro.c")
 HDR = os.path.join(HERE, "rhd_oracle.h")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
@@ -42,11 +44,11 @@ def build(force: bool = False) -> str:
     stale = force or not os.path.exists(LIB)
     if not stale:
         t = os.path.getmtime(LIB)
-        stale = any(os.path.getmtime(f) > t for f in (SRC, SRC_ADJ, HDR))
+        stale = any(os.path.getmtime(f) > t for f in (SRC, SRC_ADJ, SRC_HYD, HDR))
     if stale:
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, SRC, SRC_ADJ, "-lm"]
+               "-o", tmp, SRC, SRC_ADJ, SRC_HYD, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB
@@ -78,6 +80,7 @@ class OrcParams(ctypes.Structure):
         ("kappa_P_ratio", ctypes.c_double),
         ("kappa_F_ratio", ctypes.c_double),
         ("reconstruction", ctypes.c_int),
+        ("cfl_hydro", ctypes.c_double),
     ]
 
 
@@ -108,6 +111,16 @@ def lib():
         L.orc_eddington_tensor.restype = None
         L.orc_transport.argtypes = [P, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
         L.orc_transport.restype = ctypes.c_int
+        L.orc_hydro_dt.argtypes = [P, dp]
+        L.orc_hydro_dt.restype = ctypes.c_double
+        L.orc_hydro_rate.argtypes = [P, dp, dp, ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_hydro_rate.restype = ctypes.c_int
+        L.orc_hydro_step.argtypes = [P, dp, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_hydro_step.restype = ctypes.c_int
+        L.orc_split_step.argtypes = [P, dp, ctypes.c_double, ctypes.POINTER(OrcInfo),
+                                     ctypes.POINTER(ctypes.c_int)]
+        L.orc_split_step.restype = ctypes.c_int
         L.orc_local_solve.argtypes = [P, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, dp,
                                       ctypes.POINTER(ctypes.c_int),
@@ -163,6 +176,7 @@ def make_params(prob: dict) -> OrcParams:
     p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
     p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
     p.reconstruction = {"plm": 0, "ppm": 1}[prob.get("reconstruction", "plm")]
+    p.cfl_hydro = float(prob.get("cfl_hydro", 0.3))
     # bc_state[d][side] = (E, Fx, Fy, Fz) of inflow faces; default E = 1, F = 0
     st = prob.get("bc_state", {})
     for d in range(3):
@@ -308,3 +322,53 @@ def trajectory_gradient(prob: dict, U0: np.ndarray, nsteps: int, loss_grad,
     for tape in reversed(tapes):
         ybar = step_adjoint(prob, rho, kappa, tape, ybar, kbar, dt)
     return L, ybar, kbar
+
+
+# ------------------------------------------------ hydrodynamics (Sec. 3.1)
+
+def hydro_dt(prob: dict, U: np.ndarray) -> float:
+    """cfl_hydro / max_cells sum_d (|v_d| + a) / dx_d."""
+    return lib().orc_hydro_dt(ctypes.byref(make_params(prob)), _dptr(U))
+
+
+def hydro_rate(prob: dict, U: np.ndarray) -> np.ndarray:
+    """d(rho, mx, my, mz, Egas)/dt of the Euler equations, shape (5, nz, ny, nx)."""
+    rate = np.zeros((5,) + U.shape[1:], dtype=np.float64)
+    fc = ctypes.c_longlong(-1)
+    st = lib().orc_hydro_rate(ctypes.byref(make_params(prob)), _dptr(U), _dptr(rate),
+                              ctypes.byref(fc))
+    if st != 0:
+        raise RuntimeError("oracle hydro rate failed: %s at cell %d"
+                           % (STATUS.get(st, st), fc.value))
+    return rate
+
+
+def hydro_step(prob: dict, U: np.ndarray, nsteps: int = 1, dt: float = 0.0):
+    """nsteps RK2-SSP steps of the hydrodynamic subsystem (U in place); dt <= 0
+    takes hydro_dt of the state at each step."""
+    p = make_params(prob)
+    for _ in range(nsteps):
+        h = dt if dt > 0.0 else lib().orc_hydro_dt(ctypes.byref(p), _dptr(U))
+        fc = ctypes.c_longlong(-1)
+        st = lib().orc_hydro_step(ctypes.byref(p), _dptr(U), float(h), ctypes.byref(fc))
+        if st != 0:
+            raise RuntimeError("oracle hydro step failed: %s at cell %d"
+                               % (STATUS.get(st, st), fc.value))
+
+
+def split_step(prob: dict, U: np.ndarray, nsteps: int = 1, dt_h: float = 0.0):
+    """nsteps operator-split steps (hydrodynamics, then the subcycled
+    radiation step); returns the list of subcycle counts."""
+    p = make_params(prob)
+    subs = []
+    for _ in range(nsteps):
+        info = OrcInfo()
+        ns = ctypes.c_int(0)
+        st = lib().orc_split_step(ctypes.byref(p), _dptr(U), float(dt_h), ctypes.byref(info),
+                                  ctypes.byref(ns))
+        if st != 0:
+            raise RuntimeError("oracle split step failed: %s at cell %d"
+                               % (STATUS.get(st, st), info.fail_cell))
+        subs.append(ns.value)
+    return subs
+

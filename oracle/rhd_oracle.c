@@ -615,3 +615,9 @@ void orc_totals(const orc_params* p, const double* U, double out[4]) {
     out[3] += (U[ORC_MZ * N + i] + U[ORC_FZ * N + i] / (p->c * p->chat)) * V;
   }
 }
+
+/* the reconstruction as the hydrodynamic subsystem (rhd_oracle_hydro.c)
+ * uses it */
+double orc_recon_mc_slope(double um, double u0, double up) { return mc_slope(um, u0, up); }
+
+void orc_recon_ppm_edges(const double u[5], double* aL, double* aR) { ppm_edges(u, aL, aR); }

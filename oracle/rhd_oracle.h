@@ -65,6 +65,7 @@ typedef struct {
   double kappa_P_ratio;   /* chi_0P / chi_0E (1: grey) */
   double kappa_F_ratio;   /* chi_0F / chi_0E (1: grey) */
   int reconstruction;     /* ORC_RECON_*: face states of the transport */
+  double cfl_hydro;       /* CFL number of the hydrodynamic step */
 } orc_params;
 
 typedef struct {
@@ -110,6 +111,33 @@ void orc_totals(const orc_params* p, const double* U, double out[4]);
 
 /* One step as orc_step that also writes the tape: y(n), y(n+1/2), y(n+1),
  * 3 x 8 x ncell doubles. */
+/* ---- the hydrodynamic subsystem and the operator split (Sec. 3.1),
+ * rhd_oracle_hydro.c ---- */
+
+/* dt of the hydrodynamic step: cfl_hydro / max over cells of
+ * sum_d (|v_d| + a)/dx_d, a the adiabatic sound speed; <= 0 if a cell is
+ * nonphysical. */
+double orc_hydro_dt(const orc_params* p, const double* U);
+
+/* Rates d(rho, m_x, m_y, m_z, E_gas)/dt of the Euler equations (Sec. 3.1),
+ * rate[5][N]. */
+int orc_hydro_rate(const orc_params* p, const double* U, double* rate,
+                   long long* fail_cell);
+
+/* One RK2-SSP step of the hydrodynamic subsystem; the radiation fields are
+ * untouched.  On failure U is left unchanged. */
+int orc_hydro_step(const orc_params* p, double* U, double dt, long long* fail_cell);
+
+/* One operator-split step: the hydrodynamic step of dt_h (dt_h <= 0:
+ * orc_hydro_dt), then nsub = ceil(dt_h / orc_dt - 1e-12) radiation steps of
+ * dt_h / nsub.  *nsub_out (nullable) receives nsub. */
+int orc_split_step(const orc_params* p, double* U, double dt_h, orc_info* info,
+                   int* nsub_out);
+
+/* the transport's reconstruction, shared with the hydrodynamic subsystem */
+double orc_recon_mc_slope(double um, double u0, double up);
+void orc_recon_ppm_edges(const double u[5], double* aL, double* aR);
+
 int orc_step_tape(const orc_params* p, double* U, double dt, double* tape);
 
 /* Adjoint of one taped step: ybar0 = dL/dy(n) from ybar1 = dL/dy(n+1);

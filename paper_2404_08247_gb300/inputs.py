@@ -32,6 +32,34 @@ NFIELD = len(FIELDS)
 F_RHO, F_MX, F_MY, F_MZ, F_EGAS, F_ERAD, F_FX, F_FY, F_FZ, F_KAPPA = range(10)
 
 
+def gas_state(prob: dict, rho, v, p, kappa=0.0) -> np.ndarray:
+    """State of a gas given by density, velocity (3, nz, ny, nx) and pressure,
+    with radiation in comoving equilibrium at the gas temperature
+    T = p / (rho kB_over_mu) (ideal gas) and specific opacity kappa."""
+    kB = prob.get("kB_over_mu", 1.0)
+    rho = np.asarray(rho, dtype=np.float64)
+    T = np.asarray(p, dtype=np.float64) / (rho * kB)
+    kap = np.broadcast_to(np.asarray(kappa, dtype=np.float64), rho.shape)
+    return equilibrium_state(prob, rho, T, v, kap)
+
+
+def riemann_problem_1d(n: int, left, right, x0: float = 0.5, gamma: float = 1.4,
+                       bc: str = "reflect", **kw):
+    """Shock-tube initial state on [0, 1]: primitive states left = (rho, u, p)
+    for x < x0 and right beyond; no radiation coupling (kappa = 0).  Returns
+    (problem, state)."""
+    prob = base_problem(1, [n], [1.0 / n], gamma=gamma, bc=bc, **kw)
+    x = (np.arange(n) + 0.5) / n
+    sh = (1, 1, n)
+    L = x < x0
+    rho = np.where(L, left[0], right[0]).reshape(sh)
+    u = np.where(L, left[1], right[1]).reshape(sh)
+    pr = np.where(L, left[2], right[2]).reshape(sh)
+    v = np.zeros((3,) + sh)
+    v[0] = u
+    return prob, gas_state(prob, rho, v, pr)
+
+
 def base_problem(ndim, n, dx, **kw) -> dict:
     """Problem dict with the library defaults filled in."""
     prob = {
