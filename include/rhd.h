@@ -129,6 +129,8 @@ typedef struct {
   double kappa_P_ratio;
   double kappa_F_ratio;
   int reconstruction; /* rhd_recon */
+  /* CFL number of the hydrodynamic step (rhd_hydro_step, rhd_step_split) */
+  double cfl_hydro;
 } rhd_params;
 
 typedef struct {
@@ -150,7 +152,8 @@ typedef struct {
  * a_rad = kB_over_mu = 1, CFL 0.4, M1, v/c order 2, HLL TAU, FP64,
  * tolerances 1e-13, 64 Newton updates, 32 outer passes, IMEX PD-ARS,
  * temperature-independent grey opacity (kappa_T_exp 0, kappa_T_ref 1,
- * kappa_P_ratio = kappa_F_ratio = 1), inflow states E = 1, F = 0, PLM faces.  The grid
+ * kappa_P_ratio = kappa_F_ratio = 1), inflow states E = 1, F = 0, PLM faces,
+ * hydrodynamic CFL 0.3.  The grid
  * fields are zeroed; the caller sets ndim, n and dx. */
 void rhd_params_default(rhd_params* p);
 
@@ -273,6 +276,41 @@ rhd_status rhd_step_record(rhd_ctx* ctx, int nsteps, double dt, double* tape,
  * converged solve is singular.  Synchronises. */
 rhd_status rhd_adjoint(rhd_ctx* ctx, const double* tape, int64_t count, int nsteps,
                        double dt, double* ybar, double* kappa_bar);
+
+/* ---- Radiation hydrodynamics: the hydrodynamic subsystem and the
+ * operator split of Sec. 3.1 ----
+ * The gas state is rho (RHD_F_RHO, which these calls evolve), m and E_gas
+ * (the total gas energy); ideal gas p = (gamma - 1)(E_gas - |m|^2/(2 rho)).
+ * The paper leaves the hydrodynamic method to its host code; this library
+ * advances the Euler equations by a method of lines with RK2-SSP (Shu &
+ * Osher 1988), the primitives (rho, v, p) reconstructed with the context's
+ * `reconstruction` and HLLC fluxes (Toro, Spruce & Speares 1994) with the
+ * wave-speed bounds min/max(u -+ a) of both sides; ghost cells as for the
+ * radiation (a reflecting wall negates the normal velocity).  FP64 in both
+ * precisions.  Axes with an inflow face are refused (RHD_ERR_ARG).  The
+ * first call allocates 10 * ncell + 5 * (faces of every axis) doubles of
+ * scratch that the context keeps.  Failures (rho <= 0 or p <= 0 in a stage)
+ * return RHD_ERR_NONPHYSICAL with the first failing step; that step is not
+ * applied, earlier ones are.  info (nullable): steps_done, fail_cell,
+ * fail_step, fail_stage (3 and 4: the hydrodynamic stages 1 and 2), dt (the
+ * last step size) and t.  These calls synchronise. */
+
+/* dt of the hydrodynamic step for the current state: cfl_hydro / max over
+ * cells of sum_d (|v_d| + a)/dx_d, a = sqrt(gamma p / rho). */
+rhd_status rhd_hydro_dt(rhd_ctx* ctx, double* dt);
+
+/* nsteps RK2-SSP steps of the hydrodynamic subsystem alone, each of dt
+ * (dt <= 0: rhd_hydro_dt of the state before each step); the radiation
+ * fields are untouched.  Advances rhd_time. */
+rhd_status rhd_hydro_step(rhd_ctx* ctx, int nsteps, double dt, rhd_step_info* info);
+
+/* nsteps operator-split steps of the full system (Sec. 3.1): the
+ * hydrodynamic step of dt_h (dt_h <= 0: rhd_hydro_dt of the state), then
+ * the radiation update subcycled: nsub = ceil(dt_h / rhd_default_dt - 1e-12)
+ * rhd_step steps of dt_h / nsub.  info: steps_done counts split steps; the
+ * iteration statistics sum over the radiation steps; fail_stage 1-2 is a
+ * radiation stage, 3-4 a hydrodynamic one. */
+rhd_status rhd_step_split(rhd_ctx* ctx, int nsteps, double dt_h, rhd_step_info* info);
 
 /* Number of kernels this context has launched since rhd_init. */
 int64_t rhd_launch_count(const rhd_ctx* ctx);

@@ -5,6 +5,7 @@
 // rho and kappa, a status block and the totals scratch.  A step enqueues two
 // kernels; nothing waits on the host until rhd_sync/rhd_step reads the status
 // block once per batch.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "rhd_adjoint.cuh"
+#include "rhd_hydro.cuh"
 #include "rhd_internal.cuh"
 
 using namespace rhd;
@@ -66,6 +68,10 @@ struct rhd_ctx {
   std::vector<cudaEvent_t> pool;
   double* adj_q = nullptr;   // adjoint scratch, allocated by the first rhd_adjoint
   double* adj_fp = nullptr;
+  double* hyd_w = nullptr;   // hydrodynamic scratch, allocated by the first hydro call
+  double* hyd_u1 = nullptr;
+  double* hyd_f[3] = {nullptr, nullptr, nullptr};
+  unsigned long long* hyd_bits = nullptr;
 };
 
 static rhd_status fail(rhd_ctx* c, rhd_status s, const char* fmt, ...) {
@@ -140,6 +146,7 @@ void rhd_params_default(rhd_params* p) {
   p->kappa_P_ratio = 1.0;
   p->kappa_F_ratio = 1.0;
   p->reconstruction = RHD_RECON_PLM;
+  p->cfl_hydro = 0.3;
   for (int d = 0; d < 3; ++d)
     for (int s = 0; s < 2; ++s) {
       p->bc_state[d][s][0] = 1.0;
@@ -227,6 +234,8 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
       !(p->kappa_F_ratio > 0.0) || !std::isfinite(p->kappa_F_ratio))
     return bad(msg, msglen, "kappa_P_ratio and kappa_F_ratio must be positive"),
            RHD_ERR_ARG;
+  if (!(p->cfl_hydro > 0.0) || !std::isfinite(p->cfl_hydro))
+    return bad(msg, msglen, "cfl_hydro must be positive"), RHD_ERR_ARG;
   if (p->reconstruction != RHD_RECON_PLM && p->reconstruction != RHD_RECON_PPM)
     return bad(msg, msglen, "reconstruction is not an rhd_recon"), RHD_ERR_ARG;
   if (p->reconstruction == RHD_RECON_PPM)
@@ -313,6 +322,10 @@ static void release(rhd_ctx* c) {
   cudaFree(c->d_flag);
   cudaFree(c->adj_q);
   cudaFree(c->adj_fp);
+  cudaFree(c->hyd_w);
+  cudaFree(c->hyd_u1);
+  for (int d = 0; d < 3; ++d) cudaFree(c->hyd_f[d]);
+  cudaFree(c->hyd_bits);
   cudaFreeHost(c->h_status);
   cudaFreeHost(c->h_tot);
   cudaFreeHost(c->h_flag);
@@ -881,6 +894,180 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
                 "adjoint step %d: singular local-solve Jacobian at cell %lld",
                 c->h_status->fail_step, (long long)(c->h_status->fail_key >> 8));
   return RHD_OK;
+}
+
+// ------------------------------------------------ hydrodynamics (Sec. 3.1)
+
+static rhd_status hydro_ready(rhd_ctx* c) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  for (int d = 0; d < c->p.ndim; ++d)
+    if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
+      return fail(c, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (!c->hyd_w) {
+    const size_t N = (size_t)c->ncell;
+    CUDA_TRY(c, cudaMalloc(&c->hyd_w, sizeof(double) * 5 * N));
+    CUDA_TRY(c, cudaMalloc(&c->hyd_u1, sizeof(double) * 5 * N));
+    for (int d = 0; d < c->p.ndim; ++d)
+      CUDA_TRY(c, cudaMalloc(&c->hyd_f[d], sizeof(double) * 5 * hydro_faces(c->g, d)));
+    CUDA_TRY(c, cudaMalloc(&c->hyd_bits, sizeof(unsigned long long)));
+  }
+  return RHD_OK;
+}
+
+static HydroBufs hydro_bufs(rhd_ctx* c) {
+  HydroBufs b;
+  b.rho = c->rho;
+  b.y = c->ybuf[c->cur];
+  b.w = c->hyd_w;
+  b.u1 = c->hyd_u1;
+  for (int d = 0; d < 3; ++d) b.f[d] = c->hyd_f[d];
+  b.dt_bits = c->hyd_bits;
+  return b;
+}
+
+static rhd_status hydro_dt_of(rhd_ctx* c, double* dt) {
+  HydroBufs b = hydro_bufs(c);
+  CUDA_TRY(c, launch_hydro_speed(c->g, c->p.gamma, b, c->stream));
+  c->launches += 1;
+  unsigned long long bits = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&bits, c->hyd_bits, sizeof(bits), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  double smax;
+  memcpy(&smax, &bits, sizeof(smax));
+  if (!(smax > 0.0) || !std::isfinite(smax))
+    return fail(c, RHD_ERR_NONPHYSICAL, "a cell has rho <= 0 or p <= 0: no hydrodynamic step");
+  *dt = c->p.cfl_hydro / smax;
+  return RHD_OK;
+}
+
+// nsteps hydrodynamic steps of dt (dt <= 0: the CFL step of each state);
+// steps_done and the failure go to info; time advances by each step when
+// advance_time.
+static rhd_status hydro_run(rhd_ctx* c, int nsteps, double dt, rhd_step_info* info,
+                            bool advance_time) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->fail_cell = -1;
+    info->fail_step = -1;
+  }
+  const int launches_per_step = 5 + 2 * c->p.ndim;
+  int done = 0;
+  double last = dt;
+  rhd_status code = RHD_OK;
+  while (done < nsteps && code == RHD_OK) {
+    // fixed dt: every remaining step in one batch; else one step per CFL bound
+    int batch = dt > 0.0 ? nsteps - done : 1;
+    double h = dt;
+    if (!(h > 0.0)) {
+      rhd_status s = hydro_dt_of(c, &h);
+      if (s != RHD_OK) {
+        code = s;
+        break;
+      }
+    }
+    last = h;
+    CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+    c->launches += 1;
+    HydroBufs b = hydro_bufs(c);
+    for (int k = 0; k < batch; ++k) {
+      CUDA_TRY(c, launch_hydro_step(c->g, c->p.gamma, c->p.reconstruction, h, b, c->d_status,
+                                    k, c->stream));
+      c->launches += launches_per_step;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
+                                cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const DevStatus& st = *c->h_status;
+    int ok = batch;
+    c->eps_dirty = true;  // rho has changed
+    if (st.fail_key != ~0ull) {
+      code = (rhd_status)(st.fail_key & 0xffull);
+      ok = st.fail_step;
+      if (info) {
+        info->fail_cell = (int64_t)(st.fail_key >> 8);
+        info->fail_step = done + st.fail_step;
+        info->fail_stage = st.fail_stage;
+      }
+    }
+    done += ok;
+    if (advance_time) c->t += ok * h;
+  }
+  if (info) {
+    info->status = code;
+    info->steps_done = done;
+    info->t = c->t;
+    info->dt = last;
+  }
+  if (code != RHD_OK)
+    return fail(c, code, "hydrodynamic step %d failed (status %d)", done, (int)code);
+  return RHD_OK;
+}
+
+rhd_status rhd_hydro_dt(rhd_ctx* c, double* dt) {
+  rhd_status s = hydro_ready(c);
+  if (s != RHD_OK) return s;
+  if (!dt) return fail(c, RHD_ERR_ARG, "dt is NULL");
+  return hydro_dt_of(c, dt);
+}
+
+rhd_status rhd_hydro_step(rhd_ctx* c, int nsteps, double dt, rhd_step_info* info) {
+  rhd_status s = hydro_ready(c);
+  if (s == RHD_OK && nsteps < 0) s = fail(c, RHD_ERR_ARG, "nsteps < 0");
+  if (s == RHD_OK && !std::isfinite(dt)) s = fail(c, RHD_ERR_ARG, "dt is not finite");
+  if (s != RHD_OK) {
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->status = s;
+      info->fail_cell = -1;
+      info->fail_step = -1;
+    }
+    return s;
+  }
+  return hydro_run(c, nsteps, dt, info, true);
+}
+
+rhd_status rhd_step_split(rhd_ctx* c, int nsteps, double dt_h, rhd_step_info* info) {
+  rhd_status s = hydro_ready(c);
+  if (s == RHD_OK && nsteps < 0) s = fail(c, RHD_ERR_ARG, "nsteps < 0");
+  if (s == RHD_OK && !std::isfinite(dt_h)) s = fail(c, RHD_ERR_ARG, "dt_h is not finite");
+  rhd_step_info total;
+  memset(&total, 0, sizeof(total));
+  total.fail_cell = -1;
+  total.fail_step = -1;
+  total.t = c ? c->t : 0.0;
+  const double dt_rad = c ? rhd_default_dt(&c->p) : 0.0;
+  for (int k = 0; s == RHD_OK && k < nsteps; ++k) {
+    rhd_step_info one;
+    s = hydro_run(c, 1, dt_h, &one, false);
+    const double h = one.dt;
+    if (s == RHD_OK) {
+      int nsub = (int)std::ceil(h / dt_rad - 1e-12);
+      if (nsub < 1) nsub = 1;
+      s = rhd_step(c, nsub, h / nsub, &one);
+      total.max_newton = std::max(total.max_newton, one.max_newton);
+      total.max_outer = std::max(total.max_outer, one.max_outer);
+      total.sum_newton += one.sum_newton;
+      total.sum_outer += one.sum_outer;
+      total.n_solves += one.n_solves;
+    }
+    total.dt = h;
+    if (s != RHD_OK) {
+      total.fail_cell = one.fail_cell;
+      total.fail_step = k;
+      total.fail_stage = one.fail_stage;
+    } else {
+      total.steps_done = k + 1;
+    }
+  }
+  total.status = s;
+  if (c) total.t = c->t;
+  if (info) *info = total;
+  return s;
 }
 
 int64_t rhd_launch_count(const rhd_ctx* c) { return c ? c->launches : 0; }

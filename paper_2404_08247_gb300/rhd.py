@@ -73,6 +73,7 @@ class rhd_params(ctypes.Structure):
         ("kappa_P_ratio", ctypes.c_double),
         ("kappa_F_ratio", ctypes.c_double),
         ("reconstruction", ctypes.c_int),
+        ("cfl_hydro", ctypes.c_double),
     ]
 
 
@@ -129,6 +130,11 @@ SIGNATURES = {
                                        ctypes.POINTER(rhd_step_info)]),
     "rhd_adjoint": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int, ctypes.c_double, _V, _V]),
     "rhd_eval_recip": (ctypes.c_int, [_V, _I64, _V, _V]),
+    "rhd_hydro_dt": (ctypes.c_int, [_V, _D]),
+    "rhd_hydro_step": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(rhd_step_info)]),
+    "rhd_step_split": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(rhd_step_info)]),
     "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
                                         ctypes.POINTER(rhd_step_info)]),
     "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
@@ -224,6 +230,7 @@ def params_from_problem(prob: dict, precision: str | int = "fp64") -> rhd_params
     p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
     p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
     p.reconstruction = _RECON[prob.get("reconstruction", "plm")]
+    p.cfl_hydro = float(prob.get("cfl_hydro", 0.3))
     st = prob.get("bc_state", {})
     for d in range(3):
         for side in range(2):
@@ -354,6 +361,29 @@ class RHDContext:
     def sync(self, raise_on_error=True) -> dict:
         info = rhd_step_info()
         st = self.lib.rhd_sync(self.h, ctypes.byref(info))
+        if raise_on_error:
+            _check(st, self.h)
+        return info.as_dict()
+
+    def hydro_dt(self) -> float:
+        """dt of the hydrodynamic step of the current state (Sec. 3.1)."""
+        out = ctypes.c_double(0.0)
+        _check(self.lib.rhd_hydro_dt(self.h, ctypes.byref(out)), self.h)
+        return out.value
+
+    def hydro_step(self, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
+        """nsteps RK2-SSP steps of the hydrodynamic subsystem alone."""
+        info = rhd_step_info()
+        st = self.lib.rhd_hydro_step(self.h, int(nsteps), float(dt), ctypes.byref(info))
+        if raise_on_error:
+            _check(st, self.h)
+        return info.as_dict()
+
+    def step_split(self, nsteps: int = 1, dt_h: float = 0.0, raise_on_error=True) -> dict:
+        """nsteps operator-split steps: hydrodynamics, then the subcycled
+        radiation update (Sec. 3.1)."""
+        info = rhd_step_info()
+        st = self.lib.rhd_step_split(self.h, int(nsteps), float(dt_h), ctypes.byref(info))
         if raise_on_error:
             _check(st, self.h)
         return info.as_dict()

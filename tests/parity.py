@@ -1,7 +1,8 @@
 """Comparison helpers shared by the parity tests.
 
 Per-field error of a GPU state against the oracle's:
-  * positive fields (rho, Egas, Erad, kappa): max pointwise |a - b| / |b|;
+  * positive fields (rho, Egas, Erad, kappa): max pointwise |a - b| / |b|
+    (|a - b| where b = 0);
   * signed fields (m, F): ||a - b||_inf / ||b||_inf (pointwise relative error
     is meaningless where they cross zero).
 """
@@ -18,7 +19,10 @@ def field_errors(Ug, Uo):
         a = np.asarray(Ug[f], dtype=np.float64)
         b = np.asarray(Uo[f], dtype=np.float64)
         if f in POSITIVE:
-            errs[I.FIELDS[f]] = float(np.max(np.abs(a - b) / np.abs(b)))
+            # a field that is zero in the reference (kappa of a gas without
+            # coupling) is compared absolutely there
+            den = np.where(b != 0.0, np.abs(b), 1.0)
+            errs[I.FIELDS[f]] = float(np.max(np.abs(a - b) / den))
         else:
             s = float(np.max(np.abs(b)))
             d = float(np.max(np.abs(a - b)))

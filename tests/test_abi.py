@@ -163,3 +163,13 @@ def test_batch_refuses_ppm_before_touching_the_device(rhd):
     st = rhd.load().rhd_batch_init(probs, 2, ctypes.byref(h))
     assert st == rhd.RHD_ERR_ARG and not h.value
     assert b"PLM" in rhd.load().rhd_last_error(None)
+
+
+def test_hydro_cfl_is_validated(rhd):
+    assert rhd.rhd_params_default().cfl_hydro == 0.3
+    q = rhd.rhd_params_default()
+    q.cfl_hydro = 0.0
+    st, msg = rhd.rhd_params_validate(q)
+    assert st == rhd.RHD_ERR_ARG and "cfl_hydro" in msg
+    p = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16], cfl_hydro=0.2))
+    assert p.cfl_hydro == 0.2
