@@ -74,6 +74,8 @@ def parse(argv=None):
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the 512^2 differentiation workload")
     ap.add_argument("--adj-n", type=int, default=512)
+    ap.add_argument("--no-split", action="store_true",
+                    help="skip the hydrodynamic step and the operator-split step")
     ap.add_argument("--single-form", action="store_true",
                     help="time only --precision (default: FP64 and mixed)")
     return ap.parse_args(argv)
@@ -419,6 +421,63 @@ def run_adjoint(args, rhd, torch, rank, ws, dist, barrier):
     }
 
 
+# bytes per cell of one hydrodynamic step that the kernels must move (3-D):
+# per stage the primitives (read 5, write 5 fields), three face kernels
+# (read the primitives, write 5 face fluxes per cell each), the update (read
+# the state and the three axes' fluxes, write 5 fields), stage 2 also reading
+# the stage-1 state and committing (read 5, write 5): 8 B x (10 + 30 + 25)
+# + 8 B x (10 + 30 + 30 + 10)
+HYDRO_BYTES_PER_CELL = 8 * (10 + 30 + 25) + 8 * (10 + 30 + 30 + 10)
+
+
+def run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier):
+    """The hydrodynamic step (RK2-SSP, HLLC) and one operator-split step
+    (Sec. 3.1: hydrodynamics, then the subcycled radiation update) on the
+    same 256^3 box, FP64."""
+    stream = torch.cuda.current_stream()
+    N = int(np.prod(prob["n"]))
+    ctx = rhd.RHDContext(prob, "fp64", stream=stream)
+    ctx.set_state(Ud)
+    dt_h = ctx.hydro_dt()
+    ctx.hydro_step(3, dt_h)
+    ctx.set_state(Ud)
+    K = 5
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.hydro_step(K, dt_h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hydro_ms = reduce_max(e0.elapsed_time(e1), dist, "cuda") / K
+    ctx.set_state(Ud)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = ctx.step_split(1, dt_h)
+    torch.cuda.synchronize()
+    split_ms = reduce_max((time.perf_counter() - t0) * 1e3, dist, "cuda")
+    ctx.close()
+    nsub = info["n_solves"] // (2 * N)
+    peaks, _ = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    achieved = HYDRO_BYTES_PER_CELL * N / (hydro_ms * 1e-3) / 1e9
+    return {
+        "hydro": {"value": whole_job_rate(N, 1, ws, hydro_ms * 1e-3), "unit": UNIT,
+                  "ms_per_step": hydro_ms, "steps": K, "dt": dt_h,
+                  "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                               "unit": "GB/s", "frac": achieved / hbm,
+                               "bytes_per_cell": HYDRO_BYTES_PER_CELL,
+                               "note": "model of the multi-kernel step's traffic; the "
+                                       "face kernels' FP64 work (HLLC) is the bound"}},
+        "split": {"value": whole_job_rate(N, 1, ws, split_ms * 1e-3), "unit": UNIT,
+                  "ms_per_step": split_ms, "radiation_substeps": int(nsub),
+                  "hydro_share": hydro_ms / split_ms,
+                  "note": "host clock around rhd_step_split (two status reads per step)"},
+        "reconstruction": prob.get("reconstruction", "plm"),
+    }
+
+
 def run_ours(args):
     import torch
     from paper_2404_08247_gb300 import rhd
@@ -525,6 +584,10 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = run_adjoint(args, rhd, torch, rank, ws, dist, barrier)
 
+    split = None
+    if not args.no_split:
+        split = run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -558,6 +621,7 @@ def run_ours(args):
             "forms": form_lines,
             "batched": batched,
             "adjoint": adjoint,
+            "hydro_split": split,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -360,3 +360,32 @@ def marshak_wave_1d(n: int = 60, L: float = 0.66, scheme: str = "imex", cfl: flo
     U = equilibrium_state(prob, np.ones(sh), np.full(sh, T0), np.zeros((3,) + sh),
                           np.full(sh, 300.0))
     return prob, U
+
+
+A_RAD_CGS = 7.5657e-15   # radiation constant, erg cm^-3 K^-4
+K_B_CGS = 1.380649e-16   # erg K^-1
+
+
+def advecting_pulse_1d(v0: float = 1e6, n: int = 512, kappa: float = 100.0,
+                       T0: float = 1e7, T1: float = 2e7, rho0: float = 1.2, w: float = 24.0,
+                       mu: float = 3.9e-24, gamma: float = 5.0 / 3.0, **kw):
+    """The advecting radiation pulse of Sec. 5.3: a Gaussian temperature pulse
+    T = T0 + (T1 - T0) exp(-x^2 / 2w^2) on (-512, 512) cm (periodic, n cells),
+    the density rho = rho0 T0/T + (a mu / 3 k_B)(T0^4/T - T^3) that balances
+    gas and radiation pressure, gas and radiation at the same temperature
+    (radiation in comoving equilibrium), grey kappa = 100 cm^2 g^-1, the
+    Eddington closure, chat = c, uniform velocity v0 (0: the comoving run).
+    Returns (problem, state)."""
+    L = 1024.0
+    dx = L / n
+    prob = base_problem(1, [n], [dx], c=C_CGS, chat=C_CGS, a_rad=A_RAD_CGS,
+                        kB_over_mu=K_B_CGS / mu, gamma=gamma, closure="eddington",
+                        hll_mode="none", bc="periodic", **kw)
+    x = -0.5 * L + (np.arange(n) + 0.5) * dx
+    T = T0 + (T1 - T0) * np.exp(-x ** 2 / (2.0 * w * w))
+    rho = rho0 * T0 / T + A_RAD_CGS * mu / (3.0 * K_B_CGS) * (T0 ** 4 / T - T ** 3)
+    sh = (1, 1, n)
+    v = np.zeros((3,) + sh)
+    v[0] = v0
+    U = equilibrium_state(prob, rho.reshape(sh), T.reshape(sh), v, np.full(sh, kappa))
+    return prob, U
