@@ -76,6 +76,9 @@ def parse(argv=None):
     ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-split", action="store_true",
                     help="skip the hydrodynamic step and the operator-split step")
+    ap.add_argument("--hydro-only", action="store_true",
+                    help="time only the hydrodynamic step on the --n^3 box (for "
+                         "profiling); prints its own JSON line")
     ap.add_argument("--single-form", action="store_true",
                     help="time only --precision (default: FP64 and mixed)")
     return ap.parse_args(argv)
@@ -469,13 +472,41 @@ def run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier):
                                "unit": "GB/s", "frac": achieved / hbm,
                                "bytes_per_cell": HYDRO_BYTES_PER_CELL,
                                "note": "model of the multi-kernel step's traffic; the "
-                                       "face kernels' FP64 work (HLLC) is the bound"}},
+                                       "face kernels are bound by the FP64 pipe (84 % busy, "
+                                       "profiles/hydro_kernels_turbulent_box.md)"}},
         "split": {"value": whole_job_rate(N, 1, ws, split_ms * 1e-3), "unit": UNIT,
                   "ms_per_step": split_ms, "radiation_substeps": int(nsub),
                   "hydro_share": hydro_ms / split_ms,
                   "note": "host clock around rhd_step_split (two status reads per step)"},
         "reconstruction": prob.get("reconstruction", "plm"),
     }
+
+
+def run_hydro_only(args):
+    """2 + 3 hydrodynamic steps of the --n^3 box at its CFL step; one line."""
+    import torch
+    from paper_2404_08247_gb300 import build as B
+    B.build()
+    from paper_2404_08247_gb300 import rhd
+    rhd.load()
+    prob, U = workload(args)
+    Ud = torch.from_numpy(U).cuda()
+    ctx = rhd.RHDContext(prob, "fp64", stream=torch.cuda.current_stream())
+    ctx.set_state(Ud)
+    dt = ctx.hydro_dt()
+    ctx.hydro_step(2, dt)
+    ctx.set_state(Ud)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.hydro_step(3, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    ctx.close()
+    print(json.dumps({"hydro_only": True, "n": args.n, "reconstruction": args.reconstruction,
+                      "ms_per_step": ms, "value": args.n ** 3 / ms / 1e3, "unit": UNIT}))
+    return 0
 
 
 def run_ours(args):
@@ -633,6 +664,8 @@ def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.hydro_only:
+        return run_hydro_only(args)
     return run_ours(args)
 
 

@@ -110,8 +110,12 @@ __device__ __forceinline__ bool hllc(double g, double g1i, const double L[5], co
   const double uK = K[1 + D];
   double FK[5];
   euler_flux<D>(K, EK, FK);
-  const double fac = K[0] * dK / (SK - Ss);
-  const double Es = fac * (EK * rKi + (Ss - uK) * (Ss + K[4] * rKi / dK));
+  // one reciprocal serves 1/(S_K - S*) = d_K r and 1/d_K = (S_K - S*) r,
+  // r = 1/(d_K (S_K - S*)) (positive while S* lies between the bounds)
+  const double sK = SK - Ss, den = dK * sK;
+  const double r = pos_finite(den) ? rcp_pos(den) : 1.0 / den;
+  const double fac = K[0] * dK * dK * r;
+  const double Es = fac * (EK * rKi + (Ss - uK) * (Ss + K[4] * rKi * sK * r));
   F[0] = FK[0] + SK * (fac - K[0]);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
