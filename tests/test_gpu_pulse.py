@@ -2,14 +2,14 @@
 the paper's test of the full operator-split system, run on the GPU through
 rhd_step_split: a pulse in pressure balance carried at v0 = 1e6 cm/s (the
 lab-frame run) and the same pulse at rest (the comoving run), 512 cells,
-PPM faces (Sec. 3.3), chat = c, to t = 4.8e-5 s (about 2,800 hydrodynamic
-steps and 1.8 million radiation steps).
+kappa = 100 cm^2/g, PPM faces (Sec. 3.3), chat = c, to t = 4.8e-5 s (about
+3,100 hydrodynamic and 2.0 million radiation steps per frame).
 
-The paper reports that the two runs, the lab-frame one shifted back by
-v0 t, differ by less than 0.03 % in density and temperature anywhere, and
-that gas and radiation temperatures stay within 3e-9 of each other.  v0 t =
-48 cm is exactly 24 cells, so the comparison needs no interpolation.  One
-split step of the lab-frame run is also checked against the oracle."""
+The paper reports that the lab-frame run shifted back by v0 t differs from
+the comoving run by less than 0.03 % anywhere, and that gas and radiation
+temperatures stay within 3e-9 of each other.  v0 t = 48 cm is exactly 24
+cells, so the comparison needs no interpolation.  One split step of the
+lab-frame run is also checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -59,51 +59,72 @@ def test_split_step_of_the_pulse_matches_oracle(R, oracle_mod):
     assert_parity(Ug, Uo, 1e-11, "pulse split step")
 
 
+CASES = {
+    # Sec. 5.3 (static diffusion): (v0, cells, kappa, the paper's bound on the
+    # frame difference).  The dynamic-diffusion pulse of Sec. 5.4 (3e7 cm/s,
+    # 1,024 cells, kappa 500; 4.0 million radiation steps per frame) is a
+    # measurement recorded with the design notes, not a test: it takes eight
+    # minutes of GPU time.
+    "static": (1e6, 512, 100.0, 3e-4),
+}
+
+
 @pytest.fixture(scope="module")
 def runs(R):
-    """Both frames with the paper's PPM faces, at once: each context runs on
-    its own stream from its own host thread (the library releases the
-    interpreter during a call), so the two 512-cell runs share the GPU."""
+    """Every frame of both tests with the paper's PPM faces, at once: each
+    context runs on its own stream from its own host thread (the library
+    releases the interpreter during a call), so the small runs share the GPU.
+    Both frames of a test take the same fixed step (0.9 of the lab frame's
+    initial CFL step)."""
     from concurrent.futures import ThreadPoolExecutor
-    prob, U = I.advecting_pulse_1d(1e6, reconstruction="ppm")
-    with R.RHDContext(prob) as ctx:
-        ctx.set_state(U)
-        dth = ctx.hydro_dt()
-    nh = int(np.ceil(T_END / (0.9 * dth)))
+    jobs = []
+    for name, (v0, n, kappa, _) in CASES.items():
+        prob, U = I.advecting_pulse_1d(v0, n=n, kappa=kappa, reconstruction="ppm")
+        with R.RHDContext(prob) as ctx:
+            ctx.set_state(U)
+            nh = int(np.ceil(T_END / (0.9 * ctx.hydro_dt())))
+        jobs += [(name, v0, n, kappa, nh), (name, 0.0, n, kappa, nh)]
 
-    def run(v0):
-        prob, U = I.advecting_pulse_1d(v0, reconstruction="ppm")
+    def run(job):
+        name, v0, n, kappa, nh = job
+        prob, U = I.advecting_pulse_1d(v0, n=n, kappa=kappa, reconstruction="ppm")
         with R.RHDContext(prob) as ctx:
             ctx.set_state(U)
             info = ctx.step_split(nh, T_END / nh)
-            return prob, ctx.get_state(), info, ctx.time()
+            return prob, ctx.get_state(), info, ctx.time(), nh
 
-    with ThreadPoolExecutor(2) as ex:
-        res = dict(zip((1e6, 0.0), ex.map(run, (1e6, 0.0))))
-    for v0, (prob, U, info, t) in res.items():
+    with ThreadPoolExecutor(len(jobs)) as ex:
+        res = list(ex.map(run, jobs))
+    out = {}
+    for job, (prob, U, info, t, nh) in zip(jobs, res):
         assert info["steps_done"] == nh
         assert t == pytest.approx(T_END, rel=1e-12)
-    return {v0: r[:3] for v0, r in res.items()}
+        out[(job[0], job[1] != 0.0)] = (prob, U, info)
+    return out
 
 
-def test_advected_pulse_equals_the_comoving_pulse(runs):
-    prob, lab, _ = runs[1e6]
-    _, com, _ = runs[0.0]
-    shift = int(round(1e6 * T_END / prob["dx"][0]))
-    assert shift == 24
-    lab_s = np.roll(lab, -shift, axis=-1)
+@pytest.mark.parametrize("case", list(CASES))
+def test_advected_pulse_equals_the_comoving_pulse(runs, case):
+    v0, n, kappa, bound = CASES[case]
+    prob, lab, _ = runs[(case, True)]
+    _, com, _ = runs[(case, False)]
+    L = n * prob["dx"][0]
+    shift = (v0 * T_END % L) / prob["dx"][0]
+    assert abs(shift - round(shift)) < 1e-9
+    lab_s = np.roll(lab, -int(round(shift)), axis=-1)
     d_rho = np.max(np.abs(lab_s[I.F_RHO] - com[I.F_RHO]) / com[I.F_RHO])
     Tl, Tc = gas_T(prob, lab_s), gas_T(prob, com)
     d_T = np.max(np.abs(Tl - Tc) / Tc)
-    print("advected vs comoving: rho %.3e, T %.3e" % (d_rho, d_T))
-    assert d_rho < 3e-4 and d_T < 3e-4, (d_rho, d_T)
+    print("%s: advected vs comoving: rho %.3e, T %.3e" % (case, d_rho, d_T))
+    assert d_rho < bound and d_T < bound, (d_rho, d_T)
     # the pulse has diffused: the comparison is not between two unchanged states
-    _, U0 = I.advecting_pulse_1d(0.0)
+    _, U0 = I.advecting_pulse_1d(0.0, n=n, kappa=kappa)
     assert np.max(np.abs(Tc - gas_T(prob, U0)) / Tc) > 1e-2
 
 
 def test_gas_and_radiation_stay_in_equilibrium(runs):
-    prob, lab, _ = runs[1e6]
+    """Sec. 5.3: T_gas - T_rad below 3e-9 in the advected static-diffusion run."""
+    prob, lab, _ = runs[("static", True)]
     Tg, Tr = gas_T(prob, lab), rad_T(prob, lab)
     print("T_gas vs T_rad: %.3e" % np.max(np.abs(Tg - Tr) / Tg))
     assert np.max(np.abs(Tg - Tr) / Tg) < 3e-9
