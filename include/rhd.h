@@ -74,7 +74,8 @@ typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_EDDINGTON = 1 } rhd_closure;
  * per cell -- without contact steepening or flattening.  PPM reads three
  * cells on each side of a face, so a reflecting or inflow axis needs n >= 3;
  * a forward-Euler transport stage keeps E > 0 for CFL <= 1/3 with PPM (1/2
- * with PLM).  The batched form and rhd_adjoint take PLM only. */
+ * with PLM).  rhd_adjoint takes PLM only; a batch holding a PPM problem runs
+ * the default 2-D tile shape (rhd_batch_configure's tile2d is then ignored). */
 typedef enum { RHD_RECON_PLM = 0, RHD_RECON_PPM = 1 } rhd_recon;
 /* HLL energy-flux dissipation (Sec. 4.3): TAU scales it by
  * (1 - exp(-tau))/tau, tau = chi dx of the face; NONE is the paper's own
@@ -337,8 +338,8 @@ void rhd_destroy(rhd_ctx* ctx);
  * ------------------------------------------------------------------- */
 typedef struct rhd_batch rhd_batch;
 
-/* Validate and allocate nprob problems (probs[p].ndim must be 1 or 2, PLM
- * faces, one precision for all).  *out is NULL on error (message: rhd_last_error(NULL)). */
+/* Validate and allocate nprob problems (probs[p].ndim must be 1 or 2, one
+ * precision for all).  *out is NULL on error (message: rhd_last_error(NULL)). */
 rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out);
 
 /* Run on this CUDA stream (drops the captured graphs).  The legacy default

@@ -29,7 +29,8 @@ struct ProblemDesc {
 };
 
 struct WorkItem {
-  int prob, x0, y0, kind;  // kind 0: a 1-D row tile, 1: a 2-D tile
+  int prob, x0, y0, kind;  // kind 0: a 1-D row tile, 1: a 2-D tile; 2, 3: the same
+                           // with PPM faces
 };
 
 struct BatchArgs {
@@ -53,9 +54,13 @@ using Tile1 = TileT<1, 256, 1, 1>;
 using Tile2a = TileT<2, 32, 8, 1>;
 using Tile2b = TileT<2, 64, 4, 1>;
 using Tile2c = TileT<2, 16, 16, 1>;
+// PPM tiles (kinds 2, 3): the single-grid PPM shapes
+using Tile1P = TileT<1, 256, 1, 1, true>;
+using Tile2P = TileT<2, 32, 8, 1, true>;
 constexpr int kBatchThreads = 256;
 
-template <int STAGE, class T2, typename R, bool GEN>
+// PPMX: the batch holds PPM problems (the kernel then carries both tile kinds)
+template <int STAGE, class T2, typename R, bool GEN, bool PPMX>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item, s_skip;
@@ -94,25 +99,37 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
     for (int q = 0; q < 4; ++q) A.rate[q] = nullptr;
     if (w.kind == 0)
       stage_tile<STAGE, Tile1, R, GEN>(A, w.x0, 0, 0, smem_raw, ts);
-    else
+    else if (!PPMX || w.kind == 1)
       stage_tile<STAGE, T2, R, GEN>(A, w.x0, w.y0, 0, smem_raw, ts);
+    else if constexpr (PPMX) {
+      if (w.kind == 2)
+        stage_tile<STAGE, Tile1P, R, true>(A, w.x0, 0, 0, smem_raw, ts);
+      else
+        stage_tile<STAGE, Tile2P, R, true>(A, w.x0, w.y0, 0, smem_raw, ts);
+    }
   }
   flush_stats<kBatchThreads>(B.st, ts);
 }
 
-template <class T2, typename R>
+template <class T2, typename R, bool PPMX>
 size_t batch_smem() {
   size_t a = SmemT<Tile1, R>::BYTES, b = SmemT<T2, R>::BYTES;
-  return a > b ? a : b;
+  size_t m = a > b ? a : b;
+  if (PPMX) {
+    size_t c = SmemT<Tile1P, R>::BYTES, d = SmemT<Tile2P, R>::BYTES;
+    m = m > c ? m : c;
+    m = m > d ? m : d;
+  }
+  return m;
 }
 
-template <int STAGE, class T2, typename R, bool GEN>
+template <int STAGE, class T2, typename R, bool GEN, bool PPMX = false>
 cudaError_t launch_batch_t(const BatchArgs& B, int grid, cudaStream_t s) {
-  size_t sm = batch_smem<T2, R>();
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<STAGE, T2, R, GEN>,
+  size_t sm = batch_smem<T2, R, PPMX>();
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<STAGE, T2, R, GEN, PPMX>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  batch_kernel<STAGE, T2, R, GEN><<<grid, kBatchThreads, sm, s>>>(B);
+  batch_kernel<STAGE, T2, R, GEN, PPMX><<<grid, kBatchThreads, sm, s>>>(B);
   return cudaGetLastError();
 }
 
@@ -132,9 +149,17 @@ cudaError_t launch_batch_p(int stage, int tile2d, const BatchArgs& B, int grid,
                     : launch_batch_r<2, R, GEN>(tile2d, B, grid, s);
 }
 
-// general: some problem of the batch needs the general kernels
-cudaError_t launch_batch(int stage, int precision, bool general, int tile2d,
+// general: some problem of the batch needs the general kernels; ppm: some
+// problem has PPM faces (general kernels, the default 2-D tile shape)
+cudaError_t launch_batch(int stage, int precision, bool general, bool ppm, int tile2d,
                          const BatchArgs& B, int grid, cudaStream_t s) {
+  if (ppm) {
+    if (precision == RHD_PREC_MIXED)
+      return stage == 1 ? launch_batch_t<1, Tile2a, float, true, true>(B, grid, s)
+                        : launch_batch_t<2, Tile2a, float, true, true>(B, grid, s);
+    return stage == 1 ? launch_batch_t<1, Tile2a, double, true, true>(B, grid, s)
+                      : launch_batch_t<2, Tile2a, double, true, true>(B, grid, s);
+  }
   if (precision == RHD_PREC_MIXED)
     return general ? launch_batch_p<float, true>(stage, tile2d, B, grid, s)
                    : launch_batch_p<float, false>(stage, tile2d, B, grid, s);
@@ -182,6 +207,7 @@ struct rhd_batch {
   int tile2d = 0;
   int blocks_per_sm = 2;
   bool general = false;  // some problem needs the general kernels
+  bool ppm = false;      // some problem has PPM faces
   int items_tile = -1;  // tile shape the work list was built for
   struct Graph {
     int nsteps, cur0, tile2d, bps;
@@ -244,15 +270,18 @@ static void batch_release(rhd_batch* b) {
 static rhd_status build_items(rhd_batch* b) {
   if (b->items_tile == b->tile2d) return RHD_OK;
   std::vector<WorkItem> items;
-  const int tx = kTileX[b->tile2d], ty = kTileY[b->tile2d];
+  // a batch with PPM problems runs the default 2-D tile shape for all
+  const int shape = b->ppm ? 0 : b->tile2d;
+  const int tx = kTileX[shape], ty = kTileY[shape];
   for (int pass = 0; pass < 2; ++pass)
     for (int p = 0; p < b->nprob; ++p) {
       const Geometry& g = b->desc[p].g;
+      const int ppm = b->desc[p].ph.reconstruction == RHD_RECON_PPM ? 2 : 0;
       if (pass == 0 && g.ndim == 2) {
         for (int y0 = 0; y0 < g.n[1]; y0 += ty)
-          for (int x0 = 0; x0 < g.n[0]; x0 += tx) items.push_back({p, x0, y0, 1});
+          for (int x0 = 0; x0 < g.n[0]; x0 += tx) items.push_back({p, x0, y0, 1 + ppm});
       } else if (pass == 1 && g.ndim == 1) {
-        for (int x0 = 0; x0 < g.n[0]; x0 += 256) items.push_back({p, x0, 0, 0});
+        for (int x0 = 0; x0 < g.n[0]; x0 += 256) items.push_back({p, x0, 0, ppm});
       }
     }
   cudaFree(b->d_items);
@@ -277,8 +306,6 @@ rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out) {
       return bfail(nullptr, RHD_ERR_ARG, "problem %d: %s", p, msg);
     if (probs[p].ndim > 2)
       return bfail(nullptr, RHD_ERR_ARG, "problem %d: the batch takes 1-D and 2-D grids", p);
-    if (probs[p].reconstruction != RHD_RECON_PLM)
-      return bfail(nullptr, RHD_ERR_ARG, "problem %d: the batch takes PLM faces", p);
     if (probs[p].precision != probs[0].precision)
       return bfail(nullptr, RHD_ERR_ARG, "problem %d: all problems share one precision", p);
   }
@@ -292,6 +319,7 @@ rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out) {
   for (int p = 0; p < nprob; ++p) {
     fill_desc(&probs[p], b->desc[p]);
     b->general = b->general || needs_general(b->desc[p].g, b->desc[p].ph);
+    b->ppm = b->ppm || probs[p].reconstruction == RHD_RECON_PPM;
     b->desc[p].offset = off;
     b->offsets[p] = off;
     off += b->desc[p].g.ncell;
@@ -465,11 +493,13 @@ static rhd_status capture(rhd_batch* b, int nsteps, int cur0, cudaGraphExec_t* e
     B.yn = b->ybuf[cur];
     B.yo = b->yhalf;
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
-    if (e == cudaSuccess) e = launch_batch(1, b->precision, b->general, b->tile2d, B, grid, cs);
+    if (e == cudaSuccess)
+      e = launch_batch(1, b->precision, b->general, b->ppm, b->tile2d, B, grid, cs);
     B.yt = b->yhalf;
     B.yo = b->ybuf[cur ^ 1];
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
-    if (e == cudaSuccess) e = launch_batch(2, b->precision, b->general, b->tile2d, B, grid, cs);
+    if (e == cudaSuccess)
+      e = launch_batch(2, b->precision, b->general, b->ppm, b->tile2d, B, grid, cs);
     cur ^= 1;
   }
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

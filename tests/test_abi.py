@@ -154,17 +154,6 @@ def test_reconstruction_option_is_validated(rhd):
     assert p.reconstruction == rhd.RHD_RECON_PPM
 
 
-def test_batch_refuses_ppm_before_touching_the_device(rhd):
-    probs = (rhd.rhd_params * 2)()
-    for i in range(2):
-        probs[i] = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16]))
-    probs[1].reconstruction = rhd.RHD_RECON_PPM
-    h = ctypes.c_void_p()
-    st = rhd.load().rhd_batch_init(probs, 2, ctypes.byref(h))
-    assert st == rhd.RHD_ERR_ARG and not h.value
-    assert b"PLM" in rhd.load().rhd_last_error(None)
-
-
 def test_hydro_cfl_is_validated(rhd):
     assert rhd.rhd_params_default().cfl_hydro == 0.3
     q = rhd.rhd_params_default()

@@ -144,3 +144,29 @@ def test_ppm_marshak_wave_matches_oracle(R, oracle_mod, cfl):
         e = marshak_errors(Ug, Uo)
         assert e["erad_vs_etot"] <= TOL, (n, e)
         assert max(e["egas"], e["mx"], e["fx"]) <= 1e-8, (n, e)
+
+
+def test_batch_with_ppm_problems_equals_single_grids(R):
+    """The batched form runs PPM and PLM problems side by side (a batch with a
+    PPM problem runs the default 2-D tile shape), each bit for bit as alone,
+    in both precisions; the autotuner's tile choice is ignored."""
+    for precision in ("fp64", "mixed"):
+        probs = []
+        for i, (rec, n, extra) in enumerate((("ppm", (200,), {}), ("plm", (24, 20), {}),
+                                             ("ppm", (33, 17), {"scheme": "rk2ssp"}),
+                                             ("ppm", (3, 40), {"bc": "reflect"}),
+                                             ("plm", (96,), {"kappa_T_exp": -3.0}))):
+            kw = dict(c=1e3, chat=2e2, hll_mode="none", reconstruction=rec, cfl=0.3,
+                      newton_max_iter=400)
+            kw.update(extra)
+            prob = I.base_problem(len(n), n, tuple(1.0 / v for v in n), **kw)
+            probs.append((prob, I.random_state(prob, seed=800 + i, tau_range=(1e-2, 1e2))))
+        with R.RHDBatch([p for p, _ in probs], precision) as b:
+            b.configure(1, 2)
+            for i, (_, U) in enumerate(probs):
+                b.set_state(i, U)
+            b.step(3)
+            got = [b.get_state(i) for i in range(len(probs))]
+        for (p, U), G in zip(probs, got):
+            A, _, _, _ = run_gpu(R, p, U, 3, precision=precision)
+            assert np.array_equal(A, G), (precision, p["reconstruction"], p["n"])
