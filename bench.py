@@ -593,18 +593,26 @@ def run_ours(args):
         ctx.get_state(hout)
         barrier()
         torch.cuda.synchronize()
+        parts = [0.0, 0.0, 0.0]
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            ta = time.perf_counter()
             ctx.set_state(hin)
+            tb = time.perf_counter()
             ctx.step(1)
+            tc = time.perf_counter()
             ctx.get_state(hout)
+            td = time.perf_counter()
+            parts = [parts[0] + tb - ta, parts[1] + tc - tb, parts[2] + td - tc]
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         tt = max_over_ranks(t1 - t0)
         e2e = {"value": whole_job_rate(N, args.e2e_steps, ws, tt), "unit": UNIT,
                "h2d_bytes_per_step": int(hin.numel() * 8),
                "d2h_bytes_per_step": int(hout.numel() * 8),
-               "steps": args.e2e_steps, "precision": args.precision}
+               "steps": args.e2e_steps, "precision": args.precision,
+               "ms_per_step_parts": {k: 1e3 * v / args.e2e_steps for k, v in
+                                     zip(("set_state", "step", "get_state"), parts)}}
     ctx.close()
 
     batched = None
