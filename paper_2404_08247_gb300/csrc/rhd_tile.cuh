@@ -64,7 +64,10 @@ struct SmemT {
   static constexpr int RING = T::NPL * 4 * PS;         // doubles
   static constexpr int FX = 4 * T::TY * (T::TX + 1);   // x-face fluxes
   static constexpr int FY = T::NDIM >= 2 ? 4 * (T::TY + 1) * T::TX : 0;
-  static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY);
+  // PPM z march: each thread's carried right edge and interface value (kept
+  // in shared memory: in registers they push the FP64 kernel past its budget)
+  static constexpr int CZ = (T::PPM && T::NDIM == 3) ? 8 * T::NT : 0;
+  static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY + CZ);
 };
 
 // Coordinate x >= -3 folded onto [0, n) by the boundary condition (padding
@@ -291,8 +294,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   // PPM z march: the constrained right edge of the current cell and the
   // interface value above it, carried from plane to plane, so each plane
   // adds one cell's edges; the start reads the own column from memory
-  R rz[4] = {R(0), R(0), R(0), R(0)};
-  R az[4] = {R(0), R(0), R(0), R(0)};
+  R* rz = fys + S::FY + threadIdx.x;       // rz[q * NT]: right edge of cell k
+  R* az = rz + 4 * NT;                      // az[q * NT]: interface value a(k+1/2)
   if constexpr (NDIM == 3 && T::PPM) {
     R u[6][4];
 #pragma unroll
@@ -309,8 +312,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       const R a34 = ppm_interface(u[3][q], u[4][q], h3, h4);
       L[q] = ppm_edge_of<false>(u[2][q], a12, a23);
       Rr[q] = ppm_edge_of<true>(u[3][q], a23, a34);
-      rz[q] = ppm_edge_of<false>(u[3][q], a23, a34);
-      az[q] = a34;
+      rz[q * NT] = ppm_edge_of<false>(u[3][q], a23, a34);
+      az[q * NT] = a34;
     }
     R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
     zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
@@ -365,10 +368,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         const R ha = half_slope(v0[q], v1[q], v2[q]);
         const R hb = half_slope(v1[q], v2[q], v3[q]);
         const R an = ppm_interface(v1[q], v2[q], ha, hb);
-        L[q] = rz[q];
-        Rr[q] = ppm_edge_of<true>(v1[q], az[q], an);
-        rz[q] = ppm_edge_of<false>(v1[q], az[q], an);
-        az[q] = an;
+        L[q] = rz[q * NT];
+        Rr[q] = ppm_edge_of<true>(v1[q], az[q * NT], an);
+        rz[q * NT] = ppm_edge_of<false>(v1[q], az[q * NT], an);
+        az[q * NT] = an;
       }
       R eps = (R)face_eps(A, 2, cx, cy, k);
       zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
