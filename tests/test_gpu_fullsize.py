@@ -20,11 +20,76 @@ RAD = 4
 
 
 @pytest.fixture(scope="module")
-def big():
+def box():
+    """The 256^3 turbulent box (generated once for the module)."""
     from paper_2404_08247_gb300 import build as B
     B.build()
-    from paper_2404_08247_gb300 import rhd
     prob, U, _ = I.turbulent_box_3d(n=256)
+    return prob, U
+
+
+def one_step(prob, U, precision="fp64"):
+    from paper_2404_08247_gb300 import rhd
+    Ud = torch.from_numpy(U).cuda()
+    with rhd.RHDContext(prob, precision, stream=torch.cuda.current_stream()) as ctx:
+        ctx.set_state(Ud)
+        info = ctx.step(1)
+        out = torch.empty_like(Ud)
+        ctx.get_state(out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), info["dt"]
+
+
+def sampled_worst(oracle_mod, prob, U, Ug, dt, rad, seed):
+    """Largest per-field error at 48 sampled cells (two corners) against the
+    oracle stepping the (2 rad + 1)^3 periodic block around each cell."""
+    n = prob["n"][0]
+    rng = np.random.default_rng(seed)
+    cells = rng.integers(0, n, size=(48, 3))
+    cells[0] = (0, 0, 0)
+    cells[1] = (n - 1, n - 1, n - 1)
+    w = 2 * rad + 1
+    sub = I.base_problem(3, [w, w, w], prob["dx"], **{k: prob[k] for k in (
+        "c", "chat", "gamma", "a_rad", "kB_over_mu", "cfl", "closure", "vc_order",
+        "hll_mode", "newton_rtol", "outer_rtol", "newton_max_iter", "outer_max_iter")},
+        reconstruction=prob.get("reconstruction", "plm"))
+    worst = 0.0
+    for (i, j, k) in cells:
+        zi = (np.arange(k - rad, k + rad + 1) % n)
+        yi = (np.arange(j - rad, j + rad + 1) % n)
+        xi = (np.arange(i - rad, i + rad + 1) % n)
+        blk = np.ascontiguousarray(U[:, zi][:, :, yi][:, :, :, xi])
+        oracle_mod.step(sub, blk, nsteps=1, dt=dt)
+        for f in range(I.NFIELD):
+            b = blk[f, rad, rad, rad]
+            a = Ug[f, k, j, i]
+            scale = abs(b) if f in (I.F_RHO, I.F_EGAS, I.F_ERAD, I.F_KAPPA) else \
+                np.abs(blk[f]).max()
+            e = abs(a - b) / scale if scale > 0 else abs(a)
+            worst = max(worst, e)
+    return worst
+
+
+def test_fullsize_ppm_sampled_cells_match_oracle(box, oracle_mod):
+    """The PPM form as bench.py times it: a step depends on the state within
+    6 cells (3 per stage), so 13^3 blocks reproduce sampled cells."""
+    prob, U = box
+    prob = dict(prob, reconstruction="ppm")
+    Ug, dt = one_step(prob, U)
+    assert sampled_worst(oracle_mod, prob, U, Ug, dt, 6, 2026) <= TOL
+
+
+def test_fullsize_mixed_sampled_cells_match_oracle(box, oracle_mod):
+    """The mixed form as bench.py times it, against the FP64 oracle: 1e-5."""
+    prob, U = box
+    Ug, dt = one_step(prob, U, "mixed")
+    assert sampled_worst(oracle_mod, prob, U, Ug, dt, RAD, 2027) <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def big(box):
+    from paper_2404_08247_gb300 import rhd
+    prob, U = box
     Ud = torch.from_numpy(U).cuda()
     with rhd.RHDContext(prob, stream=torch.cuda.current_stream()) as ctx:
         ctx.set_state(Ud)
@@ -83,11 +148,11 @@ def test_fullsize_conservation_and_sanity(big):
 
 
 @pytest.fixture(scope="module")
-def big_hydro():
+def big_hydro(box):
     """One hydrodynamic step (RK2-SSP, HLLC, PLM) of the same 256^3 box at its
     CFL step, as bench.py's hydro_split leg times it."""
     from paper_2404_08247_gb300 import rhd
-    prob, U, _ = I.turbulent_box_3d(n=256)
+    prob, U = box
     Ud = torch.from_numpy(U).cuda()
     with rhd.RHDContext(prob, stream=torch.cuda.current_stream()) as ctx:
         ctx.set_state(Ud)
