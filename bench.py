@@ -48,6 +48,13 @@ UNIT = "Mcell-updates/s"
 ALG_BYTES = {0: 8 * (8 + 2 + 8), 1: 8 * (8 + 8 + 2 + 8)}
 KERNEL_NAMES = {0: "stage1", 1: "stage2"}
 FALLBACK_HBM_GBS = 6800.0
+# FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA per
+# clock x 2 flops x 2.07 GHz (the probe of the design notes measured 600 G
+# DFMA/s, 95 % of it)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 flops per face of the hydrodynamic face kernel (PLM, ncu thread
+# counts dadd + dmul + 2 dfma at 128^3; profiles/hydro_kernels_turbulent_box.md)
+HYDRO_FACE_FLOPS = 210
 
 
 def parse(argv=None):
@@ -465,6 +472,9 @@ def run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier):
     peaks, _ = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     achieved = HYDRO_BYTES_PER_CELL * N / (hydro_ms * 1e-3) / 1e9
+    nd = prob["ndim"]
+    faces = sum(N // prob["n"][d] * (prob["n"][d] + 1) for d in range(nd))
+    fp64_face = 2 * faces * HYDRO_FACE_FLOPS
     return {
         "hydro": {"value": whole_job_rate(N, 1, ws, hydro_ms * 1e-3), "unit": UNIT,
                   "ms_per_step": hydro_ms, "steps": K, "dt": dt_h,
@@ -473,7 +483,15 @@ def run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier):
                                "bytes_per_cell": HYDRO_BYTES_PER_CELL,
                                "note": "model of the multi-kernel step's traffic; the "
                                        "face kernels are bound by the FP64 pipe (84 % busy, "
-                                       "profiles/hydro_kernels_turbulent_box.md)"}},
+                                       "profiles/hydro_kernels_turbulent_box.md)",
+                               "fp64_view": {
+                                   "achieved": fp64_face / (hydro_ms * 1e-3) / 1e12,
+                                   "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": fp64_face / (hydro_ms * 1e-3) / 1e12
+                                           / FP64_PEAK_TFLOPS,
+                                   "note": "the face kernels' flops only (2 stages x ndim "
+                                           "axes x faces x HYDRO_FACE_FLOPS) over the "
+                                           "whole step"}}},
         "split": {"value": whole_job_rate(N, 1, ws, split_ms * 1e-3), "unit": UNIT,
                   "ms_per_step": split_ms, "radiation_substeps": int(nsub),
                   "hydro_share": hydro_ms / split_ms,
@@ -556,32 +574,56 @@ def run_ours(args):
     ms = head["ms"]
     value = whole_job_rate(N, args.steps, ws, ms * 1e-3)
 
-    # dominant kernel roofline (HBM view)
+    # dominant kernel roofline: the FP64 pipe (its bound) when the committed
+    # ncu counts belong to these kernel sources, with the HBM view beside it
     peaks, peak_src = measured_peaks()
     kms, klaunch = head["kms"], head["klaunch"]
     dom = max((0, 1), key=lambda k: kms[k])
     avg_ms = kms[dom] / max(klaunch[dom], 1)
-    achieved = ALG_BYTES[dom] * N / (avg_ms * 1e-3) / 1e9
-    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    hbm_achieved = ALG_BYTES[dom] * N / (avg_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     rec = stage_traffic_record() if args.precision == "fp64" else None
-    traffic = rec["dram_bytes_per_cell"][KERNEL_NAMES[dom]] * N if rec else None
-    roofline = {
-        "bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak,
-        "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-        "traffic_source": ("ncu dram__bytes_read+write per cell at 128^3 x cells "
-                           "(profiles/stage_kernel_traffic.json)") if rec else None,
-        "fp64_pipe_busy": ({"while_active": rec["fp64_pipe_busy_active"][KERNEL_NAMES[dom]],
-                            "of_elapsed_128": rec["fp64_pipe_busy_elapsed"][KERNEL_NAMES[dom]]}
-                           if rec else None),
+    kname = KERNEL_NAMES[dom]
+    traffic = rec["dram_bytes_per_cell"][kname] * N if rec else None
+    hbm_view = {
+        "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+        "frac": hbm_achieved / hbm_peak, "alg_bytes_per_cell": ALG_BYTES[dom],
         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
         if peak_src == "measured" else "fallback",
-        "alg_bytes_per_cell": ALG_BYTES[dom],
+    }
+    common = {
+        "kernel": kname, "traffic": traffic,
+        "traffic_source": ("ncu dram__bytes_read+write per cell at 128^3 x cells "
+                           "(profiles/stage_kernel_traffic.json)") if rec else None,
+        "fp64_pipe_busy": ({"while_active": rec["fp64_pipe_busy_active"][kname],
+                            "of_elapsed_128": rec["fp64_pipe_busy_elapsed"][kname]}
+                           if rec else None),
         "avg_launch_ms": avg_ms,
         "kernel_ms": {KERNEL_NAMES[k]: kms[k] / max(klaunch[k], 1) for k in (0, 1)},
-        "step_alg_bytes_per_cell_min": 144,
-        "note": "the FP64 stage kernels are bound by the FP64 pipe (ncu: 85 % busy "
-                "while active), not by HBM; see profiles/stage_kernel_fp64_turbulent_box.md",
     }
+    if rec and "fp64_flop_per_cell" in rec:
+        flops = rec["fp64_flop_per_cell"][kname]
+        achieved = flops * N / (avg_ms * 1e-3) / 1e12
+        roofline = dict(
+            {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+             "flop_per_cell": flops,
+             "flop_source": "ncu thread counts dadd + dmul + 2 dfma per cell at 128^3 "
+                            "(profiles/stage_kernel_traffic.json) x cells",
+             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
+             "hbm_view": hbm_view,
+             "note": "FP64-pipe bound: the fraction of the FP64 flop peak also loses "
+                     "the lanes idle in the per-cell iterations and the FP64-pipe "
+                     "slots of adds and multiplies (1 flop) against FMAs (2)"},
+            **common)
+    else:
+        roofline = dict(
+            {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+             "frac": hbm_achieved / hbm_peak, "alg_bytes_per_cell": ALG_BYTES[dom],
+             "peak_source": hbm_view["peak_source"],
+             "note": "the stage kernels are bound by the FP64 pipe (ncu: 85 % busy while "
+                     "active), not by HBM; see profiles/stage_kernel_fp64_turbulent_box.md"},
+            **common)
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -644,7 +686,7 @@ def run_ours(args):
                 "ms_per_step": r["ms"] / args.steps,
                 "kernel_ms": {KERNEL_NAMES[k]: r["kms"][k] / max(r["klaunch"][k], 1)
                               for k in (0, 1)},
-                "hbm_frac_144B": 144 * N * args.steps / (r["ms"] * 1e-3) / 1e9 / peak,
+                "hbm_frac_144B": 144 * N * args.steps / (r["ms"] * 1e-3) / 1e9 / hbm_peak,
                 "mean_newton": inf["sum_newton"] / max(inf["n_solves"], 1),
                 "mean_outer": inf["sum_outer"] / max(inf["n_solves"], 1),
                 "max_newton": inf["max_newton"], "max_outer": inf["max_outer"],
