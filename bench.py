@@ -83,6 +83,9 @@ def parse(argv=None):
     ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-split", action="store_true",
                     help="skip the hydrodynamic step and the operator-split step")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the 512-problem batched workload (for profiling); "
+                         "prints its own JSON line")
     ap.add_argument("--hydro-only", action="store_true",
                     help="time only the hydrodynamic step on the --n^3 box (for "
                          "profiling); prints its own JSON line")
@@ -716,6 +719,15 @@ def main(argv=None):
         return run_reference(args)
     if args.hydro_only:
         return run_hydro_only(args)
+    if args.batched_only:
+        import torch
+        from paper_2404_08247_gb300 import build as B
+        B.build()
+        from paper_2404_08247_gb300 import rhd
+        rhd.load()
+        r = run_batched(args, rhd, torch, 0, 1, None, lambda: None)
+        print(json.dumps(dict(r, batched_only=True)))
+        return 0
     return run_ours(args)
 
 
