@@ -178,3 +178,35 @@ def test_split_in_mixed_precision(R, oracle_mod):
     for d in range(3):
         scale = (np.abs(Ug[I.F_MX + d]).sum() + np.abs(Ug[I.F_FX + d]).sum() / cc) * V
         assert abs(t1[1 + d] - t0[1 + d]) <= 1e-13 * scale
+
+
+def test_edge_cases(R):
+    """Zero steps change nothing; a one-cell periodic grid (every ghost is the
+    cell itself) keeps its state exactly; a state with negative pressure has
+    no hydrodynamic step (nonphysical, state untouched)."""
+    prob = I.base_problem(2, [12, 10], [1 / 12, 1 / 10], gamma=1.4)
+    U = random_gas(prob, 3)
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        info = ctx.hydro_step(0)
+        assert info["steps_done"] == 0 and np.array_equal(ctx.get_state(), U)
+        info = ctx.step_split(0)
+        assert info["steps_done"] == 0 and np.array_equal(ctx.get_state(), U)
+    for ndim in (1, 3):
+        n = [1] * ndim
+        p1 = I.base_problem(ndim, n, [1.0] * ndim, gamma=1.4)
+        U1 = random_gas(p1, 4)
+        with R.RHDContext(p1) as ctx:
+            ctx.set_state(U1)
+            ctx.hydro_step(3, 0.1)
+            assert np.array_equal(ctx.get_state(), U1)
+    Ub = U.copy()
+    Ub[I.F_EGAS, 0, 3, 4] = 0.25 * Ub[I.F_RHO, 0, 3, 4] * (
+        (Ub[I.F_MX, 0, 3, 4] / Ub[I.F_RHO, 0, 3, 4]) ** 2)  # below the kinetic energy
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(Ub)
+        with pytest.raises(R.RHDError, match="rho <= 0 or p <= 0"):
+            ctx.hydro_dt()
+        info = ctx.hydro_step(1, raise_on_error=False)
+        assert info["status"] == R.RHD_ERR_NONPHYSICAL and info["steps_done"] == 0
+        assert np.array_equal(ctx.get_state(), Ub)
