@@ -175,7 +175,7 @@ def make_params(prob: dict) -> OrcParams:
     p.kappa_T_ref = float(prob.get("kappa_T_ref", 1.0))
     p.kappa_P_ratio = float(prob.get("kappa_P_ratio", 1.0))
     p.kappa_F_ratio = float(prob.get("kappa_F_ratio", 1.0))
-    p.reconstruction = {"plm": 0, "ppm": 1}[prob.get("reconstruction", "plm")]
+    p.reconstruction = {"plm": 0, "ppm": 1, "ppm_cs": 2}[prob.get("reconstruction", "plm")]
     p.cfl_hydro = float(prob.get("cfl_hydro", 0.3))
     # bc_state[d][side] = (E, Fx, Fy, Fz) of inflow faces; default E = 1, F = 0
     st = prob.get("bc_state", {})

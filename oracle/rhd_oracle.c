@@ -152,6 +152,76 @@ static void ppm_edges(const double u[5], double* aL, double* aR) {
   *aR = r;
 }
 
+/* The PPM limiter of Colella & Sekora (2008), which keeps smooth extrema
+ * (the option ORC_RECON_PPM_CS; C = 1.25).  Interface value between cells j
+ * and j+1 from u_{j-1} .. u_{j+2}: the fourth-order value
+ * 7/12 (u_j + u_{j+1}) - 1/12 (u_{j-1} + u_{j+2}); if it does not lie
+ * between u_j and u_{j+1}, its second difference 3 (u_j - 2a + u_{j+1}) is
+ * limited against the second differences of the cells on either side (the
+ * smallest magnitude if all three share a sign, else zero) and
+ * a = (u_j + u_{j+1})/2 - D2_lim/6. */
+static const double CS_C = 1.25;
+
+static int same_sign3(double a, double b, double c) {
+  return (a > 0.0 && b > 0.0 && c > 0.0) || (a < 0.0 && b < 0.0 && c < 0.0);
+}
+
+static double cs_interface(double um, double u0, double up, double upp) {
+  double a = 7.0 / 12.0 * (u0 + up) - 1.0 / 12.0 * (um + upp);
+  if ((a - u0) * (up - a) < 0.0) {
+    double d2 = 3.0 * (u0 - 2.0 * a + up);
+    double d2l = um - 2.0 * u0 + up;
+    double d2r = u0 - 2.0 * up + upp;
+    double lim = 0.0;
+    if (same_sign3(d2, d2l, d2r)) {
+      double m = fmin(CS_C * fabs(d2), fmin(fabs(d2l), fabs(d2r)));
+      lim = d2 > 0.0 ? m : -m;
+    }
+    a = 0.5 * (u0 + up) - lim / 6.0;
+  }
+  return a;
+}
+
+/* Edge values (aL, aR) of cell j from u_{j-2} .. u_{j+2} with the
+ * Colella-Sekora constraint: at a local extremum (of the edge values or of
+ * the cell averages) the parabola's curvature -12 u_j + 6 (aL + aR) is
+ * limited against C times the second differences of cells j-1, j and j+1
+ * (smallest magnitude if all share its sign, else zero) and both edges are
+ * scaled towards u_j by the ratio; elsewhere an edge more than twice as far
+ * from u_j as the other is moved to twice that distance (as in the
+ * Colella-Woodward constraint), so the parabola stays monotone. */
+static void ppm_cs_edges(const double u[5], double* aL, double* aR) {
+  double l = cs_interface(u[0], u[1], u[2], u[3]);
+  double r = cs_interface(u[1], u[2], u[3], u[4]);
+  const double u0 = u[2];
+  if ((r - u0) * (u0 - l) <= 0.0 || (u[1] - u0) * (u0 - u[3]) <= 0.0) {
+    double d2 = -12.0 * u0 + 6.0 * (l + r);
+    double d2c = u[1] - 2.0 * u0 + u[3];
+    double d2l = u[0] - 2.0 * u[1] + u0;
+    double d2r = u0 - 2.0 * u[3] + u[4];
+    double lim = 0.0;
+    if (same_sign3(d2, d2c, d2l) && same_sign3(d2, d2c, d2r)) {
+      double m = fmin(fabs(d2), CS_C * fmin(fabs(d2c), fmin(fabs(d2l), fabs(d2r))));
+      lim = d2 > 0.0 ? m : -m;
+    }
+    if (d2 != 0.0) {
+      double fac = lim / d2;
+      l = u0 + (l - u0) * fac;
+      r = u0 + (r - u0) * fac;
+    } else {
+      l = r = u0;
+    }
+  } else {
+    double dl = u0 - l, dr = r - u0;
+    if (fabs(dr) >= 2.0 * fabs(dl))
+      r = u0 + 2.0 * dl;
+    else if (fabs(dl) >= 2.0 * fabs(dr))
+      l = u0 - 2.0 * dr;
+  }
+  *aL = l;
+  *aR = r;
+}
+
 /* Face states of the face between s[2] and s[3] along axis d from the
  * stencil s[0..5] (cells i-2 .. i+3): E and F.
  *   PLM (reading: Sec. 3.3 uses PPM; PLM with the monotonised-central
@@ -160,13 +230,15 @@ static void ppm_edges(const double u[5], double* aL, double* aR) {
  *   PPM: the right edge value of s[2] | the left edge value of s[3]. */
 static void face_states(const orc_params* p, const rad_cell* s, double* EL, double FL[3],
                         double* ER, double FR[3]) {
-  if (p->reconstruction == ORC_RECON_PPM) {
+  if (p->reconstruction == ORC_RECON_PPM || p->reconstruction == ORC_RECON_PPM_CS) {
+    void (*edges)(const double*, double*, double*) =
+        p->reconstruction == ORC_RECON_PPM ? ppm_edges : ppm_cs_edges;
     double u[6], l, r;
     for (int q = 0; q < 4; ++q) {
       for (int k = 0; k < 6; ++k) u[k] = q == 0 ? s[k].E : s[k].F[q - 1];
-      ppm_edges(u, &l, &r);       /* cell s[2] */
+      edges(u, &l, &r);       /* cell s[2] */
       double left = r;
-      ppm_edges(u + 1, &l, &r);   /* cell s[3] */
+      edges(u + 1, &l, &r);   /* cell s[3] */
       if (q == 0) {
         *EL = left;
         *ER = l;
@@ -621,3 +693,7 @@ void orc_totals(const orc_params* p, const double* U, double out[4]) {
 double orc_recon_mc_slope(double um, double u0, double up) { return mc_slope(um, u0, up); }
 
 void orc_recon_ppm_edges(const double u[5], double* aL, double* aR) { ppm_edges(u, aL, aR); }
+
+void orc_recon_ppm_cs_edges(const double u[5], double* aL, double* aR) {
+  ppm_cs_edges(u, aL, aR);
+}

@@ -33,7 +33,7 @@ enum { ORC_RHO = 0, ORC_MX, ORC_MY, ORC_MZ, ORC_EGAS, ORC_ERAD, ORC_FX, ORC_FY,
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_REFLECT = 1, ORC_BC_INFLOW = 2 };
 enum { ORC_SCHEME_IMEX = 0, ORC_SCHEME_RK2_SSP = 1 };
-enum { ORC_RECON_PLM = 0, ORC_RECON_PPM = 1 };
+enum { ORC_RECON_PLM = 0, ORC_RECON_PPM = 1, ORC_RECON_PPM_CS = 2 };
 enum { ORC_CLOSURE_M1 = 0, ORC_CLOSURE_EDDINGTON = 1 };
 enum { ORC_HLL_TAU = 0, ORC_HLL_NONE = 1 };
 
@@ -137,6 +137,7 @@ int orc_split_step(const orc_params* p, double* U, double dt_h, orc_info* info,
 /* the transport's reconstruction, shared with the hydrodynamic subsystem */
 double orc_recon_mc_slope(double um, double u0, double up);
 void orc_recon_ppm_edges(const double u[5], double* aL, double* aR);
+void orc_recon_ppm_cs_edges(const double u[5], double* aL, double* aR);
 
 int orc_step_tape(const orc_params* p, double* U, double dt, double* tape);
 

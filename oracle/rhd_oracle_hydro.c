@@ -12,7 +12,8 @@
  *   - state (rho, m, E_gas), E_gas the total gas energy, ideal gas
  *     p = (gamma - 1)(E_gas - |m|^2 / (2 rho));
  *   - face states: the primitives (rho, v, p) reconstructed with the
- *     transport's option (PLM with the MC limiter, or PPM), per component;
+ *     transport's option (PLM with the MC limiter, PPM, or PPM with the
+ *     Colella-Sekora limiter), per component;
  *   - fluxes: the HLLC Riemann solver (Toro, Spruce & Speares 1994) with
  *     the wave-speed bounds S_L = min(u_L - a_L, u_R - a_R),
  *     S_R = max(u_L + a_L, u_R + a_R) (Davis 1988);
@@ -96,10 +97,12 @@ static void hface_states(const orc_params* p, const prim s[6], prim* L, prim* R)
     double u[6];
     for (int o = 0; o < 6; ++o) u[o] = comp(&s[o], k);
     double l, r;
-    if (p->reconstruction == ORC_RECON_PPM) {
+    if (p->reconstruction == ORC_RECON_PPM || p->reconstruction == ORC_RECON_PPM_CS) {
+      void (*edges)(const double*, double*, double*) =
+          p->reconstruction == ORC_RECON_PPM ? orc_recon_ppm_edges : orc_recon_ppm_cs_edges;
       double al, ar, bl, br;
-      orc_recon_ppm_edges(u, &al, &ar);     /* cell s[2] */
-      orc_recon_ppm_edges(u + 1, &bl, &br); /* cell s[3] */
+      edges(u, &al, &ar);     /* cell s[2] */
+      edges(u + 1, &bl, &br); /* cell s[3] */
       l = ar;
       r = bl;
     } else {
