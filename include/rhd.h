@@ -76,7 +76,14 @@ typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_EDDINGTON = 1 } rhd_closure;
  * a forward-Euler transport stage keeps E > 0 for CFL <= 1/3 with PPM (1/2
  * with PLM).  rhd_adjoint takes PLM only; a batch holding a PPM problem runs
  * the default 2-D tile shape (rhd_batch_configure's tile2d is then ignored). */
-typedef enum { RHD_RECON_PLM = 0, RHD_RECON_PPM = 1 } rhd_recon;
+/* PPM_CS: PPM with the limiter of Colella & Sekora (2008), which keeps
+ * smooth extrema (fourth order there, where PPM's constraint flattens the
+ * cell): interface values limited through second differences, and at an
+ * extremum the parabola's curvature limited against C = 1.25 times the
+ * neighbouring second differences.  It does not keep an edge within its
+ * neighbours' range, so on rough data a face state can turn nonphysical
+ * where PPM's would not.  Same stencil, n >= 3 rule and restrictions as PPM. */
+typedef enum { RHD_RECON_PLM = 0, RHD_RECON_PPM = 1, RHD_RECON_PPM_CS = 2 } rhd_recon;
 /* HLL energy-flux dissipation (Sec. 4.3): TAU scales it by
  * (1 - exp(-tau))/tau, tau = chi dx of the face; NONE is the paper's own
  * uncorrected IMEX choice. */

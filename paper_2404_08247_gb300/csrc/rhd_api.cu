@@ -236,9 +236,10 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
            RHD_ERR_ARG;
   if (!(p->cfl_hydro > 0.0) || !std::isfinite(p->cfl_hydro))
     return bad(msg, msglen, "cfl_hydro must be positive"), RHD_ERR_ARG;
-  if (p->reconstruction != RHD_RECON_PLM && p->reconstruction != RHD_RECON_PPM)
+  if (p->reconstruction != RHD_RECON_PLM && p->reconstruction != RHD_RECON_PPM &&
+      p->reconstruction != RHD_RECON_PPM_CS)
     return bad(msg, msglen, "reconstruction is not an rhd_recon"), RHD_ERR_ARG;
-  if (p->reconstruction == RHD_RECON_PPM)
+  if (p->reconstruction != RHD_RECON_PLM)
     for (int d = 0; d < p->ndim; ++d)
       if (p->bc[d][0] != RHD_BC_PERIODIC && p->n[d] < 3)
         return bad(msg, msglen, "PPM on a reflecting or inflow axis %d needs n >= 3", d),

@@ -276,7 +276,7 @@ static rhd_status build_items(rhd_batch* b) {
   for (int pass = 0; pass < 2; ++pass)
     for (int p = 0; p < b->nprob; ++p) {
       const Geometry& g = b->desc[p].g;
-      const int ppm = b->desc[p].ph.reconstruction == RHD_RECON_PPM ? 2 : 0;
+      const int ppm = b->desc[p].ph.reconstruction != RHD_RECON_PLM ? 2 : 0;
       if (pass == 0 && g.ndim == 2) {
         for (int y0 = 0; y0 < g.n[1]; y0 += ty)
           for (int x0 = 0; x0 < g.n[0]; x0 += tx) items.push_back({p, x0, y0, 1 + ppm});
@@ -319,7 +319,7 @@ rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out) {
   for (int p = 0; p < nprob; ++p) {
     fill_desc(&probs[p], b->desc[p]);
     b->general = b->general || needs_general(b->desc[p].g, b->desc[p].ph);
-    b->ppm = b->ppm || probs[p].reconstruction == RHD_RECON_PPM;
+    b->ppm = b->ppm || probs[p].reconstruction != RHD_RECON_PLM;
     b->desc[p].offset = off;
     b->offsets[p] = off;
     off += b->desc[p].g.ncell;

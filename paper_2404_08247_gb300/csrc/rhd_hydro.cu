@@ -1,7 +1,8 @@
 // rhd_hydro.cu -- the hydrodynamic subsystem of Sec. 3.1 on the GPU: the
 // Euler equations (rho, m, E_gas; ideal gas p = (gamma-1)(E_gas - |m|^2/2rho))
 // advanced by a method of lines with RK2-SSP, the primitives reconstructed
-// with the transport's option (PLM-MC or PPM) and HLLC fluxes.
+// with the transport's option (PLM-MC, PPM or PPM with the Colella-Sekora
+// limiter) and HLLC fluxes.
 //
 // One stage is three kinds of launch over the grid:
 //   prim:   primitives w = (rho, v, p) of every cell, once (the face kernels
@@ -127,15 +128,15 @@ __device__ __forceinline__ bool hllc(double g, double g1i, const double L[5], co
 }
 
 // one thread per face of axis D: faces between cells c-1 and c along D,
-// c in [0, n_D]; nf = hydro_faces(g, D)
-template <int D, bool PPM>
+// c in [0, n_D]; nf = hydro_faces(g, D).  RK: the rhd_recon of the faces
+template <int D, int RK>
 __global__ void __launch_bounds__(kThreads) face_kernel(const Geometry g, double gamma,
                                                          double g1i,
                                                          const double* __restrict__ w,
                                                          double* __restrict__ f, long long nf,
                                                          DevStatus* st, int step, int stage) {
   if (block_skip(st)) return;
-  constexpr int H = PPM ? 3 : 2, NS = 2 * H;
+  constexpr int H = RK != RHD_RECON_PLM ? 3 : 2, NS = 2 * H;
   const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1);
   const int N = g.ncell;
   for (long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x; fi < nf;
@@ -159,7 +160,9 @@ __global__ void __launch_bounds__(kThreads) face_kernel(const Geometry g, double
     double L[5], R[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      if constexpr (PPM) {
+      if constexpr (RK == RHD_RECON_PPM_CS) {
+        ppm_cs_face(u[k], L[k], R[k]);
+      } else if constexpr (RK == RHD_RECON_PPM) {
         ppm_face(u[k], L[k], R[k]);
       } else {
         L[k] = u[k][1] + half_slope(u[k][0], u[k][1], u[k][2]);
@@ -280,7 +283,7 @@ int blocks_for(long long n) {
   return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
 }
 
-template <bool PPM>
+template <int RK>
 cudaError_t launch_faces(const Geometry& g, double gamma, const double* w, const HydroBufs& b,
                          DevStatus* st, int step, int stage, cudaStream_t s) {
   const double g1i = 1.0 / (gamma - 1.0);
@@ -288,11 +291,11 @@ cudaError_t launch_faces(const Geometry& g, double gamma, const double* w, const
     const long long nf = hydro_faces(g, d);
     const int nb = blocks_for(nf);
     if (d == 0)
-      face_kernel<0, PPM><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[0], nf, st, step, stage);
+      face_kernel<0, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[0], nf, st, step, stage);
     else if (d == 1)
-      face_kernel<1, PPM><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[1], nf, st, step, stage);
+      face_kernel<1, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[1], nf, st, step, stage);
     else
-      face_kernel<2, PPM><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[2], nf, st, step, stage);
+      face_kernel<2, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[2], nf, st, step, stage);
   }
   return cudaGetLastError();
 }
@@ -319,8 +322,11 @@ cudaError_t launch_hydro_step(const Geometry& g, double gamma, int recon, double
     F.nf[d] = d < g.ndim ? hydro_faces(g, d) : 0;
   }
   auto faces = [&](int stage) {
-    return recon == RHD_RECON_PPM ? launch_faces<true>(g, gamma, b.w, b, st, step, stage, s)
-                                  : launch_faces<false>(g, gamma, b.w, b, st, step, stage, s);
+    if (recon == RHD_RECON_PPM_CS)
+      return launch_faces<RHD_RECON_PPM_CS>(g, gamma, b.w, b, st, step, stage, s);
+    if (recon == RHD_RECON_PPM)
+      return launch_faces<RHD_RECON_PPM>(g, gamma, b.w, b, st, step, stage, s);
+    return launch_faces<RHD_RECON_PLM>(g, gamma, b.w, b, st, step, stage, s);
   };
   // stage 1: U1 = U + dt L(U)
   prim_kernel<<<nb, kThreads, 0, s>>>(N, gm1, un, b.w, st, step, 3);

@@ -236,6 +236,76 @@ __device__ __forceinline__ void ppm_face(const R u[6], R& L, R& Rr) {
   Rr = ppm_edge_of<true>(u[3], a23, a34);
 }
 
+// The PPM limiter of Colella & Sekora (2008) (reconstruction PPM_CS), which
+// keeps smooth extrema.  Interface value between cells u0 and up from
+// um .. upp: the fourth-order value 7/12 (u0 + up) - 1/12 (um + upp); where it
+// leaves [u0, up] its second difference 3 (u0 - 2a + up) is limited against
+// those of the two cells (the smallest magnitude, C = 1.25 on its own, if all
+// three share a sign, else zero) and a = (u0 + up)/2 - D2_lim/6.
+template <typename R>
+__device__ __forceinline__ bool same_sign3(R a, R b, R c) {
+  return (a > R(0) && b > R(0) && c > R(0)) || (a < R(0) && b < R(0) && c < R(0));
+}
+
+template <typename R>
+__device__ __forceinline__ R cs_interface(R um, R u0, R up, R upp) {
+  R a = R(7.0 / 12.0) * (u0 + up) - R(1.0 / 12.0) * (um + upp);
+  if ((a - u0) * (up - a) < R(0)) {
+    const R d2 = R(3) * (u0 - R(2) * a + up);
+    const R d2l = um - R(2) * u0 + up, d2r = u0 - R(2) * up + upp;
+    R lim = R(0);
+    if (same_sign3(d2, d2l, d2r))
+      lim = copysign(fmin(R(1.25) * fabs(d2), fmin(fabs(d2l), fabs(d2r))), d2);
+    a = R(0.5) * (u0 + up) - lim * R(1.0 / 6.0);
+  }
+  return a;
+}
+
+// Edges (l, r) of a cell of mean u0 with neighbours um, up under the
+// Colella-Sekora constraint; d2L, d2R: second differences of the cells on
+// either side.  At a local extremum (of the edges or of the means) the
+// curvature -12 u0 + 6 (l + r) is limited against C = 1.25 times the second
+// differences of the three cells and both edges scale towards u0 by the
+// ratio; elsewhere an edge more than twice as far from u0 as the other is
+// moved to twice that distance.
+template <typename R>
+__device__ __forceinline__ void cs_edges(R um, R u0, R up, R d2L, R d2R, R& l, R& r) {
+  if ((r - u0) * (u0 - l) <= R(0) || (um - u0) * (u0 - up) <= R(0)) {
+    const R d2 = R(-12) * u0 + R(6) * (l + r), d2c = um - R(2) * u0 + up;
+    R lim = R(0);
+    if (same_sign3(d2, d2c, d2L) && same_sign3(d2, d2c, d2R))
+      lim = copysign(fmin(fabs(d2), R(1.25) * fmin(fabs(d2c), fmin(fabs(d2L), fabs(d2R)))),
+                     d2);
+    if (d2 != R(0)) {
+      const R fac = lim / d2;
+      l = u0 + (l - u0) * fac;
+      r = u0 + (r - u0) * fac;
+    } else {
+      l = u0;
+      r = u0;
+    }
+  } else {
+    const R dl = u0 - l, dr = r - u0;
+    if (fabs(dr) >= R(2) * fabs(dl))
+      r = u0 + R(2) * dl;
+    else if (fabs(dl) >= R(2) * fabs(dr))
+      l = u0 - R(2) * dr;
+  }
+}
+
+// Colella-Sekora states of the face between u[2] and u[3] from u[0..5]
+template <typename R>
+__device__ __forceinline__ void ppm_cs_face(const R u[6], R& L, R& Rr) {
+  const R a12 = cs_interface(u[0], u[1], u[2], u[3]);
+  const R a23 = cs_interface(u[1], u[2], u[3], u[4]);
+  const R a34 = cs_interface(u[2], u[3], u[4], u[5]);
+  R l2 = a12, r2 = a23, l3 = a23, r3 = a34;
+  cs_edges(u[1], u[2], u[3], u[0] - R(2) * u[1] + u[2], u[2] - R(2) * u[3] + u[4], l2, r2);
+  cs_edges(u[2], u[3], u[4], u[1] - R(2) * u[2] + u[3], u[3] - R(2) * u[4] + u[5], l3, r3);
+  L = r2;
+  Rr = l3;
+}
+
 // ---------------------------------------------------------------- closure
 // Levermore M1 closure (the paper leaves the closure free, Sec. 2.1):
 // P = E [(1 - xi)/2 I + (3 xi - 1)/2 n n], xi = (3 + 4 f^2)/(5 + 2 sqrt(4 - 3 f^2)),

@@ -63,7 +63,7 @@ cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* k
 // general ones; PPM faces the PPM unit's (general physics, wider halo).
 template <int STAGE>
 static cudaError_t launch_stage_t(int precision, const StageArgs& A, cudaStream_t s) {
-  if (A.ph.reconstruction == RHD_RECON_PPM) return launch_stage_ppm(STAGE, precision, A, s);
+  if (A.ph.reconstruction != RHD_RECON_PLM) return launch_stage_ppm(STAGE, precision, A, s);
   const bool gen = needs_general(A.g, A.ph);
   if (precision == RHD_PREC_MIXED)
     return gen ? launch_prec<STAGE, float, true, false>(A, s)

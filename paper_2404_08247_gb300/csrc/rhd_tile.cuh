@@ -66,7 +66,7 @@ struct SmemT {
   static constexpr int FY = T::NDIM >= 2 ? 4 * (T::TY + 1) * T::TX : 0;
   // PPM z march: each thread's carried right edge and interface value (kept
   // in shared memory: in registers they push the FP64 kernel past its budget)
-  static constexpr int CZ = (T::PPM && T::NDIM == 3) ? 8 * T::NT : 0;
+  static constexpr int CZ = (T::PPM && T::NDIM == 3) ? 12 * T::NT : 0;
   static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY + CZ);
 };
 
@@ -189,27 +189,32 @@ __device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
 }
 
 // PPM states of the face between cells u[2] and u[3] of the six cells u
+// (cs: the Colella-Sekora limiter)
 template <typename R>
-__device__ __forceinline__ void ppm_states(const R u[6][4], R L[4], R Rr[4]) {
+__device__ __forceinline__ void ppm_states(const R u[6][4], R L[4], R Rr[4], bool cs) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     R v[6];
 #pragma unroll
     for (int o = 0; o < 6; ++o) v[o] = u[o][q];
-    ppm_face(v, L[q], Rr[q]);
+    if (cs)
+      ppm_cs_face(v, L[q], Rr[q]);
+    else
+      ppm_face(v, L[q], Rr[q]);
   }
 }
 
-// flux through the face between plane cells c - st and c (stride st)
+// flux through the face between plane cells c - st and c (stride st); cs:
+// PPM tiles with the Colella-Sekora limiter
 template <class T, typename R>
 __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R eps, R chat,
-                                           int closure, R out[4]) {
+                                           int closure, R out[4], bool cs = false) {
   R L[4], Rr[4];
   if constexpr (T::PPM) {
     R u[6][4];
 #pragma unroll
     for (int o = 0; o < 6; ++o) cell_of<T, R>(pl, c + (o - 3) * st, u[o]);
-    ppm_states(u, L, Rr);
+    ppm_states(u, L, Rr, cs);
   } else {
     R am[4], a[4], b[4], bp[4];
     cell_of<T, R>(pl, c - 2 * st, am);
@@ -296,24 +301,47 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   // adds one cell's edges; the start reads the own column from memory
   R* rz = fys + S::FY + threadIdx.x;       // rz[q * NT]: right edge of cell k
   R* az = rz + 4 * NT;                      // az[q * NT]: interface value a(k+1/2)
+  R* dz = az + 4 * NT;                      // dz[q * NT]: second difference of cell k
+  const bool cs = T::PPM && ph.reconstruction == RHD_RECON_PPM_CS;
   if constexpr (NDIM == 3 && T::PPM) {
     R u[6][4];
 #pragma unroll
     for (int o = 0; o < 6; ++o) column_cell<T, R, GEN>(A, cx, cy, kbeg - 3 + o, u[o]);
     R L[4], Rr[4];
+    if (cs) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const R h1 = half_slope(u[0][q], u[1][q], u[2][q]);
-      const R h2 = half_slope(u[1][q], u[2][q], u[3][q]);
-      const R h3 = half_slope(u[2][q], u[3][q], u[4][q]);
-      const R h4 = half_slope(u[3][q], u[4][q], u[5][q]);
-      const R a12 = ppm_interface(u[1][q], u[2][q], h1, h2);
-      const R a23 = ppm_interface(u[2][q], u[3][q], h2, h3);
-      const R a34 = ppm_interface(u[3][q], u[4][q], h3, h4);
-      L[q] = ppm_edge_of<false>(u[2][q], a12, a23);
-      Rr[q] = ppm_edge_of<true>(u[3][q], a23, a34);
-      rz[q * NT] = ppm_edge_of<false>(u[3][q], a23, a34);
-      az[q * NT] = a34;
+      for (int q = 0; q < 4; ++q) {
+        R w[6];
+#pragma unroll
+        for (int o = 0; o < 6; ++o) w[o] = u[o][q];
+        const R a12 = cs_interface(w[0], w[1], w[2], w[3]);
+        const R a23 = cs_interface(w[1], w[2], w[3], w[4]);
+        const R a34 = cs_interface(w[2], w[3], w[4], w[5]);
+        const R d2a = w[1] - R(2) * w[2] + w[3], d2b = w[2] - R(2) * w[3] + w[4];
+        R l2 = a12, r2 = a23, l3 = a23, r3 = a34;
+        cs_edges(w[1], w[2], w[3], w[0] - R(2) * w[1] + w[2], d2b, l2, r2);
+        cs_edges(w[2], w[3], w[4], d2a, w[3] - R(2) * w[4] + w[5], l3, r3);
+        L[q] = r2;
+        Rr[q] = l3;
+        rz[q * NT] = r3;
+        az[q * NT] = a34;
+        dz[q * NT] = d2b;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R h1 = half_slope(u[0][q], u[1][q], u[2][q]);
+        const R h2 = half_slope(u[1][q], u[2][q], u[3][q]);
+        const R h3 = half_slope(u[2][q], u[3][q], u[4][q]);
+        const R h4 = half_slope(u[3][q], u[4][q], u[5][q]);
+        const R a12 = ppm_interface(u[1][q], u[2][q], h1, h2);
+        const R a23 = ppm_interface(u[2][q], u[3][q], h2, h3);
+        const R a34 = ppm_interface(u[3][q], u[4][q], h3, h4);
+        L[q] = ppm_edge_of<false>(u[2][q], a12, a23);
+        Rr[q] = ppm_edge_of<true>(u[3][q], a23, a34);
+        rz[q * NT] = ppm_edge_of<false>(u[3][q], a23, a34);
+        az[q * NT] = a34;
+      }
     }
     R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
     zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
@@ -363,15 +391,30 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       cell_of<T, R>(ring + ring_slot<T>(k + 2) * 4 * S::PS, own, v2);
       cell_of<T, R>(ring + ring_slot<T>(k + 3) * 4 * S::PS, own, v3);
       R L[4], Rr[4];
+      if (cs) {
+        // the cell k+1 needs the second difference of cell k, carried
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const R ha = half_slope(v0[q], v1[q], v2[q]);
-        const R hb = half_slope(v1[q], v2[q], v3[q]);
-        const R an = ppm_interface(v1[q], v2[q], ha, hb);
-        L[q] = rz[q * NT];
-        Rr[q] = ppm_edge_of<true>(v1[q], az[q * NT], an);
-        rz[q * NT] = ppm_edge_of<false>(v1[q], az[q * NT], an);
-        az[q * NT] = an;
+        for (int q = 0; q < 4; ++q) {
+          const R an = cs_interface(v0[q], v1[q], v2[q], v3[q]);
+          R l1 = az[q * NT], r1 = an;
+          cs_edges(v0[q], v1[q], v2[q], dz[q * NT], v1[q] - R(2) * v2[q] + v3[q], l1, r1);
+          L[q] = rz[q * NT];
+          Rr[q] = l1;
+          rz[q * NT] = r1;
+          az[q * NT] = an;
+          dz[q * NT] = v0[q] - R(2) * v1[q] + v2[q];
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const R ha = half_slope(v0[q], v1[q], v2[q]);
+          const R hb = half_slope(v1[q], v2[q], v3[q]);
+          const R an = ppm_interface(v1[q], v2[q], ha, hb);
+          L[q] = rz[q * NT];
+          Rr[q] = ppm_edge_of<true>(v1[q], az[q * NT], an);
+          rz[q * NT] = ppm_edge_of<false>(v1[q], az[q * NT], an);
+          az[q * NT] = an;
+        }
       }
       R eps = (R)face_eps(A, 2, cx, cy, k);
       zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
@@ -402,7 +445,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       bool real = xl < g.n[0] && (NDIM < 2 || yr < g.n[1]);
       R eps = real ? (R)face_eps(A, 0, xl, yr, k) : R(1);
       R out[4];
-      if (!plane_face<T, R>(pl, c, 1, 0, eps, chat, ph.closure, out) && real) {
+      if (!plane_face<T, R>(pl, c, 1, 0, eps, chat, ph.closure, out, cs) && real) {
         // a face with E <= 0 poisons both neighbours' fluxes
 #pragma unroll
         for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
@@ -419,7 +462,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         bool real = xr < g.n[0] && yl < g.n[1];
         R eps = real ? (R)face_eps(A, 1, xr, yl, k) : R(1);
         R out[4];
-        if (!plane_face<T, R>(pl, c, S::PW, 1, eps, chat, ph.closure, out) && real) {
+        if (!plane_face<T, R>(pl, c, S::PW, 1, eps, chat, ph.closure, out, cs) && real) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
         }

@@ -27,7 +27,7 @@ RHD_SCHEME_IMEX_PDARS, RHD_SCHEME_RK2_SSP = 0, 1
 RHD_CLOSURE_M1, RHD_CLOSURE_EDDINGTON = 0, 1
 RHD_HLL_TAU, RHD_HLL_NONE = 0, 1
 RHD_PREC_FP64, RHD_PREC_MIXED = 0, 1
-RHD_RECON_PLM, RHD_RECON_PPM = 0, 1
+RHD_RECON_PLM, RHD_RECON_PPM, RHD_RECON_PPM_CS = 0, 1, 2
 RHD_NFIELDS = 10
 (RHD_F_RHO, RHD_F_MX, RHD_F_MY, RHD_F_MZ, RHD_F_EGAS, RHD_F_ERAD, RHD_F_FX,
  RHD_F_FY, RHD_F_FZ, RHD_F_KAPPA) = range(10)
@@ -37,7 +37,7 @@ _SCHEME = {"imex": RHD_SCHEME_IMEX_PDARS, "rk2ssp": RHD_SCHEME_RK2_SSP}
 _CLOSURE = {"m1": RHD_CLOSURE_M1, "eddington": RHD_CLOSURE_EDDINGTON}
 _HLL = {"tau": RHD_HLL_TAU, "none": RHD_HLL_NONE}
 _PREC = {"fp64": RHD_PREC_FP64, "mixed": RHD_PREC_MIXED}
-_RECON = {"plm": RHD_RECON_PLM, "ppm": RHD_RECON_PPM}
+_RECON = {"plm": RHD_RECON_PLM, "ppm": RHD_RECON_PPM, "ppm_cs": RHD_RECON_PPM_CS}
 
 
 class RHDError(RuntimeError):

@@ -47,6 +47,9 @@ CASES = [
     (3, (17, 9, 11), "ppm", "reflect"),
     (3, (3, 3, 3), "ppm", "reflect"),
     (2, (2, 16), "plm", "periodic"),
+    (1, (300,), "ppm_cs", "periodic"),
+    (2, (33, 17), "ppm_cs", "reflect"),
+    (3, (17, 9, 11), "ppm_cs", "periodic"),
 ]
 
 
