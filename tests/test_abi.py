@@ -149,7 +149,11 @@ def test_reconstruction_option_is_validated(rhd):
     assert st == rhd.RHD_ERR_ARG and "n >= 3" in msg
     assert rhd.rhd_params_validate(params(3, rhd.RHD_BC_REFLECT, rhd.RHD_RECON_PPM))[0] == rhd.RHD_OK
     assert rhd.rhd_params_validate(params(1, rhd.RHD_BC_PERIODIC, rhd.RHD_RECON_PPM))[0] == rhd.RHD_OK
-    assert rhd.rhd_params_validate(params(8, rhd.RHD_BC_PERIODIC, 2))[0] == rhd.RHD_ERR_ARG
+    assert rhd.rhd_params_validate(params(8, rhd.RHD_BC_PERIODIC, 3))[0] == rhd.RHD_ERR_ARG
+    st, msg = rhd.rhd_params_validate(params(2, rhd.RHD_BC_REFLECT, rhd.RHD_RECON_PPM_CS))
+    assert st == rhd.RHD_ERR_ARG and "n >= 3" in msg
+    p = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16], reconstruction="ppm_cs"))
+    assert p.reconstruction == rhd.RHD_RECON_PPM_CS
     p = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16], reconstruction="ppm"))
     assert p.reconstruction == rhd.RHD_RECON_PPM
 
