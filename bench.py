@@ -66,7 +66,7 @@ def parse(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--hll", default="tau", choices=["tau", "none"])
-    ap.add_argument("--reconstruction", default="plm", choices=["plm", "ppm"],
+    ap.add_argument("--reconstruction", default="plm", choices=["plm", "ppm", "ppm_cs"],
                     help="face states of the headline form (Sec. 3.3)")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -557,7 +557,10 @@ def run_ours(args):
                                 and not args.single_form]
     if not args.single_form:
         forms.append("fp64-rk2ssp")  # the paper's comparison scheme (Sec. 4.2)
-        forms += ["fp64-ppm", "mixed-ppm"]  # the paper's PPM faces (Sec. 3.3)
+        # the paper's PPM faces (Sec. 3.3); the Colella-Sekora variant turns a
+        # face state of this box's iid temperatures nonphysical in its first
+        # step (it does not keep edges within the neighbours' range)
+        forms += ["fp64-ppm", "mixed-ppm"]
     results = {}
     ctx = None
     for form in forms:
@@ -566,6 +569,8 @@ def run_ours(args):
             fprob, fprec = dict(prob, scheme="rk2ssp"), "fp64"
         elif form.endswith("-ppm"):
             fprob, fprec = dict(prob, reconstruction="ppm"), form[:-4]
+        elif form.endswith("-ppm_cs"):
+            fprob, fprec = dict(prob, reconstruction="ppm_cs"), form[:-7]
         c, r = time_form(args, rhd, torch, fprob, Ud, fprec, barrier, stream, local)
         r["ms"] = max_over_ranks(r["ms"])
         results[form] = r
