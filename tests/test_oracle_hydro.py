@@ -255,6 +255,38 @@ def test_split_runs_hydro_then_subcycled_radiation(oracle_mod):
     assert np.array_equal(A, B)
 
 
+@pytest.mark.parametrize("kappa", [0.5, 20.0])
+def test_split_error_is_first_order_in_the_hydro_step(oracle_mod, kappa):
+    """Sec. 3.1 splits the hydrodynamic step from the radiation update once per
+    step (first order): on a fixed grid, with every radiation substep the same
+    dt_rad (t_end = 512 dt_rad, dt_h = t_end/m), the state at t_end moves
+    toward the m = 512 result in proportion to dt_h (error ratio 2 per halving;
+    a symmetric split would give 4, a split that loses or misplaces a substep
+    would not converge).  A smooth coupled gas, optically thin and thick."""
+    n = 48
+    prob = I.base_problem(1, [n], [1.0 / n], gamma=5 / 3, c=300.0, chat=100.0, bc="periodic")
+    x = (np.arange(n) + 0.5) / n
+    sh = (1, 1, n)
+    rho = (1 + 0.2 * np.sin(2 * np.pi * x)).reshape(sh)
+    p = (1 + 0.2 * np.cos(2 * np.pi * x)).reshape(sh)
+    v = np.zeros((3,) + sh)
+    v[0] = 0.3 * np.sin(2 * np.pi * x + 1).reshape(sh)
+    U0 = I.gas_state(prob, rho, v, p, kappa=kappa)
+    t_end = 512 * oracle_mod.dt(prob)
+    assert t_end / 16 < oracle_mod.hydro_dt(prob, U0)
+    out = {}
+    for m in (16, 32, 64, 512):
+        U = U0.copy()
+        subs = oracle_mod.split_step(prob, U, m, t_end / m)
+        assert subs == [512 // m] * m
+        out[m] = U
+    fields = (I.F_RHO, I.F_MX, I.F_EGAS, I.F_ERAD, I.F_FX)
+    err = [max(np.max(np.abs(out[m][f] - out[512][f])) / np.max(np.abs(out[512][f]))
+               for f in fields) for m in (16, 32, 64)]
+    for a, b in zip(err, err[1:]):
+        assert 1.8 < a / b < 2.5, err
+
+
 def test_split_conserves_total_energy_and_momentum(oracle_mod):
     """Hydrodynamics conserves E_gas and m, the radiation step E_gas +
     (c/chat) E and m + F/(c chat): the split conserves the latter (1e-13)."""
