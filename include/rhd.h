@@ -58,8 +58,13 @@ typedef enum {
 /* Boundaries of the radiation transport.  PERIODIC: wrap; REFLECT: mirror
  * the cells, negating the normal flux; INFLOW: ghost cells hold the fixed
  * radiation state bc_state of that face (e.g. an isotropic source of
- * temperature T_s: E = a_rad T_s^4, F = 0). */
-typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_REFLECT = 1, RHD_BC_INFLOW = 2 } rhd_bc;
+ * temperature T_s: E = a_rad T_s^4, F = 0).  HALO: the face is shared with
+ * the neighbouring z-slab of a decomposed grid (3-D, z faces only, n[2] >= 3);
+ * its ghost planes are the neighbour's boundary planes, copied in by
+ * rhd_step_slabs before each stage. */
+typedef enum {
+  RHD_BC_PERIODIC = 0, RHD_BC_REFLECT = 1, RHD_BC_INFLOW = 2, RHD_BC_HALO = 3
+} rhd_bc;
 /* Time integration.  IMEX_PDARS: the paper's scheme (eq. imex1/imex2), the
  * local exchange solved in both stages.  RK2_SSP: the comparison scheme of
  * Sec. 4.2, transport alone in the first stage and the exchange solved once,
@@ -106,7 +111,8 @@ typedef struct {
   int64_t n[3];        /* cells per axis; axes >= ndim must be 1 */
   double dx[3];        /* cell widths (> 0 on the active axes) */
   int bc[3][2];        /* rhd_bc of the low/high face of each axis; a
-                          reflecting axis needs n >= 2 */
+                          reflecting axis needs n >= 2, a HALO face
+                          (z only) n[2] >= 3 */
   double gamma;        /* adiabatic index (> 1) */
   double c;            /* speed of light (> 0) */
   double chat;         /* reduced speed of light, 0 < chat <= c (Sec. 3.2) */
@@ -319,6 +325,34 @@ rhd_status rhd_hydro_step(rhd_ctx* ctx, int nsteps, double dt, rhd_step_info* in
  * iteration statistics sum over the radiation steps; fail_stage 1-2 is a
  * radiation stage, 3-4 a hydrodynamic one. */
 rhd_status rhd_step_split(rhd_ctx* ctx, int nsteps, double dt_h, rhd_step_info* info);
+
+/* ---- Domain decomposition: z-slabs of one grid on one device ----
+ * The radiation step needs no communication beyond ghost layers (Sec. 3.2:
+ * the explicit stages read face neighbours, the implicit solve is local):
+ * before each stage every slab receives the (E, F) planes of its neighbours
+ * that its face states read (2 with PLM, 3 with PPM), and nothing else.
+ * slabs[0..nslab-1] are contexts of consecutive z ranges of one 3-D grid,
+ * bottom to top (slab s + 1 sits on slab s).  The contexts must be created
+ * with identical params except n[2] (>= 3) and the z faces: every face
+ * between two slabs is RHD_BC_HALO on both sides; the bottom face of slab 0
+ * and the top face of the last slab are either both HALO (a periodic grid:
+ * they face each other) or neither (their own reflecting or inflow faces).
+ * All slabs share one stream and one device, and every field of every slab
+ * must be set.  Advances nsteps steps of dt (dt <= 0: rhd_default_dt) with
+ * the same arithmetic per cell as the undecomposed grid: the results are
+ * bit-identical to it.  Each exchange is one cudaMemcpyAsync per field and
+ * face, device to device (the calls a multi-GPU run would replace by
+ * point-to-point sends); TAU-mode face factors at the slab faces are
+ * computed from the neighbour's rho and kappa on the first call and after a
+ * field change.  Failure: all slabs stay at the last step that every slab
+ * completed; info (nullable) reports as rhd_step with fail_cell counted in
+ * the whole grid (cell index of slab s plus the cells of the slabs below).
+ * The first call allocates 27 * n[0] * n[1] doubles per slab.  A context
+ * with a HALO face is refused (RHD_ERR_STATE) by every other stepping call
+ * (rhd_step, rhd_step_async, rhd_transport, rhd_step_record, rhd_adjoint,
+ * rhd_hydro_step, rhd_step_split).  Synchronises. */
+rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                          rhd_step_info* info);
 
 /* Number of kernels this context has launched since rhd_init. */
 int64_t rhd_launch_count(const rhd_ctx* ctx);

@@ -72,7 +72,19 @@ struct rhd_ctx {
   double* hyd_u1 = nullptr;
   double* hyd_f[3] = {nullptr, nullptr, nullptr};
   unsigned long long* hyd_bits = nullptr;
+  // HALO faces: the neighbours' ghost planes (2 sides x 4 fields x
+  // HALO_PLANES planes), plane 0 of the slab above (kappa, rho) and the TAU
+  // factors of the low face; allocated by the first rhd_step_slabs
+  double* halo = nullptr;
 };
+
+// a context whose grid is a z-slab of a decomposed grid
+static bool has_halo(const rhd_ctx* c) {
+  return c->p.bc[2][0] == RHD_BC_HALO || c->p.bc[2][1] == RHD_BC_HALO;
+}
+static const int kHaloSlots = 2 * 4 * HALO_PLANES + 3;  // planes of n0 n1 doubles
+static const char* const kHaloOnly =
+    "a context with a HALO face steps through rhd_step_slabs only";
 
 static rhd_status fail(rhd_ctx* c, rhd_status s, const char* fmt, ...) {
   va_list ap;
@@ -178,8 +190,13 @@ rhd_status rhd_params_validate(const rhd_params* p, char* msg, int msglen) {
         return bad(msg, msglen, "dx[%d] must be positive and finite", d), RHD_ERR_ARG;
       for (int s = 0; s < 2; ++s) {
         if (p->bc[d][s] != RHD_BC_PERIODIC && p->bc[d][s] != RHD_BC_REFLECT &&
-            p->bc[d][s] != RHD_BC_INFLOW)
+            p->bc[d][s] != RHD_BC_INFLOW && p->bc[d][s] != RHD_BC_HALO)
           return bad(msg, msglen, "bc[%d][%d] is not an rhd_bc", d, s), RHD_ERR_ARG;
+        if (p->bc[d][s] == RHD_BC_HALO && (p->ndim != 3 || d != 2))
+          return bad(msg, msglen, "HALO faces are z faces of a 3-D grid (bc[%d][%d])", d, s),
+                 RHD_ERR_ARG;
+        if (p->bc[d][s] == RHD_BC_HALO && p->n[d] < HALO_PLANES)
+          return bad(msg, msglen, "a HALO face needs n[2] >= %d", HALO_PLANES), RHD_ERR_ARG;
         if (p->bc[d][s] != RHD_BC_PERIODIC && p->n[d] < 2)
           return bad(msg, msglen, "a reflecting or inflow axis %d needs n >= 2", d),
                  RHD_ERR_ARG;
@@ -327,6 +344,7 @@ static void release(rhd_ctx* c) {
   cudaFree(c->hyd_u1);
   for (int d = 0; d < 3; ++d) cudaFree(c->hyd_f[d]);
   cudaFree(c->hyd_bits);
+  cudaFree(c->halo);
   cudaFreeHost(c->h_status);
   cudaFreeHost(c->h_tot);
   cudaFreeHost(c->h_flag);
@@ -546,6 +564,7 @@ rhd_status rhd_step_async(rhd_ctx* c, int nsteps, double dt) {
   if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is already pending");
   if (c->fields_set != kAllFields)
     return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (has_halo(c)) return fail(c, RHD_ERR_STATE, "%s", kHaloOnly);
   if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
   if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
   if (!std::isfinite(dt)) return fail(c, RHD_ERR_ARG, "dt is not finite");
@@ -647,6 +666,7 @@ rhd_status rhd_transport(rhd_ctx* c, double* rates, int64_t count, int dst_on_de
   if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
   if (c->fields_set != kAllFields)
     return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (has_halo(c)) return fail(c, RHD_ERR_STATE, "%s", kHaloOnly);
   if (!rates) return fail(c, RHD_ERR_ARG, "rates is NULL");
   if (count != 4 * (int64_t)c->ncell) return fail(c, RHD_ERR_ARG, "count must be 4 * ncell");
   CUDA_TRY(c, cudaSetDevice(c->device));
@@ -772,6 +792,7 @@ rhd_status rhd_step_record(rhd_ctx* c, int nsteps, double dt, double* tape, int6
   if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
   if (c->fields_set != kAllFields)
     return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (has_halo(c)) return fail(c, RHD_ERR_STATE, "%s", kHaloOnly);
   if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
   if (!tape) return fail(c, RHD_ERR_ARG, "tape is NULL");
   const size_t N = (size_t)c->ncell;
@@ -841,6 +862,7 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
   if ((c->fields_set & ((1u << RHD_F_RHO) | (1u << RHD_F_KAPPA))) !=
       ((1u << RHD_F_RHO) | (1u << RHD_F_KAPPA)))
     return fail(c, RHD_ERR_STATE, "rho and kappa must be set");
+  if (has_halo(c)) return fail(c, RHD_ERR_STATE, "%s", kHaloOnly);
   if (nsteps < 0) return fail(c, RHD_ERR_ARG, "nsteps < 0");
   if (!tape || !ybar || !kappa_bar) return fail(c, RHD_ERR_ARG, "a buffer is NULL");
   if (c->p.scheme != RHD_SCHEME_IMEX_PDARS || c->p.kappa_T_exp != 0.0 ||
@@ -904,6 +926,7 @@ static rhd_status hydro_ready(rhd_ctx* c) {
   if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
   if (c->fields_set != kAllFields)
     return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (has_halo(c)) return fail(c, RHD_ERR_STATE, "%s", kHaloOnly);
   for (int d = 0; d < c->p.ndim; ++d)
     if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
       return fail(c, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
@@ -1069,6 +1092,228 @@ rhd_status rhd_step_split(rhd_ctx* c, int nsteps, double dt_h, rhd_step_info* in
   if (c) total.t = c->t;
   if (info) *info = total;
   return s;
+}
+
+// ---- z-slabs of one grid on one device
+
+}  // extern "C"
+
+// params of two slabs of one grid: equal but for n[2] and the z faces
+static bool same_grid_but_z(const rhd_params& a, const rhd_params& b) {
+  if (a.ndim != b.ndim || a.n[0] != b.n[0] || a.n[1] != b.n[1]) return false;
+  for (int d = 0; d < 3; ++d) {
+    if (a.dx[d] != b.dx[d]) return false;
+    for (int s = 0; s < 2; ++s) {
+      if (d < 2 && a.bc[d][s] != b.bc[d][s]) return false;
+      for (int q = 0; q < 4; ++q)
+        if (a.bc_state[d][s][q] != b.bc_state[d][s][q]) return false;
+    }
+  }
+  return a.gamma == b.gamma && a.c == b.c && a.chat == b.chat && a.a_rad == b.a_rad &&
+         a.kB_over_mu == b.kB_over_mu && a.cfl == b.cfl && a.closure == b.closure &&
+         a.vc_order == b.vc_order && a.hll_mode == b.hll_mode && a.precision == b.precision &&
+         a.newton_rtol == b.newton_rtol && a.outer_rtol == b.outer_rtol &&
+         a.newton_max_iter == b.newton_max_iter && a.outer_max_iter == b.outer_max_iter &&
+         a.scheme == b.scheme && a.kappa_T_exp == b.kappa_T_exp &&
+         a.kappa_T_ref == b.kappa_T_ref && a.kappa_P_ratio == b.kappa_P_ratio &&
+         a.kappa_F_ratio == b.kappa_F_ratio && a.reconstruction == b.reconstruction;
+}
+
+// Copy the ghost planes of slab s from its neighbours' state buffers src[]
+// (slot-major, NY * ncell doubles each): depth planes of E, Fx, Fy, Fz per
+// HALO face, one device-to-device copy per field and face.
+static cudaError_t exchange(rhd_ctx* const* slabs, int nslab, int s, double* const* src,
+                            int depth, cudaStream_t st) {
+  rhd_ctx* c = slabs[s];
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  static const int slot[4] = {Y_ERAD, Y_FX, Y_FY, Y_FZ};
+  for (int side = 0; side < 2; ++side) {
+    if (c->p.bc[2][side] != RHD_BC_HALO) continue;
+    const int nb = side == 0 ? (s + nslab - 1) % nslab : (s + 1) % nslab;
+    const rhd_ctx* u = slabs[nb];
+    // the low face takes the top depth planes of the slab below (ghost
+    // planes -depth..-1), the high face the bottom ones of the slab above
+    const size_t z0 = side == 0 ? (size_t)u->g.n[2] - depth : 0;
+    const size_t i0 = side == 0 ? HALO_PLANES - depth : 0;
+    double* h = c->halo + (size_t)side * 4 * HALO_PLANES * P;
+    for (int q = 0; q < 4; ++q) {
+      cudaError_t e = cudaMemcpyAsync(
+          h + ((size_t)q * HALO_PLANES + i0) * P,
+          src[nb] + (size_t)slot[q] * u->ncell + z0 * P, sizeof(double) * depth * P,
+          cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+extern "C" {
+
+rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                          rhd_step_info* info) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->fail_cell = -1;
+    info->fail_step = -1;
+  }
+  if (!slabs || nslab < 1) return fail(nullptr, RHD_ERR_ARG, "slabs is NULL or nslab < 1");
+  for (int s = 0; s < nslab; ++s) {
+    if (!slabs[s]) return fail(nullptr, RHD_ERR_ARG, "slabs[%d] is NULL", s);
+    for (int r = 0; r < s; ++r)
+      if (slabs[r] == slabs[s])
+        return fail(slabs[s], RHD_ERR_ARG, "slabs[%d] and slabs[%d] are one context", r, s);
+  }
+  rhd_ctx* c0 = slabs[0];
+  const int last = nslab - 1;
+  for (int s = 0; s < nslab; ++s) {
+    rhd_ctx* c = slabs[s];
+    if (c->p.ndim != 3) return fail(c0, RHD_ERR_ARG, "slab %d: slabs are 3-D grids", s);
+    if (!same_grid_but_z(c->p, c0->p))
+      return fail(c0, RHD_ERR_ARG, "slab %d: params differ from slab 0 beyond n[2] and "
+                  "the z faces", s);
+    if (c->device != c0->device || c->stream != c0->stream)
+      return fail(c0, RHD_ERR_ARG, "slab %d: slabs share one device and one stream", s);
+    if (c->pending) return fail(c0, RHD_ERR_STATE, "slab %d: a step batch is pending", s);
+    if (c->fields_set != kAllFields)
+      return fail(c0, RHD_ERR_STATE, "slab %d: not every field has been set", s);
+    if (s < last && (c->p.bc[2][1] != RHD_BC_HALO || slabs[s + 1]->p.bc[2][0] != RHD_BC_HALO))
+      return fail(c0, RHD_ERR_ARG, "the face between slabs %d and %d must be HALO on both "
+                  "sides", s, s + 1);
+  }
+  const bool wrap = c0->p.bc[2][0] == RHD_BC_HALO;
+  if (wrap != (slabs[last]->p.bc[2][1] == RHD_BC_HALO))
+    return fail(c0, RHD_ERR_ARG, "the bottom face of slab 0 and the top face of slab %d "
+                "are both HALO (a periodic grid) or neither", last);
+  if (!wrap && (c0->p.bc[2][0] == RHD_BC_PERIODIC) && nslab > 1)
+    return fail(c0, RHD_ERR_ARG, "a periodic z axis of several slabs uses HALO end faces");
+  if (nsteps < 0) return fail(c0, RHD_ERR_ARG, "nsteps < 0");
+  if (!(dt > 0.0)) dt = rhd_default_dt(&c0->p);
+  if (!std::isfinite(dt)) return fail(c0, RHD_ERR_ARG, "dt is not finite");
+  CUDA_TRY(c0, cudaSetDevice(c0->device));
+  const cudaStream_t st = c0->stream;
+  const size_t P = (size_t)c0->g.n[0] * c0->g.n[1];
+  for (int s = 0; s < nslab; ++s)
+    if (!slabs[s]->halo) {
+      cudaError_t e = cudaMalloc(&slabs[s]->halo, sizeof(double) * kHaloSlots * P);
+      if (e != cudaSuccess)
+        return fail(c0, RHD_ERR_CUDA, "slab %d: halo buffers: %s", s, cudaGetErrorString(e));
+    }
+  auto hk = [&](rhd_ctx* c) { return c->halo + (size_t)8 * HALO_PLANES * P; };
+  auto hr = [&](rhd_ctx* c) { return hk(c) + P; };
+  auto ezlo = [&](rhd_ctx* c) { return hk(c) + 2 * P; };
+
+  // TAU factors: a slab's top face needs plane 0 of the slab above, its
+  // bottom face is the top face of the slab below (recomputed every call:
+  // a neighbour's rho or kappa may have changed)
+  if (c0->p.hll_mode == RHD_HLL_TAU) {
+    for (int s = 0; s < nslab; ++s) {
+      rhd_ctx* c = slabs[s];
+      const bool top = c->p.bc[2][1] == RHD_BC_HALO;
+      if (top) {
+        const rhd_ctx* u = slabs[(s + 1) % nslab];
+        CUDA_TRY(c0, cudaMemcpyAsync(hk(c), u->kappa, sizeof(double) * P,
+                                     cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(c0, cudaMemcpyAsync(hr(c), u->rho, sizeof(double) * P,
+                                     cudaMemcpyDeviceToDevice, st));
+      }
+      CUDA_TRY(c0, launch_tau_eps(c->g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps, st,
+                                  top ? hk(c) : nullptr, top ? hr(c) : nullptr));
+      c->launches += 1;
+      c->eps_dirty = false;
+    }
+    for (int s = 0; s < nslab; ++s) {
+      rhd_ctx* c = slabs[s];
+      if (c->p.bc[2][0] != RHD_BC_HALO) continue;
+      const rhd_ctx* l = slabs[(s + nslab - 1) % nslab];
+      CUDA_TRY(c0, cudaMemcpyAsync(ezlo(c), l->eps[2] + (size_t)(l->g.n[2] - 1) * P,
+                                   sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+
+  CUDA_TRY(c0, launch_status_reset(c0->d_status, st));
+  c0->launches += 1;
+  const int depth = c0->p.reconstruction == RHD_RECON_PLM ? 2 : 3;
+  std::vector<StageArgs> A(nslab);
+  std::vector<int> cur(nslab), cur0(nslab);
+  long long base = 0;
+  for (int s = 0; s < nslab; ++s) {
+    rhd_ctx* c = slabs[s];
+    StageArgs& a = A[s];
+    a.cell_base = base;
+    base += c->ncell;
+    for (int d = 0; d < 3; ++d) a.eps[d] = c->eps[d];
+    a.g = c->g;
+    a.ph = c->ph;
+    a.dt = dt;
+    a.rho = c->rho;
+    a.kappa = c->kappa;
+    a.st = c0->d_status;  // one status block: a failure anywhere stops every slab
+    a.halo[0] = c->halo;
+    a.halo[1] = c->halo + (size_t)4 * HALO_PLANES * P;
+    a.eps_zlo = ezlo(c);
+    cur[s] = cur0[s] = c->cur;
+  }
+  std::vector<double*> src(nslab);
+  for (int k = 0; k < nsteps; ++k) {
+    for (int s = 0; s < nslab; ++s) src[s] = slabs[s]->ybuf[cur[s]];
+    for (int s = 0; s < nslab; ++s)
+      CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), depth, st));
+    for (int s = 0; s < nslab; ++s) {
+      rhd_ctx* c = slabs[s];
+      StageArgs& a = A[s];
+      a.step = k;
+      slots_of<const double*>(a.yt, c->ybuf[cur[s]], c->ncell);
+      slots_of<const double*>(a.yn, c->ybuf[cur[s]], c->ncell);
+      slots_of<double*>(a.yo, c->yhalf, c->ncell);
+      CUDA_TRY(c0, launch_stage(1, c->p.precision, a, st));
+    }
+    for (int s = 0; s < nslab; ++s) src[s] = slabs[s]->yhalf;
+    for (int s = 0; s < nslab; ++s)
+      CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), depth, st));
+    for (int s = 0; s < nslab; ++s) {
+      rhd_ctx* c = slabs[s];
+      StageArgs& a = A[s];
+      slots_of<const double*>(a.yt, c->yhalf, c->ncell);
+      slots_of<double*>(a.yo, c->ybuf[cur[s] ^ 1], c->ncell);
+      CUDA_TRY(c0, launch_stage(2, c->p.precision, a, st));
+      c->launches += 2;
+      cur[s] ^= 1;
+    }
+  }
+  CUDA_TRY(c0, cudaMemcpyAsync(c0->h_status, c0->d_status, sizeof(DevStatus),
+                               cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c0, cudaStreamSynchronize(st));
+  const DevStatus& ds = *c0->h_status;
+  rhd_status code = RHD_OK;
+  int done = nsteps;
+  int64_t cell = -1;
+  if (ds.fail_key != ~0ull) {
+    code = (rhd_status)(ds.fail_key & 0xffull);
+    cell = (int64_t)(ds.fail_key >> 8);
+    done = ds.fail_step;
+  }
+  for (int s = 0; s < nslab; ++s) {
+    slabs[s]->cur = cur0[s] ^ (done & 1);
+    slabs[s]->t += done * dt;
+  }
+  if (info) {
+    info->status = code;
+    info->steps_done = done;
+    info->fail_cell = cell;
+    info->fail_step = code == RHD_OK ? -1 : ds.fail_step;
+    info->fail_stage = code == RHD_OK ? 0 : ds.fail_stage;
+    info->max_newton = ds.max_newton;
+    info->max_outer = ds.max_outer;
+    info->sum_newton = (int64_t)ds.sum_newton;
+    info->n_solves = (int64_t)ds.n_solves;
+    info->sum_outer = (int64_t)ds.sum_outer;
+    info->t = c0->t;
+    info->dt = dt;
+  }
+  if (code != RHD_OK)
+    return fail(c0, code, "step %d stage %d failed at cell %lld of the slabs (status %d)",
+                ds.fail_step, ds.fail_stage, (long long)cell, (int)code);
+  return RHD_OK;
 }
 
 int64_t rhd_launch_count(const rhd_ctx* c) { return c ? c->launches : 0; }

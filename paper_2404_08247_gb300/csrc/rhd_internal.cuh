@@ -76,7 +76,16 @@ struct StageArgs {
   double* rate[4];       // transport-only launch: dE/dt, dFx/dt, dFy/dt, dFz/dt
   long long cell_base;   // added to cell indices in failure reports (batched pools)
   DevStatus* st;
+  // RHD_BC_HALO z faces: the ghost planes the neighbouring slabs supplied,
+  // per side [4 fields E, Fx, Fy, Fz][HALO_PLANES planes][n0 n1], planes in
+  // z order (low side: z = -3..-1; high side: z = n2..n2+2); and the TAU
+  // factors of the low slab face (n0 n1)
+  const double* halo[2] = {nullptr, nullptr};
+  const double* eps_zlo = nullptr;
 };
+
+// ghost planes a HALO face holds (the widest face stencil: PPM's 3)
+constexpr int HALO_PLANES = 3;
 
 // slot pointers of a slot-major buffer of NY * n doubles
 template <typename P>
@@ -822,8 +831,11 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
 cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
                           double* partials, int npart, double* out4, cudaStream_t s);
 int totals_partials_needed();
+// halo_kappa, halo_rho: plane 0 of the slab above a HALO top face (else null)
 cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
-                           double tau_scale, double* const eps[3], cudaStream_t s);
+                           double tau_scale, double* const eps[3], cudaStream_t s,
+                           const double* halo_kappa = nullptr,
+                           const double* halo_rho = nullptr);
 cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
                                cudaStream_t s);
 // message returned by rhd_last_error(NULL) on this thread

@@ -83,6 +83,8 @@ extern "C" rhd_status rhd_step_noalloc(const rhd_params* p, const double* state_
   char msg[200];
   if (rhd_params_validate(p, msg, sizeof(msg)) != RHD_OK)
     return noalloc_fail(RHD_ERR_ARG, msg);
+  if (p->bc[2][0] == RHD_BC_HALO || p->bc[2][1] == RHD_BC_HALO)
+    return noalloc_fail(RHD_ERR_ARG, "a grid with a HALO face steps through rhd_step_slabs");
   const int64_t ncell64 = p->n[0] * p->n[1] * p->n[2];
   if (ncell64 > kMaxCells) {
     snprintf(msg, sizeof(msg),

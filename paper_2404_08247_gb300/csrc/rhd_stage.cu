@@ -32,7 +32,8 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
 // is chi_0F / chi_0E (the face depth is that of the flux-mean opacity).
 __global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
                                const double* __restrict__ kappa, double tau_scale, double* e0,
-                               double* e1, double* e2) {
+                               double* e1, double* e2, const double* __restrict__ hk,
+                               const double* __restrict__ hr) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell) return;
   int c[3];
@@ -46,15 +47,26 @@ __global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
     bool flip;
     int xb = fold(c[d] + 1, g.n[d], g.bc[d][0], g.bc[d][1], flip);
     int nb = idx + (xb - c[d]) * g.stride[d];
-    double tau = 0.5 * (chi_a + kappa[nb] * rho[nb]) * g.dx[d];
+    const double* kb = kappa;
+    const double* rb = rho;
+    if (d == 2 && c[2] == g.n[2] - 1 && g.bc[2][1] == RHD_BC_HALO) {
+      // the top face of a slab: its neighbour is plane 0 of the slab above
+      kb = hk;
+      rb = hr;
+      nb = c[0] + g.n[0] * c[1];
+    }
+    double tau = 0.5 * (chi_a + kb[nb] * rb[nb]) * g.dx[d];
     out[d][idx] = tau_factor(tau * tau_scale);
   }
 }
 
 cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
-                           double tau_scale, double* const eps[3], cudaStream_t s) {
+                           double tau_scale, double* const eps[3], cudaStream_t s,
+                           const double* halo_kappa, const double* halo_rho) {
+  if (g.bc[2][1] == RHD_BC_HALO && (!halo_kappa || !halo_rho)) return cudaErrorInvalidValue;
   int blocks = (g.ncell + 255) / 256;
-  tau_eps_kernel<<<blocks, 256, 0, s>>>(g, rho, kappa, tau_scale, eps[0], eps[1], eps[2]);
+  tau_eps_kernel<<<blocks, 256, 0, s>>>(g, rho, kappa, tau_scale, eps[0], eps[1], eps[2],
+                                        halo_kappa, halo_rho);
   return cudaGetLastError();
 }
 

@@ -103,6 +103,21 @@ __device__ __forceinline__ int inflow_side(const Geometry& g, int d, int x) {
   return -1;
 }
 
+// Side (0 low, 1 high) of a ghost plane z that a neighbouring slab supplies
+// (an RHD_BC_HALO z face), or -1.
+__device__ __forceinline__ int halo_side(const Geometry& g, int z) {
+  if (z < 0) return g.bc[2][0] == RHD_BC_HALO ? 0 : -1;
+  if (z >= g.n[2]) return g.bc[2][1] == RHD_BC_HALO ? 1 : -1;
+  return -1;
+}
+
+// Field E of ghost plane z in its halo buffer (F_x, F_y, F_z follow at
+// strides of HALO_PLANES planes).
+__device__ __forceinline__ const double* halo_plane(const StageArgs& A, int side, int z) {
+  const int i = side == 0 ? z + HALO_PLANES : z - A.g.n[2];
+  return A.halo[side] + (size_t)i * A.g.n[0] * A.g.n[1];
+}
+
 // optical depth of the face from the flux-mean opacity chi_0F
 __device__ __forceinline__ double eps_direct(const StageArgs& A, int ia, int ib, int d) {
   double tau = 0.5 * (A.kappa[ia] * A.rho[ia] + A.kappa[ib] * A.rho[ib]) * A.g.dx[d];
@@ -116,6 +131,8 @@ __device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, in
   const Geometry& g = A.g;
   int c[3] = {cx, cy, cz};
   if (c[d] < 0) {
+    // the low face of a slab: the factor its neighbour below computed
+    if (g.bc[d][0] == RHD_BC_HALO) return __ldg(A.eps_zlo + c[0] + g.n[0] * c[1]);
     if (g.bc[d][0] != RHD_BC_PERIODIC) {
       c[d] = 0;  // reflecting wall: the ghost mirrors cell 0
       int i0 = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
@@ -142,6 +159,11 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
   bool fz = false;
   int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz, T::HX - 1) : 0;
   const int zin = GEN && NDIM == 3 ? inflow_side(g, 2, zg) : -1;
+  // a ghost plane of a HALO face: the neighbour's plane, not mirrored
+  const int hs = NDIM == 3 ? halo_side(g, zg) : -1;
+  const double* hp = hs >= 0 ? halo_plane(A, hs, zg) : nullptr;
+  const size_t hq = (size_t)HALO_PLANES * g.n[0] * g.n[1];
+  if (hs >= 0) fz = false;
   R* pl = ring + slot * 4 * S::PS;
   for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
     int ii = c % S::PW, jj = c / S::PW;
@@ -149,11 +171,20 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
     int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx, T::HX - 1);
     int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy, T::HX - 1)
                        : 0;
-    int idx = xf + g.n[0] * (yf + g.n[1] * zf);
-    R E = (R)__ldg(A.yt[Y_ERAD] + idx);
-    R Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
-    R Fy = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
-    R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+    R E, Fx, Fy, Fz;
+    if (hs >= 0) {
+      const int pidx = xf + g.n[0] * yf;
+      E = (R)__ldg(hp + pidx);
+      Fx = (R)__ldg(hp + hq + pidx) * inv_c;
+      Fy = (R)__ldg(hp + 2 * hq + pidx) * inv_c;
+      Fz = (R)__ldg(hp + 3 * hq + pidx) * inv_c;
+    } else {
+      int idx = xf + g.n[0] * (yf + g.n[1] * zf);
+      E = (R)__ldg(A.yt[Y_ERAD] + idx);
+      Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
+      Fy = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
+      Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+    }
     Fx = fx ? -Fx : Fx;
     Fy = fy ? -Fy : Fy;
     Fz = fz ? -Fz : Fz;
@@ -240,12 +271,22 @@ __device__ __forceinline__ void column_cell(const StageArgs& A, int cx, int cy, 
   const R inv_c = (R)A.ph.inv_c;
   bool fz = false;
   const int zf = fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz, T::HX - 1);
-  const int idx = cx + g.n[0] * (cy + g.n[1] * zf);
-  u[0] = (R)__ldg(A.yt[Y_ERAD] + idx);
-  u[1] = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
-  u[2] = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
-  const R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
-  u[3] = fz ? -Fz : Fz;
+  const int hs = halo_side(g, zg);
+  if (hs >= 0) {
+    const double* hp = halo_plane(A, hs, zg) + cx + g.n[0] * cy;
+    const size_t hq = (size_t)HALO_PLANES * g.n[0] * g.n[1];
+    u[0] = (R)__ldg(hp);
+    u[1] = (R)__ldg(hp + hq) * inv_c;
+    u[2] = (R)__ldg(hp + 2 * hq) * inv_c;
+    u[3] = (R)__ldg(hp + 3 * hq) * inv_c;
+  } else {
+    const int idx = cx + g.n[0] * (cy + g.n[1] * zf);
+    u[0] = (R)__ldg(A.yt[Y_ERAD] + idx);
+    u[1] = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
+    u[2] = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
+    const R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+    u[3] = fz ? -Fz : Fz;
+  }
   const int side = GEN ? inflow_side(g, 2, zg) : -1;
   if (side >= 0) {
     const double* st = g.bc_state[2][side];

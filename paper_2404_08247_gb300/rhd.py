@@ -22,7 +22,7 @@ RHD_OK, RHD_ERR_ARG, RHD_ERR_CUDA, RHD_ERR_NEWTON, RHD_ERR_OUTER, \
     RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE = range(8)
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "newton", 4: "outer",
                 5: "nonphysical", 6: "timeout", 7: "state"}
-RHD_BC_PERIODIC, RHD_BC_REFLECT, RHD_BC_INFLOW = 0, 1, 2
+RHD_BC_PERIODIC, RHD_BC_REFLECT, RHD_BC_INFLOW, RHD_BC_HALO = 0, 1, 2, 3
 RHD_SCHEME_IMEX_PDARS, RHD_SCHEME_RK2_SSP = 0, 1
 RHD_CLOSURE_M1, RHD_CLOSURE_EDDINGTON = 0, 1
 RHD_HLL_TAU, RHD_HLL_NONE = 0, 1
@@ -32,7 +32,8 @@ RHD_NFIELDS = 10
 (RHD_F_RHO, RHD_F_MX, RHD_F_MY, RHD_F_MZ, RHD_F_EGAS, RHD_F_ERAD, RHD_F_FX,
  RHD_F_FY, RHD_F_FZ, RHD_F_KAPPA) = range(10)
 
-_BC = {"periodic": RHD_BC_PERIODIC, "reflect": RHD_BC_REFLECT, "inflow": RHD_BC_INFLOW}
+_BC = {"periodic": RHD_BC_PERIODIC, "reflect": RHD_BC_REFLECT, "inflow": RHD_BC_INFLOW,
+       "halo": RHD_BC_HALO}
 _SCHEME = {"imex": RHD_SCHEME_IMEX_PDARS, "rk2ssp": RHD_SCHEME_RK2_SSP}
 _CLOSURE = {"m1": RHD_CLOSURE_M1, "eddington": RHD_CLOSURE_EDDINGTON}
 _HLL = {"tau": RHD_HLL_TAU, "none": RHD_HLL_NONE}
@@ -135,6 +136,8 @@ SIGNATURES = {
                                       ctypes.POINTER(rhd_step_info)]),
     "rhd_step_split": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(rhd_step_info)]),
+    "rhd_step_slabs": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.POINTER(rhd_step_info)]),
     "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
                                         ctypes.POINTER(rhd_step_info)]),
     "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
@@ -444,6 +447,47 @@ class RHDContext:
 
     def default_dt(self) -> float:
         return rhd_default_dt(self.params)
+
+
+def slab_problems(prob: dict, cuts) -> list:
+    """Problem dicts of the z-slabs [cuts[i], cuts[i+1]) of a 3-D problem for
+    rhd_step_slabs (cuts from 0 to n[2], each slab >= 3 planes): the faces
+    between slabs become "halo"; a periodic z axis makes the outer faces
+    "halo" too (they face each other), otherwise they keep their kind."""
+    if int(prob["ndim"]) != 3:
+        raise ValueError("slabs are z ranges of a 3-D grid")
+    cuts = [int(c) for c in cuts]
+    if cuts[0] != 0 or cuts[-1] != int(prob["n"][2]) or len(cuts) < 2:
+        raise ValueError("cuts must run from 0 to n[2]")
+    bc = prob.get("bc", "periodic")
+    axes = [[bc, bc] for _ in range(3)] if isinstance(bc, str) else \
+        [list(bc[d]) if d < len(bc) else ["periodic", "periodic"] for d in range(3)]
+    zper = axes[2][0] == "periodic"
+    out = []
+    for i in range(len(cuts) - 1):
+        q = dict(prob)
+        n = list(prob["n"])
+        n[2] = cuts[i + 1] - cuts[i]
+        q["n"] = n
+        lo = "halo" if (i > 0 or zper) else axes[2][0]
+        hi = "halo" if (i < len(cuts) - 2 or zper) else axes[2][1]
+        q["bc"] = [axes[0], axes[1], [lo, hi]]
+        out.append(q)
+    return out
+
+
+def step_slabs(contexts, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
+    """rhd_step_slabs: nsteps steps of the z-slabs (RHDContext, bottom to top)
+    of one grid, with the ghost planes exchanged before every stage."""
+    lib = load()
+    arr = (_V * len(contexts))(*[c.h.value for c in contexts])
+    info = rhd_step_info()
+    st = lib.rhd_step_slabs(arr, len(contexts), int(nsteps), float(dt), ctypes.byref(info))
+    if raise_on_error:
+        _check(st, contexts[0].h)
+    d = info.as_dict()
+    d["status"] = st
+    return d
 
 
 class RHDBatch:

@@ -166,3 +166,56 @@ def test_hydro_cfl_is_validated(rhd):
     assert st == rhd.RHD_ERR_ARG and "cfl_hydro" in msg
     p = rhd.params_from_problem(I.base_problem(1, [16], [1 / 16], cfl_hydro=0.2))
     assert p.cfl_hydro == 0.2
+
+
+def test_halo_faces_are_validated(rhd):
+    """HALO faces join z-slabs of one 3-D grid: z faces only, n[2] >= 3, never
+    paired with a periodic face; the no-allocation step refuses them."""
+    def params(ndim, n, bc):
+        q = rhd.rhd_params_default()
+        q.ndim = ndim
+        for d in range(3):
+            q.n[d] = n[d] if d < ndim else 1
+            q.dx[d] = 0.1
+        for d, s, kind in bc:
+            q.bc[d][s] = kind
+        return q
+
+    H, R, P = rhd.RHD_BC_HALO, rhd.RHD_BC_REFLECT, rhd.RHD_BC_PERIODIC
+    assert rhd.rhd_params_validate(params(3, [4, 4, 3], [(2, 0, H), (2, 1, H)]))[0] == rhd.RHD_OK
+    assert rhd.rhd_params_validate(params(3, [4, 4, 3], [(2, 0, R), (2, 1, H)]))[0] == rhd.RHD_OK
+    st, msg = rhd.rhd_params_validate(params(3, [4, 4, 2], [(2, 0, H), (2, 1, H)]))
+    assert st == rhd.RHD_ERR_ARG and "n[2] >= 3" in msg
+    st, msg = rhd.rhd_params_validate(params(3, [4, 4, 4], [(0, 0, H), (0, 1, H)]))
+    assert st == rhd.RHD_ERR_ARG and "z faces" in msg
+    st, msg = rhd.rhd_params_validate(params(2, [4, 4], [(1, 0, H), (1, 1, H)]))
+    assert st == rhd.RHD_ERR_ARG and "z faces" in msg
+    st, msg = rhd.rhd_params_validate(params(3, [4, 4, 4], [(2, 0, P), (2, 1, H)]))
+    assert st == rhd.RHD_ERR_ARG and "periodic" in msg
+    assert rhd.rhd_params_validate(params(3, [4, 4, 4], [(2, 0, 4)]))[0] == rhd.RHD_ERR_ARG
+    q = params(3, [4, 4, 4], [(2, 0, H), (2, 1, H)])
+    info = rhd.rhd_step_info()
+    st = rhd.load().rhd_step_noalloc(ctypes.byref(q), None, None, 0.0, None,
+                                     ctypes.byref(info))
+    assert st == rhd.RHD_ERR_ARG and b"rhd_step_slabs" in rhd.load().rhd_last_error(None)
+    st = rhd.load().rhd_step_slabs(None, 0, 1, 0.0, ctypes.byref(info))
+    assert st == rhd.RHD_ERR_ARG and info.fail_cell == -1
+
+
+def test_slab_problems_split_the_z_axis(rhd):
+    prob = I.base_problem(3, [8, 6, 12], [1 / 8, 1 / 6, 1 / 12], bc="reflect")
+    qs = rhd.slab_problems(prob, [0, 4, 9, 12])
+    assert [q["n"][2] for q in qs] == [4, 5, 3]
+    assert [q["bc"][2] for q in qs] == [["reflect", "halo"], ["halo", "halo"],
+                                        ["halo", "reflect"]]
+    assert all(q["bc"][0] == ["reflect", "reflect"] for q in qs)
+    qs = rhd.slab_problems(I.base_problem(3, [8, 6, 12], [1 / 8, 1 / 6, 1 / 12]), [0, 6, 12])
+    assert [q["bc"][2] for q in qs] == [["halo", "halo"], ["halo", "halo"]]
+    for q in qs:
+        p = rhd.params_from_problem(q)
+        assert p.bc[2][0] == p.bc[2][1] == rhd.RHD_BC_HALO
+        assert rhd.rhd_params_validate(p)[0] == rhd.RHD_OK
+    with pytest.raises(ValueError):
+        rhd.slab_problems(prob, [0, 5])
+    with pytest.raises(ValueError):
+        rhd.slab_problems(I.base_problem(2, [8, 6], [1 / 8, 1 / 6]), [0, 6])

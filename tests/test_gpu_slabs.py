@@ -1,0 +1,153 @@
+"""z-slab decomposition on one GPU (rhd_step_slabs): the radiation step needs
+only ghost layers of (E, F) from face neighbours (Sec. 3.2), so slabs that
+exchange their boundary planes before every stage step exactly like the
+undecomposed grid.  Every case compares all ten fields bit for bit with the
+single-context run (itself pinned to the oracle by the parity tests), and the
+iteration statistics with its own."""
+import numpy as np
+import pytest
+
+from paper_2404_08247_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2404_08247_gb300 import build as B
+    B.build()
+    from paper_2404_08247_gb300 import rhd
+    rhd.load()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return rhd
+
+
+def whole(R, prob, U, nsteps, dt, precision):
+    with R.RHDContext(prob, precision) as ctx:
+        ctx.set_state(U)
+        info = ctx.step(nsteps, dt, raise_on_error=False)
+        return ctx.get_state(), info
+
+
+def slabs(R, prob, U, cuts, nsteps, dt, precision, calls=1):
+    """The slabs of cuts, stepped in `calls` calls of nsteps / calls steps."""
+    stream = torch.cuda.current_stream()
+    ctxs = [R.RHDContext(q, precision, stream=stream) for q in R.slab_problems(prob, cuts)]
+    try:
+        for c, z0, z1 in zip(ctxs, cuts, cuts[1:]):
+            c.set_state(np.ascontiguousarray(U[:, z0:z1]))
+        infos = [R.step_slabs(ctxs, nsteps // calls, dt, raise_on_error=False)
+                 for _ in range(calls)]
+        Us = np.concatenate([c.get_state() for c in ctxs], axis=1)
+        times = [c.time() for c in ctxs]
+    finally:
+        for c in ctxs:
+            c.close()
+    return Us, infos, times
+
+
+CASES = [
+    # shape, cuts, options, precision, steps
+    ((37, 23, 19), [0, 9, 19], dict(hll_mode="tau"), "fp64", 4),
+    ((37, 23, 19), [0, 3, 11, 19], dict(hll_mode="none"), "fp64", 4),
+    ((24, 20, 18), [0, 5, 11, 18], dict(hll_mode="tau", walls=True), "mixed", 4),
+    ((24, 20, 18), [0, 18], dict(hll_mode="tau"), "fp64", 3),
+    ((20, 17, 16), [0, 3, 9, 16], dict(hll_mode="tau", reconstruction="ppm"), "fp64", 3),
+    ((20, 17, 16), [0, 8, 16], dict(hll_mode="none", reconstruction="ppm"), "mixed", 3),
+    ((20, 17, 16), [0, 6, 16],
+     dict(hll_mode="tau", scheme="rk2ssp", kappa_P_ratio=2.0, kappa_F_ratio=0.5), "fp64", 3),
+]
+
+
+def case_problem(shape, opts):
+    """The turbulent box of shape with opts; walls: reflecting y and z axes."""
+    opts = dict(opts)
+    walls = opts.pop("walls", False)
+    prob, U, _ = I.turbulent_box_3d(shape=shape, **opts)
+    if walls:
+        prob = dict(prob, bc=[["periodic"] * 2, ["reflect"] * 2, ["reflect"] * 2])
+    return prob, U
+
+
+@pytest.mark.parametrize("ci", range(len(CASES)), ids=[str(c[:2]) for c in CASES])
+def test_slabs_step_like_the_whole_grid(R, ci):
+    shape, cuts, opts, precision, nsteps = CASES[ci]
+    prob, U = case_problem(shape, opts)
+    dt = R.rhd_default_dt(R.params_from_problem(prob))
+    Uw, iw = whole(R, prob, U, nsteps, dt, precision)
+    assert iw["status"] == R.RHD_OK
+    Us, infos, times = slabs(R, prob, U, cuts, nsteps, dt, precision)
+    info = infos[0]
+    assert info["status"] == R.RHD_OK and info["steps_done"] == nsteps
+    assert all(t == pytest.approx(nsteps * dt, rel=1e-15) for t in times)
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), (CASES[ci], f)
+    for k in ("n_solves", "sum_newton", "sum_outer", "max_newton", "max_outer"):
+        assert info[k] == iw[k], k
+
+
+def test_inflow_and_reflecting_end_faces(R):
+    """The outer z faces keep their own kind (an inflow source below, a wall
+    above); the interior faces are HALO."""
+    shape = (16, 12, 15)
+    bc = [["periodic"] * 2, ["periodic"] * 2, ["inflow", "reflect"]]
+    prob = I.base_problem(3, list(shape), [1 / 16] * 3, c=30.0, chat=10.0, bc=bc,
+                          hll_mode="none", bc_state={(2, 0): (5.0, 2.0, 0.0, 1.0)})
+    U = I.random_state(prob, 23, tau_range=(1e-2, 10.0))
+    dt = R.rhd_default_dt(R.params_from_problem(prob))
+    Uw, iw = whole(R, prob, U, 4, dt, "fp64")
+    Us, infos, _ = slabs(R, prob, U, [0, 4, 8, 15], 4, dt, "fp64", calls=2)
+    assert all(i["status"] == R.RHD_OK for i in infos)
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), f
+
+
+def test_a_failure_stops_every_slab(R):
+    """A step far beyond the transport's CFL bound drives E negative: the
+    slabs report the whole grid's failing step, stage and smallest cell, and
+    every slab keeps the state of the last step all of them completed."""
+    prob, U, _ = I.turbulent_box_3d(shape=(24, 20, 18), hll_mode="none")
+    dt = 60.0 * R.rhd_default_dt(R.params_from_problem(prob))
+    Uw, iw = whole(R, prob, U, 2, dt, "fp64")
+    assert iw["status"] != R.RHD_OK
+    Us, infos, times = slabs(R, prob, U, [0, 6, 12, 18], 2, dt, "fp64")
+    info = infos[0]
+    for k in ("status", "steps_done", "fail_step", "fail_stage"):
+        assert info[k] == iw[k], k
+    # blocks that start after the first failure skip their cells, so the
+    # smallest failing cell reported is one of the failing cells, not
+    # necessarily the same one in both runs
+    assert 0 <= info["fail_cell"] < U[0].size
+    assert np.array_equal(Us, Uw)
+    assert all(t == iw["steps_done"] * dt for t in times)
+
+
+def test_slab_arguments_are_checked(R):
+    prob, U, _ = I.turbulent_box_3d(shape=(16, 12, 12))
+    stream = torch.cuda.current_stream()
+    qs = R.slab_problems(prob, [0, 6, 12])
+    a = R.RHDContext(qs[0], stream=stream)
+    b = R.RHDContext(qs[1], stream=stream)
+    other = dict(qs[1], n=[16, 12, 6], dx=[1 / 16, 1 / 12, 0.5])
+    c = R.RHDContext(other, stream=stream)
+    try:
+        for ctx, z0 in ((a, 0), (b, 6), (c, 6)):
+            ctx.set_state(np.ascontiguousarray(U[:, z0:z0 + 6]))
+        with pytest.raises(R.RHDError, match="rhd_step_slabs"):
+            a.step(1)
+        with pytest.raises(R.RHDError, match="rhd_step_slabs"):
+            a.transport()
+        with pytest.raises(R.RHDError, match="params differ"):
+            R.step_slabs([a, c])
+        with pytest.raises(R.RHDError, match="one context"):
+            R.step_slabs([a, a])
+        b.set_stream(None)
+        with pytest.raises(R.RHDError, match="one stream"):
+            R.step_slabs([a, b])
+        b.set_stream(stream)
+        info = R.step_slabs([a, b], 0)
+        assert info["status"] == R.RHD_OK and info["steps_done"] == 0
+    finally:
+        for ctx in (a, b, c):
+            ctx.close()
