@@ -354,6 +354,21 @@ rhd_status rhd_step_split(rhd_ctx* ctx, int nsteps, double dt_h, rhd_step_info* 
 rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
                           rhd_step_info* info);
 
+/* The hydrodynamic step (rhd_hydro_step) and the operator split
+ * (rhd_step_split) of z-slabs, with the same slab rules and the same
+ * results as on the undecomposed grid, bit for bit.  Before each of the two
+ * RK2-SSP stages every slab receives the neighbours' boundary planes of the
+ * primitives (rho, v, p), 2 with PLM and 3 with PPM; dt <= 0 (dt_h <= 0)
+ * takes the CFL step of the whole grid (the largest bound of any slab); the
+ * stage-2 result is committed to every slab only if no cell of any slab
+ * failed.  Inflow faces are refused (RHD_ERR_ARG) as for one grid.  The
+ * first call allocates the hydrodynamic scratch of rhd_hydro_step per slab
+ * and 30 * n[0] * n[1] doubles of halo.  Synchronise. */
+rhd_status rhd_hydro_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                                rhd_step_info* info);
+rhd_status rhd_step_split_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt_h,
+                                rhd_step_info* info);
+
 /* Number of kernels this context has launched since rhd_init. */
 int64_t rhd_launch_count(const rhd_ctx* ctx);
 

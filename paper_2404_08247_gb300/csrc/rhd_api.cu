@@ -76,6 +76,7 @@ struct rhd_ctx {
   // HALO_PLANES planes), plane 0 of the slab above (kappa, rho) and the TAU
   // factors of the low face; allocated by the first rhd_step_slabs
   double* halo = nullptr;
+  double* hyd_halo = nullptr;  // the same for the primitives (2 x 5 x HALO_PLANES planes)
 };
 
 // a context whose grid is a z-slab of a decomposed grid
@@ -345,6 +346,7 @@ static void release(rhd_ctx* c) {
   for (int d = 0; d < 3; ++d) cudaFree(c->hyd_f[d]);
   cudaFree(c->hyd_bits);
   cudaFree(c->halo);
+  cudaFree(c->hyd_halo);
   cudaFreeHost(c->h_status);
   cudaFreeHost(c->h_tot);
   cudaFreeHost(c->h_flag);
@@ -921,6 +923,8 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
 
 // ------------------------------------------------ hydrodynamics (Sec. 3.1)
 
+static rhd_status hydro_alloc(rhd_ctx* c);
+
 static rhd_status hydro_ready(rhd_ctx* c) {
   if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
   if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
@@ -930,6 +934,11 @@ static rhd_status hydro_ready(rhd_ctx* c) {
   for (int d = 0; d < c->p.ndim; ++d)
     if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
       return fail(c, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
+  return hydro_alloc(c);
+}
+
+// the hydrodynamic scratch of a context, allocated once
+static rhd_status hydro_alloc(rhd_ctx* c) {
   CUDA_TRY(c, cudaSetDevice(c->device));
   if (!c->hyd_w) {
     const size_t N = (size_t)c->ncell;
@@ -1116,17 +1125,20 @@ static bool same_grid_but_z(const rhd_params& a, const rhd_params& b) {
          a.newton_max_iter == b.newton_max_iter && a.outer_max_iter == b.outer_max_iter &&
          a.scheme == b.scheme && a.kappa_T_exp == b.kappa_T_exp &&
          a.kappa_T_ref == b.kappa_T_ref && a.kappa_P_ratio == b.kappa_P_ratio &&
-         a.kappa_F_ratio == b.kappa_F_ratio && a.reconstruction == b.reconstruction;
+         a.kappa_F_ratio == b.kappa_F_ratio && a.reconstruction == b.reconstruction &&
+         a.cfl_hydro == b.cfl_hydro;
 }
 
-// Copy the ghost planes of slab s from its neighbours' state buffers src[]
-// (slot-major, NY * ncell doubles each): depth planes of E, Fx, Fy, Fz per
-// HALO face, one device-to-device copy per field and face.
+// Copy the ghost planes of slab s from its neighbours: depth planes of the
+// nfield fields slot[] of the buffers src[] (field f of slab u at
+// src[u] + f * ncell(u)) per HALO face into the slab's halo buffer
+// [side][field][HALO_PLANES planes][n0 n1], one device-to-device copy per
+// field and face.
 static cudaError_t exchange(rhd_ctx* const* slabs, int nslab, int s, double* const* src,
-                            int depth, cudaStream_t st) {
+                            const int* slot, int nfield, double* halo, int depth,
+                            cudaStream_t st) {
   rhd_ctx* c = slabs[s];
   const size_t P = (size_t)c->g.n[0] * c->g.n[1];
-  static const int slot[4] = {Y_ERAD, Y_FX, Y_FY, Y_FZ};
   for (int side = 0; side < 2; ++side) {
     if (c->p.bc[2][side] != RHD_BC_HALO) continue;
     const int nb = side == 0 ? (s + nslab - 1) % nslab : (s + 1) % nslab;
@@ -1135,8 +1147,8 @@ static cudaError_t exchange(rhd_ctx* const* slabs, int nslab, int s, double* con
     // planes -depth..-1), the high face the bottom ones of the slab above
     const size_t z0 = side == 0 ? (size_t)u->g.n[2] - depth : 0;
     const size_t i0 = side == 0 ? HALO_PLANES - depth : 0;
-    double* h = c->halo + (size_t)side * 4 * HALO_PLANES * P;
-    for (int q = 0; q < 4; ++q) {
+    double* h = halo + (size_t)side * nfield * HALO_PLANES * P;
+    for (int q = 0; q < nfield; ++q) {
       cudaError_t e = cudaMemcpyAsync(
           h + ((size_t)q * HALO_PLANES + i0) * P,
           src[nb] + (size_t)slot[q] * u->ncell + z0 * P, sizeof(double) * depth * P,
@@ -1147,15 +1159,18 @@ static cudaError_t exchange(rhd_ctx* const* slabs, int nslab, int s, double* con
   return cudaSuccess;
 }
 
-extern "C" {
+static void clear_info(rhd_step_info* info, double t) {
+  if (!info) return;
+  memset(info, 0, sizeof(*info));
+  info->fail_cell = -1;
+  info->fail_step = -1;
+  info->t = t;
+}
 
-rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
-                          rhd_step_info* info) {
-  if (info) {
-    memset(info, 0, sizeof(*info));
-    info->fail_cell = -1;
-    info->fail_step = -1;
-  }
+// The checks every slab call makes: distinct contexts of one grid's z-slabs,
+// one device and stream, every field set, HALO faces between neighbours and
+// at both ends or at neither.
+static rhd_status check_slabs(rhd_ctx* const* slabs, int nslab) {
   if (!slabs || nslab < 1) return fail(nullptr, RHD_ERR_ARG, "slabs is NULL or nslab < 1");
   for (int s = 0; s < nslab; ++s) {
     if (!slabs[s]) return fail(nullptr, RHD_ERR_ARG, "slabs[%d] is NULL", s);
@@ -1184,12 +1199,17 @@ rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double d
   if (wrap != (slabs[last]->p.bc[2][1] == RHD_BC_HALO))
     return fail(c0, RHD_ERR_ARG, "the bottom face of slab 0 and the top face of slab %d "
                 "are both HALO (a periodic grid) or neither", last);
-  if (!wrap && (c0->p.bc[2][0] == RHD_BC_PERIODIC) && nslab > 1)
+  if (!wrap && c0->p.bc[2][0] == RHD_BC_PERIODIC && nslab > 1)
     return fail(c0, RHD_ERR_ARG, "a periodic z axis of several slabs uses HALO end faces");
-  if (nsteps < 0) return fail(c0, RHD_ERR_ARG, "nsteps < 0");
-  if (!(dt > 0.0)) dt = rhd_default_dt(&c0->p);
-  if (!std::isfinite(dt)) return fail(c0, RHD_ERR_ARG, "dt is not finite");
   CUDA_TRY(c0, cudaSetDevice(c0->device));
+  return RHD_OK;
+}
+
+// nsteps radiation steps of dt of checked slabs (rhd_step_slabs)
+static rhd_status slab_radiation(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                                 rhd_step_info* info) {
+  rhd_ctx* c0 = slabs[0];
+  clear_info(info, c0->t);
   const cudaStream_t st = c0->stream;
   const size_t P = (size_t)c0->g.n[0] * c0->g.n[1];
   for (int s = 0; s < nslab; ++s)
@@ -1232,6 +1252,7 @@ rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double d
 
   CUDA_TRY(c0, launch_status_reset(c0->d_status, st));
   c0->launches += 1;
+  static const int kRadSlots[4] = {Y_ERAD, Y_FX, Y_FY, Y_FZ};
   const int depth = c0->p.reconstruction == RHD_RECON_PLM ? 2 : 3;
   std::vector<StageArgs> A(nslab);
   std::vector<int> cur(nslab), cur0(nslab);
@@ -1257,7 +1278,8 @@ rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double d
   for (int k = 0; k < nsteps; ++k) {
     for (int s = 0; s < nslab; ++s) src[s] = slabs[s]->ybuf[cur[s]];
     for (int s = 0; s < nslab; ++s)
-      CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), depth, st));
+      CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), kRadSlots, 4, slabs[s]->halo, depth,
+                            st));
     for (int s = 0; s < nslab; ++s) {
       rhd_ctx* c = slabs[s];
       StageArgs& a = A[s];
@@ -1269,7 +1291,8 @@ rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double d
     }
     for (int s = 0; s < nslab; ++s) src[s] = slabs[s]->yhalf;
     for (int s = 0; s < nslab; ++s)
-      CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), depth, st));
+      CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), kRadSlots, 4, slabs[s]->halo, depth,
+                            st));
     for (int s = 0; s < nslab; ++s) {
       rhd_ctx* c = slabs[s];
       StageArgs& a = A[s];
@@ -1314,6 +1337,190 @@ rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double d
     return fail(c0, code, "step %d stage %d failed at cell %lld of the slabs (status %d)",
                 ds.fail_step, ds.fail_stage, (long long)cell, (int)code);
   return RHD_OK;
+}
+
+// the hydrodynamic step's conditions on checked slabs: no inflow face
+static rhd_status check_slabs_hydro(rhd_ctx* const* slabs, int nslab) {
+  rhd_ctx* c0 = slabs[0];
+  for (int d = 0; d < 2; ++d)
+    if (c0->p.bc[d][0] == RHD_BC_INFLOW || c0->p.bc[d][1] == RHD_BC_INFLOW)
+      return fail(c0, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
+  if (c0->p.bc[2][0] == RHD_BC_INFLOW || slabs[nslab - 1]->p.bc[2][1] == RHD_BC_INFLOW)
+    return fail(c0, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
+  for (int s = 0; s < nslab; ++s) {
+    rhd_status r = hydro_alloc(slabs[s]);
+    if (r != RHD_OK) return fail(c0, r, "slab %d: %s", s, slabs[s]->err);
+  }
+  const size_t P = (size_t)c0->g.n[0] * c0->g.n[1];
+  for (int s = 0; s < nslab; ++s)
+    if (!slabs[s]->hyd_halo) {
+      cudaError_t e =
+          cudaMalloc(&slabs[s]->hyd_halo, sizeof(double) * 2 * 5 * HALO_PLANES * P);
+      if (e != cudaSuccess)
+        return fail(c0, RHD_ERR_CUDA, "slab %d: halo buffers: %s", s, cudaGetErrorString(e));
+    }
+  return RHD_OK;
+}
+
+// nsteps hydrodynamic steps of dt (dt <= 0: the CFL step of the whole grid
+// before each step) of checked slabs, like hydro_run on the whole grid
+static rhd_status slab_hydro(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                             rhd_step_info* info, bool advance_time) {
+  rhd_ctx* c0 = slabs[0];
+  clear_info(info, c0->t);
+  const cudaStream_t st = c0->stream;
+  const size_t P = (size_t)c0->g.n[0] * c0->g.n[1];
+  static const int kPrimSlots[5] = {0, 1, 2, 3, 4};
+  const int depth = c0->p.reconstruction == RHD_RECON_PLM ? 2 : 3;
+  std::vector<unsigned long long> bits(nslab);
+  std::vector<double*> src(nslab);
+  for (int s = 0; s < nslab; ++s) src[s] = slabs[s]->hyd_w;
+  int done = 0;
+  double last = dt;
+  rhd_status code = RHD_OK;
+  while (done < nsteps && code == RHD_OK) {
+    int batch = dt > 0.0 ? nsteps - done : 1;
+    double h = dt;
+    if (!(h > 0.0)) {
+      // the largest signal-speed bound of any slab: the whole grid's
+      for (int s = 0; s < nslab; ++s) {
+        CUDA_TRY(c0, launch_hydro_speed(slabs[s]->g, c0->p.gamma, hydro_bufs(slabs[s]), st));
+        slabs[s]->launches += 1;
+        CUDA_TRY(c0, cudaMemcpyAsync(&bits[s], slabs[s]->hyd_bits, sizeof(bits[s]),
+                                     cudaMemcpyDeviceToHost, st));
+      }
+      CUDA_TRY(c0, cudaStreamSynchronize(st));
+      unsigned long long mx = 0;
+      for (int s = 0; s < nslab; ++s) mx = std::max(mx, bits[s]);
+      double smax;
+      memcpy(&smax, &mx, sizeof(smax));
+      if (!(smax > 0.0) || !std::isfinite(smax)) {
+        code = fail(c0, RHD_ERR_NONPHYSICAL,
+                    "a cell has rho <= 0 or p <= 0: no hydrodynamic step");
+        break;
+      }
+      h = c0->p.cfl_hydro / smax;
+    }
+    last = h;
+    CUDA_TRY(c0, launch_status_reset(c0->d_status, st));
+    c0->launches += 1;
+    std::vector<HydroBufs> B(nslab);
+    long long base = 0;
+    for (int s = 0; s < nslab; ++s) {
+      B[s] = hydro_bufs(slabs[s]);
+      B[s].halo[0] = slabs[s]->hyd_halo;
+      B[s].halo[1] = slabs[s]->hyd_halo + (size_t)5 * HALO_PLANES * P;
+      B[s].cell_base = base;
+      base += slabs[s]->ncell;
+    }
+    for (int k = 0; k < batch; ++k) {
+      for (int phase = 0; phase < 5; ++phase) {
+        // the face phases read the neighbours' primitives of this stage
+        if (phase == 1 || phase == 3)
+          for (int s = 0; s < nslab; ++s)
+            CUDA_TRY(c0, exchange(slabs, nslab, s, src.data(), kPrimSlots, 5,
+                                  slabs[s]->hyd_halo, depth, st));
+        for (int s = 0; s < nslab; ++s) {
+          CUDA_TRY(c0, launch_hydro_phase(phase, slabs[s]->g, c0->p.gamma,
+                                          c0->p.reconstruction, h, B[s], c0->d_status, k, st));
+          slabs[s]->launches += phase == 1 || phase == 3 ? 1 + c0->p.ndim : 1;
+        }
+      }
+    }
+    CUDA_TRY(c0, cudaMemcpyAsync(c0->h_status, c0->d_status, sizeof(DevStatus),
+                                 cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c0, cudaStreamSynchronize(st));
+    const DevStatus& ds = *c0->h_status;
+    int ok = batch;
+    for (int s = 0; s < nslab; ++s) slabs[s]->eps_dirty = true;  // rho has changed
+    if (ds.fail_key != ~0ull) {
+      code = (rhd_status)(ds.fail_key & 0xffull);
+      ok = ds.fail_step;
+      if (info) {
+        info->fail_cell = (int64_t)(ds.fail_key >> 8);
+        info->fail_step = done + ds.fail_step;
+        info->fail_stage = ds.fail_stage;
+      }
+    }
+    done += ok;
+    if (advance_time)
+      for (int s = 0; s < nslab; ++s) slabs[s]->t += ok * h;
+  }
+  if (info) {
+    info->status = code;
+    info->steps_done = done;
+    info->t = c0->t;
+    info->dt = last;
+  }
+  if (code != RHD_OK)
+    return fail(c0, code, "hydrodynamic step %d of the slabs failed (status %d)", done,
+                (int)code);
+  return RHD_OK;
+}
+
+extern "C" {
+
+rhd_status rhd_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                          rhd_step_info* info) {
+  clear_info(info, 0.0);
+  rhd_status s = check_slabs(slabs, nslab);
+  if (s != RHD_OK) return s;
+  if (nsteps < 0) return fail(slabs[0], RHD_ERR_ARG, "nsteps < 0");
+  if (!(dt > 0.0)) dt = rhd_default_dt(&slabs[0]->p);
+  if (!std::isfinite(dt)) return fail(slabs[0], RHD_ERR_ARG, "dt is not finite");
+  return slab_radiation(slabs, nslab, nsteps, dt, info);
+}
+
+rhd_status rhd_hydro_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt,
+                                rhd_step_info* info) {
+  clear_info(info, 0.0);
+  rhd_status s = check_slabs(slabs, nslab);
+  if (s == RHD_OK) s = check_slabs_hydro(slabs, nslab);
+  if (s != RHD_OK) return s;
+  if (nsteps < 0) return fail(slabs[0], RHD_ERR_ARG, "nsteps < 0");
+  if (!std::isfinite(dt)) return fail(slabs[0], RHD_ERR_ARG, "dt is not finite");
+  return slab_hydro(slabs, nslab, nsteps, dt, info, true);
+}
+
+rhd_status rhd_step_split_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt_h,
+                                rhd_step_info* info) {
+  clear_info(info, 0.0);
+  rhd_status s = check_slabs(slabs, nslab);
+  if (s == RHD_OK) s = check_slabs_hydro(slabs, nslab);
+  if (s != RHD_OK) return s;
+  rhd_ctx* c0 = slabs[0];
+  if (nsteps < 0) return fail(c0, RHD_ERR_ARG, "nsteps < 0");
+  if (!std::isfinite(dt_h)) return fail(c0, RHD_ERR_ARG, "dt_h is not finite");
+  rhd_step_info total;
+  clear_info(&total, c0->t);
+  const double dt_rad = rhd_default_dt(&c0->p);
+  for (int k = 0; s == RHD_OK && k < nsteps; ++k) {
+    rhd_step_info one;
+    s = slab_hydro(slabs, nslab, 1, dt_h, &one, false);
+    const double h = one.dt;
+    if (s == RHD_OK) {
+      int nsub = (int)std::ceil(h / dt_rad - 1e-12);
+      if (nsub < 1) nsub = 1;
+      s = slab_radiation(slabs, nslab, nsub, h / nsub, &one);
+      total.max_newton = std::max(total.max_newton, one.max_newton);
+      total.max_outer = std::max(total.max_outer, one.max_outer);
+      total.sum_newton += one.sum_newton;
+      total.sum_outer += one.sum_outer;
+      total.n_solves += one.n_solves;
+    }
+    total.dt = h;
+    if (s != RHD_OK) {
+      total.fail_cell = one.fail_cell;
+      total.fail_step = k;
+      total.fail_stage = one.fail_stage;
+    } else {
+      total.steps_done = k + 1;
+    }
+  }
+  total.status = s;
+  total.t = c0->t;
+  if (info) *info = total;
+  return s;
 }
 
 int64_t rhd_launch_count(const rhd_ctx* c) { return c ? c->launches : 0; }

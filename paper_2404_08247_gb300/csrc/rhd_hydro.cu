@@ -42,7 +42,7 @@ __device__ __forceinline__ void record_fail(DevStatus* st, long long cell, int s
 
 __global__ void __launch_bounds__(kThreads) prim_kernel(int n, double gm1, Cons U,
                                                          double* __restrict__ w, DevStatus* st,
-                                                         int step, int stage) {
+                                                         int step, int stage, long long base) {
   if (block_skip(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double r = U.q[0][i];
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) prim_kernel(int n, double gm1, Cons 
     const double ke = 0.5 * (mx * vx + my * vy + mz * vz);
     const double p = gm1 * (U.q[4][i] - ke);
     if (!(rok && pos_finite(p) && finite_bits(vx) && finite_bits(vy) && finite_bits(vz)))
-      record_fail(st, i, step, stage);
+      record_fail(st, base + i, step, stage);
     w[i] = r;
     w[n + i] = vx;
     w[2 * n + i] = vy;
@@ -134,9 +134,13 @@ __global__ void __launch_bounds__(kThreads) face_kernel(const Geometry g, double
                                                          double g1i,
                                                          const double* __restrict__ w,
                                                          double* __restrict__ f, long long nf,
-                                                         DevStatus* st, int step, int stage) {
+                                                         DevStatus* st, int step, int stage,
+                                                         const double* __restrict__ hlo,
+                                                         const double* __restrict__ hhi,
+                                                         long long base) {
   if (block_skip(st)) return;
   constexpr int H = RK != RHD_RECON_PLM ? 3 : 2, NS = 2 * H;
+  const size_t P = (size_t)g.n[0] * g.n[1];
   const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1);
   const int N = g.ncell;
   for (long long fi = (long long)blockIdx.x * blockDim.x + threadIdx.x; fi < nf;
@@ -149,6 +153,17 @@ __global__ void __launch_bounds__(kThreads) face_kernel(const Geometry g, double
     double u[5][NS];
 #pragma unroll
     for (int o = 0; o < NS; ++o) {
+      // a ghost plane of a HALO z face: the neighbouring slab's primitives
+      const int hs = D == 2 ? halo_side(g, c[2] - H + o) : -1;
+      if (hs >= 0) {
+        const int z = c[2] - H + o;
+        const double* hp = (hs == 0 ? hlo + (size_t)(z + HALO_PLANES) * P
+                                    : hhi + (size_t)(z - g.n[2]) * P) +
+                           c[0] + (size_t)g.n[0] * c[1];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) u[k][o] = __ldg(hp + (size_t)k * HALO_PLANES * P);
+        continue;
+      }
       bool flip;
       int q[3] = {c[0], c[1], c[2]};
       q[D] = fold(c[D] - H + o, g.n[D], g.bc[D][0], g.bc[D][1], flip, H - 1);
@@ -173,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) face_kernel(const Geometry g, double
     if (!hllc<D>(gamma, g1i, L, R, F)) {
       int q[3] = {c[0], c[1], c[2]};
       q[D] = min(q[D], g.n[D] - 1);
-      record_fail(st, q[0] + g.n[0] * (q[1] + g.n[1] * q[2]), step, stage);
+      record_fail(st, base + q[0] + g.n[0] * (q[1] + g.n[1] * q[2]), step, stage);
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) f[k * nf + fi] = F[k];
@@ -190,7 +205,8 @@ template <int STAGE>
 __global__ void __launch_bounds__(kThreads) update_kernel(const Geometry g, double dt, double gm1,
                                                            Cons U, const double* __restrict__ u1,
                                                            Faces F, double* __restrict__ out,
-                                                           DevStatus* st, int step) {
+                                                           DevStatus* st, int step,
+                                                           long long base) {
   if (block_skip(st)) return;
   const int N = g.ncell;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -220,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(const Geometry g, doub
     }
     const double ri = pos_finite(o[0]) ? rcp_pos(o[0]) : 0.0;
     const double p = gm1 * (o[4] - 0.5 * ri * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]));
-    if (!(pos_finite(o[0]) && pos_finite(p))) record_fail(st, i, step, 2 + STAGE);
+    if (!(pos_finite(o[0]) && pos_finite(p))) record_fail(st, base + i, step, 2 + STAGE);
 #pragma unroll
     for (int k = 0; k < 5; ++k) out[(size_t)k * N + i] = o[k];
   }
@@ -290,12 +306,17 @@ cudaError_t launch_faces(const Geometry& g, double gamma, const double* w, const
   for (int d = 0; d < g.ndim; ++d) {
     const long long nf = hydro_faces(g, d);
     const int nb = blocks_for(nf);
+    const double *hl = b.halo[0], *hh = b.halo[1];
+    const long long cb = b.cell_base;
     if (d == 0)
-      face_kernel<0, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[0], nf, st, step, stage);
+      face_kernel<0, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[0], nf, st, step, stage,
+                                                 hl, hh, cb);
     else if (d == 1)
-      face_kernel<1, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[1], nf, st, step, stage);
+      face_kernel<1, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[1], nf, st, step, stage,
+                                                 hl, hh, cb);
     else
-      face_kernel<2, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[2], nf, st, step, stage);
+      face_kernel<2, RK><<<nb, kThreads, 0, s>>>(g, gamma, g1i, w, b.f[2], nf, st, step, stage,
+                                                 hl, hh, cb);
   }
   return cudaGetLastError();
 }
@@ -306,11 +327,12 @@ long long hydro_faces(const Geometry& g, int d) {
   return (long long)g.ncell / g.n[d] * (g.n[d] + 1);
 }
 
-cudaError_t launch_hydro_step(const Geometry& g, double gamma, int recon, double dt,
-                              const HydroBufs& b, DevStatus* st, int step, cudaStream_t s) {
+cudaError_t launch_hydro_phase(int phase, const Geometry& g, double gamma, int recon, double dt,
+                               const HydroBufs& b, DevStatus* st, int step, cudaStream_t s) {
   const int N = g.ncell;
   const int nb = blocks_for(N);
   const double gm1 = gamma - 1.0;
+  const long long cb = b.cell_base;
   Cons un, c1;
   un.q[0] = b.rho;
   for (int j = 0; j < 3; ++j) un.q[1 + j] = b.y + (size_t)(Y_MX + j) * N;
@@ -328,18 +350,38 @@ cudaError_t launch_hydro_step(const Geometry& g, double gamma, int recon, double
       return launch_faces<RHD_RECON_PPM>(g, gamma, b.w, b, st, step, stage, s);
     return launch_faces<RHD_RECON_PLM>(g, gamma, b.w, b, st, step, stage, s);
   };
-  // stage 1: U1 = U + dt L(U)
-  prim_kernel<<<nb, kThreads, 0, s>>>(N, gm1, un, b.w, st, step, 3);
-  cudaError_t e = faces(3);
-  if (e != cudaSuccess) return e;
-  update_kernel<1><<<nb, kThreads, 0, s>>>(g, dt, gm1, un, nullptr, F, b.u1, st, step);
-  // stage 2: U <- (U + U1 + dt L(U1)) / 2, staged in w, then committed
-  prim_kernel<<<nb, kThreads, 0, s>>>(N, gm1, c1, b.w, st, step, 4);
-  e = faces(4);
-  if (e != cudaSuccess) return e;
-  update_kernel<2><<<nb, kThreads, 0, s>>>(g, dt, gm1, un, b.u1, F, b.w, st, step);
-  commit_kernel<<<nb, kThreads, 0, s>>>(N, b.w, b.rho, b.y, st);
+  cudaError_t e = cudaSuccess;
+  switch (phase) {
+    case 0:  // stage 1: U1 = U + dt L(U)
+      prim_kernel<<<nb, kThreads, 0, s>>>(N, gm1, un, b.w, st, step, 3, cb);
+      break;
+    case 1:
+      e = faces(3);
+      if (e != cudaSuccess) return e;
+      update_kernel<1><<<nb, kThreads, 0, s>>>(g, dt, gm1, un, nullptr, F, b.u1, st, step, cb);
+      break;
+    case 2:  // stage 2: U <- (U + U1 + dt L(U1)) / 2, staged in w, then committed
+      prim_kernel<<<nb, kThreads, 0, s>>>(N, gm1, c1, b.w, st, step, 4, cb);
+      break;
+    case 3:
+      e = faces(4);
+      if (e != cudaSuccess) return e;
+      update_kernel<2><<<nb, kThreads, 0, s>>>(g, dt, gm1, un, b.u1, F, b.w, st, step, cb);
+      break;
+    default:
+      commit_kernel<<<nb, kThreads, 0, s>>>(N, b.w, b.rho, b.y, st);
+      break;
+  }
   return cudaGetLastError();
+}
+
+cudaError_t launch_hydro_step(const Geometry& g, double gamma, int recon, double dt,
+                              const HydroBufs& b, DevStatus* st, int step, cudaStream_t s) {
+  for (int phase = 0; phase < 5; ++phase) {
+    cudaError_t e = launch_hydro_phase(phase, g, gamma, recon, dt, b, st, step, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_hydro_speed(const Geometry& g, double gamma, const HydroBufs& b,

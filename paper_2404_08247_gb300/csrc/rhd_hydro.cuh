@@ -18,6 +18,12 @@ struct HydroBufs {
   double* u1;
   double* f[3];
   unsigned long long* dt_bits;  // one word for the CFL reduction
+  // RHD_BC_HALO z faces: the neighbouring slabs' primitive planes, per side
+  // [5 fields rho, vx, vy, vz, p][HALO_PLANES planes][n0 n1] in z order (as
+  // the radiation halo), and the index of cell 0 in the whole grid (for
+  // failure reports)
+  const double* halo[2] = {nullptr, nullptr};
+  long long cell_base = 0;
 };
 
 // faces of axis d: (n_d + 1) per grid line
@@ -31,6 +37,14 @@ long long hydro_faces(const Geometry& g, int d);
 // the same status block skip their work.
 cudaError_t launch_hydro_step(const Geometry& g, double gamma, int recon, double dt,
                               const HydroBufs& b, DevStatus* st, int step, cudaStream_t s);
+
+// The same step in five phases, so that z-slabs can exchange primitive
+// planes between them and commit only once every slab has its stage 2: 0:
+// primitives of U into w; 1: face fluxes of w and U1 = U + dt L into u1; 2:
+// primitives of U1 into w; 3: face fluxes of w and the stage-2 combination,
+// staged in w; 4: the commit (skipped after a failure).
+cudaError_t launch_hydro_phase(int phase, const Geometry& g, double gamma, int recon, double dt,
+                               const HydroBufs& b, DevStatus* st, int step, cudaStream_t s);
 
 // max over cells of sum_d (|v_d| + a)/dx_d as the bit pattern of a
 // non-negative double in *b.dt_bits (0 first); a nonphysical cell gives +inf.

@@ -138,6 +138,10 @@ SIGNATURES = {
                                       ctypes.POINTER(rhd_step_info)]),
     "rhd_step_slabs": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.POINTER(rhd_step_info)]),
+    "rhd_hydro_step_slabs": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.POINTER(rhd_step_info)]),
+    "rhd_step_split_slabs": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.POINTER(rhd_step_info)]),
     "rhd_step_noalloc": (ctypes.c_int, [_P, _V, _V, ctypes.c_double, _V,
                                         ctypes.POINTER(rhd_step_info)]),
     "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
@@ -476,18 +480,32 @@ def slab_problems(prob: dict, cuts) -> list:
     return out
 
 
-def step_slabs(contexts, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
-    """rhd_step_slabs: nsteps steps of the z-slabs (RHDContext, bottom to top)
-    of one grid, with the ghost planes exchanged before every stage."""
-    lib = load()
+def _slab_call(fn, contexts, nsteps, dt, raise_on_error):
     arr = (_V * len(contexts))(*[c.h.value for c in contexts])
     info = rhd_step_info()
-    st = lib.rhd_step_slabs(arr, len(contexts), int(nsteps), float(dt), ctypes.byref(info))
+    st = fn(arr, len(contexts), int(nsteps), float(dt), ctypes.byref(info))
     if raise_on_error:
         _check(st, contexts[0].h)
     d = info.as_dict()
     d["status"] = st
     return d
+
+
+def step_slabs(contexts, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
+    """rhd_step_slabs: nsteps radiation steps of the z-slabs (RHDContext,
+    bottom to top) of one grid, the ghost planes exchanged before every stage."""
+    return _slab_call(load().rhd_step_slabs, contexts, nsteps, dt, raise_on_error)
+
+
+def hydro_step_slabs(contexts, nsteps: int = 1, dt: float = 0.0, raise_on_error=True) -> dict:
+    """rhd_hydro_step_slabs: nsteps hydrodynamic steps of the z-slabs."""
+    return _slab_call(load().rhd_hydro_step_slabs, contexts, nsteps, dt, raise_on_error)
+
+
+def step_split_slabs(contexts, nsteps: int = 1, dt_h: float = 0.0,
+                     raise_on_error=True) -> dict:
+    """rhd_step_split_slabs: nsteps operator-split steps of the z-slabs."""
+    return _slab_call(load().rhd_step_split_slabs, contexts, nsteps, dt_h, raise_on_error)
 
 
 class RHDBatch:

@@ -151,3 +151,99 @@ def test_slab_arguments_are_checked(R):
     finally:
         for ctx in (a, b, c):
             ctx.close()
+
+
+def random_gas(prob, seed, mach=0.5, kappa=0.0):
+    rng = np.random.default_rng(seed)
+    sh = I.shape_of(prob)[1:]
+    rho = 1.0 + 0.3 * rng.uniform(-1, 1, sh)
+    p = 1.0 + 0.3 * rng.uniform(-1, 1, sh)
+    v = mach * rng.uniform(-1, 1, (3,) + sh)
+    return I.gas_state(prob, rho, v, p, kappa=kappa)
+
+
+def run_slabs(R, prob, U, cuts, call):
+    """call(contexts) on the slabs of cuts; returns (state, info, times)."""
+    stream = torch.cuda.current_stream()
+    ctxs = [R.RHDContext(q, stream=stream) for q in R.slab_problems(prob, cuts)]
+    try:
+        for c, z0, z1 in zip(ctxs, cuts, cuts[1:]):
+            c.set_state(np.ascontiguousarray(U[:, z0:z1]))
+        info = call(ctxs)
+        return (np.concatenate([c.get_state() for c in ctxs], axis=1), info,
+                [c.time() for c in ctxs])
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+HYDRO_CASES = [
+    # n, cuts, reconstruction, bc
+    ((12, 10, 15), [0, 5, 10, 15], "plm", "periodic"),
+    ((12, 10, 15), [0, 3, 15], "ppm", "reflect"),
+    ((9, 11, 12), [0, 4, 8, 12], "ppm_cs", "periodic"),
+]
+
+
+@pytest.mark.parametrize("ci", range(len(HYDRO_CASES)), ids=[str(c) for c in HYDRO_CASES])
+def test_hydro_on_slabs_steps_like_the_whole_grid(R, ci):
+    """Five fixed steps, then two at the CFL step of the whole grid: every
+    field bit-identical, the same CFL step."""
+    n, cuts, rec, bc = HYDRO_CASES[ci]
+    prob = I.base_problem(3, list(n), [1.0 / v for v in n], gamma=1.4, reconstruction=rec,
+                          bc=bc)
+    U = random_gas(prob, 60 + ci)
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        dt = ctx.hydro_dt()
+        ctx.hydro_step(5, dt)
+        iw = ctx.hydro_step(2)
+        Uw = ctx.get_state()
+        tw = ctx.time()
+
+    def call(ctxs):
+        R.hydro_step_slabs(ctxs, 5, dt)
+        return R.hydro_step_slabs(ctxs, 2)
+    Us, info, times = run_slabs(R, prob, U, cuts, call)
+    assert info["steps_done"] == 2 and info["dt"] == iw["dt"]
+    assert all(t == tw for t in times)
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), (HYDRO_CASES[ci], f)
+
+
+@pytest.mark.parametrize("rec,hll", [("plm", "tau"), ("ppm", "none")])
+def test_split_on_slabs_steps_like_the_whole_grid(R, rec, hll):
+    """Two operator-split steps of a coupled gas (c = 3 chat, tau_cell ~ 0.1-1):
+    the hydrodynamic step with its CFL step, then the radiation subcycles,
+    on three slabs and on the whole grid."""
+    n = (12, 10, 12)
+    prob = I.base_problem(3, list(n), [1.0 / v for v in n], gamma=5 / 3, c=30.0, chat=10.0,
+                          reconstruction=rec, hll_mode=hll)
+    U = random_gas(prob, 95, mach=0.3, kappa=2.0)
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        iw = ctx.step_split(2)
+        Uw = ctx.get_state()
+    Us, info, _ = run_slabs(R, prob, U, [0, 4, 7, 12], lambda c: R.step_split_slabs(c, 2))
+    for k in ("steps_done", "n_solves", "sum_newton", "sum_outer", "dt"):
+        assert info[k] == iw[k], k
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), f
+
+
+def test_hydro_failure_on_slabs_leaves_every_slab(R):
+    """A step far beyond the CFL bound: nonphysical, no slab committed."""
+    n = (12, 10, 12)
+    prob = I.base_problem(3, list(n), [1.0 / v for v in n], gamma=1.4)
+    U = random_gas(prob, 7, mach=0.9)
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        dt = 40.0 * ctx.hydro_dt()
+        iw = ctx.hydro_step(3, dt, raise_on_error=False)
+    assert iw["status"] == R.RHD_ERR_NONPHYSICAL
+    Us, info, times = run_slabs(
+        R, prob, U, [0, 6, 12], lambda c: R.hydro_step_slabs(c, 3, dt, raise_on_error=False))
+    for k in ("status", "steps_done", "fail_step"):
+        assert info[k] == iw[k], k
+    assert info["fail_stage"] in (3, 4) and np.array_equal(Us, U)
+    assert all(t == 0.0 for t in times)
