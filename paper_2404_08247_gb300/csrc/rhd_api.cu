@@ -885,9 +885,19 @@ rhd_status rhd_adjoint(rhd_ctx* c, const double* tape, int64_t count, int nsteps
   if (!std::isfinite(dt)) return fail(c, RHD_ERR_ARG, "dt is not finite");
   if (nsteps == 0) return RHD_OK;
   CUDA_TRY(c, cudaSetDevice(c->device));
-  if (!c->adj_q) {
+  if (!c->adj_q || !c->adj_fp) {
+    // both or neither: a failed second allocation releases the first
+    cudaFree(c->adj_q);
+    c->adj_q = nullptr;
     CUDA_TRY(c, cudaMalloc(&c->adj_q, sizeof(double) * S));
-    CUDA_TRY(c, cudaMalloc(&c->adj_fp, sizeof(double) * adjoint_scratch_doubles(c->g)));
+    cudaError_t e = cudaMalloc(&c->adj_fp, sizeof(double) * adjoint_scratch_doubles(c->g));
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // clear the allocation error for later launch checks
+      c->adj_fp = nullptr;
+      cudaFree(c->adj_q);
+      c->adj_q = nullptr;
+      return fail(c, RHD_ERR_CUDA, "adjoint scratch: %s", cudaGetErrorString(e));
+    }
   }
   CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
   AdjointStep A;
@@ -940,13 +950,24 @@ static rhd_status hydro_ready(rhd_ctx* c) {
 // the hydrodynamic scratch of a context, allocated once
 static rhd_status hydro_alloc(rhd_ctx* c) {
   CUDA_TRY(c, cudaSetDevice(c->device));
-  if (!c->hyd_w) {
-    const size_t N = (size_t)c->ncell;
-    CUDA_TRY(c, cudaMalloc(&c->hyd_w, sizeof(double) * 5 * N));
-    CUDA_TRY(c, cudaMalloc(&c->hyd_u1, sizeof(double) * 5 * N));
-    for (int d = 0; d < c->p.ndim; ++d)
-      CUDA_TRY(c, cudaMalloc(&c->hyd_f[d], sizeof(double) * 5 * hydro_faces(c->g, d)));
-    CUDA_TRY(c, cudaMalloc(&c->hyd_bits, sizeof(unsigned long long)));
+  if (c->hyd_bits) return RHD_OK;  // allocated last: every buffer is there
+  const size_t N = (size_t)c->ncell;
+  double** bufs[5] = {&c->hyd_w, &c->hyd_u1, &c->hyd_f[0], &c->hyd_f[1], &c->hyd_f[2]};
+  size_t bytes[5] = {sizeof(double) * 5 * N, sizeof(double) * 5 * N, 0, 0, 0};
+  for (int d = 0; d < c->p.ndim; ++d) bytes[2 + d] = sizeof(double) * 5 * hydro_faces(c->g, d);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+    if (bytes[i] && !*bufs[i]) e = cudaMalloc(bufs[i], bytes[i]);
+  if (e == cudaSuccess) e = cudaMalloc(&c->hyd_bits, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the allocation error for later launch checks
+    // none or all: release what this call could not complete
+    for (int i = 0; i < 5; ++i) {
+      cudaFree(*bufs[i]);
+      *bufs[i] = nullptr;
+    }
+    c->hyd_bits = nullptr;
+    return fail(c, RHD_ERR_CUDA, "hydrodynamic scratch: %s", cudaGetErrorString(e));
   }
   return RHD_OK;
 }
@@ -1215,8 +1236,11 @@ static rhd_status slab_radiation(rhd_ctx* const* slabs, int nslab, int nsteps, d
   for (int s = 0; s < nslab; ++s)
     if (!slabs[s]->halo) {
       cudaError_t e = cudaMalloc(&slabs[s]->halo, sizeof(double) * kHaloSlots * P);
-      if (e != cudaSuccess)
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        slabs[s]->halo = nullptr;
         return fail(c0, RHD_ERR_CUDA, "slab %d: halo buffers: %s", s, cudaGetErrorString(e));
+      }
     }
   auto hk = [&](rhd_ctx* c) { return c->halo + (size_t)8 * HALO_PLANES * P; };
   auto hr = [&](rhd_ctx* c) { return hk(c) + P; };
@@ -1356,8 +1380,11 @@ static rhd_status check_slabs_hydro(rhd_ctx* const* slabs, int nslab) {
     if (!slabs[s]->hyd_halo) {
       cudaError_t e =
           cudaMalloc(&slabs[s]->hyd_halo, sizeof(double) * 2 * 5 * HALO_PLANES * P);
-      if (e != cudaSuccess)
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        slabs[s]->hyd_halo = nullptr;
         return fail(c0, RHD_ERR_CUDA, "slab %d: halo buffers: %s", s, cudaGetErrorString(e));
+      }
     }
   return RHD_OK;
 }
