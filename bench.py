@@ -83,6 +83,8 @@ def parse(argv=None):
     ap.add_argument("--adj-n", type=int, default=512)
     ap.add_argument("--no-split", action="store_true",
                     help="skip the hydrodynamic step and the operator-split step")
+    ap.add_argument("--no-slabs", action="store_true",
+                    help="skip the step of the box as two z-slabs")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the 512-problem batched workload (for profiling); "
                          "prints its own JSON line")
@@ -503,6 +505,46 @@ def run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier):
     }
 
 
+def run_slabs(args, rhd, torch, prob, U, ws, dist, barrier, whole_ms):
+    """The same box as two z-slabs on this GPU (the domain decomposition a
+    multi-GPU run uses; the ghost planes exchanged by device-to-device copies
+    before each stage): warm-up, then args.steps steps of rhd_step_slabs
+    timed with CUDA events on the stream."""
+    stream = torch.cuda.current_stream()
+    nz = prob["n"][2]
+    cuts = [0, nz // 2, nz]
+    ctxs = [rhd.RHDContext(q, args.precision, stream=stream)
+            for q in rhd.slab_problems(prob, cuts)]
+    try:
+        for c, z0, z1 in zip(ctxs, cuts, cuts[1:]):
+            c.set_state(np.ascontiguousarray(U[:, z0:z1]))
+        rhd.step_slabs(ctxs, args.warmup)
+        barrier()
+        torch.cuda.synchronize()
+        l0 = sum(c.launch_count() for c in ctxs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rhd.step_slabs(ctxs, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = sum(c.launch_count() for c in ctxs) - l0
+        ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    finally:
+        for c in ctxs:
+            c.close()
+    N = int(np.prod(prob["n"]))
+    P = prob["n"][0] * prob["n"][1]
+    depth = 2 if prob.get("reconstruction", "plm") == "plm" else 3
+    return {"value": whole_job_rate(N, args.steps, ws, ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "slabs": cuts,
+            "whole_over_slabs_time": whole_ms / ms,
+            "exchange_bytes_per_step": 2 * 2 * 2 * 4 * depth * P * 8,
+            "gpu_launches": launches,
+            "note": "two z-slabs of the box, periodic in z (each slab's two faces are "
+                    "HALO); per stage 16 device-to-device copies of the neighbours' "
+                    "boundary planes; the TAU factors are recomputed once per call"}
+
+
 def run_hydro_only(args):
     """2 + 3 hydrodynamic steps of the --n^3 box at its CFL step; one line."""
     import torch
@@ -665,6 +707,10 @@ def run_ours(args):
                                      zip(("set_state", "step", "get_state"), parts)}}
     ctx.close()
 
+    slabs = None
+    if not args.no_slabs and prob["ndim"] == 3 and prob["n"][2] >= 6:
+        slabs = run_slabs(args, rhd, torch, prob, U, ws, dist, barrier, ms)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(args, rhd, torch, rank, ws, dist, barrier)
@@ -711,6 +757,7 @@ def run_ours(args):
             "batched": batched,
             "adjoint": adjoint,
             "hydro_split": split,
+            "slabs": slabs,
         }
         print(json.dumps(line))
     if dist is not None:
