@@ -105,8 +105,9 @@ def test_inflow_and_reflecting_end_faces(R):
 
 def test_a_failure_stops_every_slab(R):
     """A step far beyond the transport's CFL bound drives E negative: the
-    slabs report the whole grid's failing step, stage and smallest cell, and
-    every slab keeps the state of the last step all of them completed."""
+    slabs report the whole grid's failing step and stage and a cell of the
+    whole grid, and every slab keeps the state of the last step all of them
+    completed."""
     prob, U, _ = I.turbulent_box_3d(shape=(24, 20, 18), hll_mode="none")
     dt = 60.0 * R.rhd_default_dt(R.params_from_problem(prob))
     Uw, iw = whole(R, prob, U, 2, dt, "fp64")
