@@ -87,6 +87,24 @@ def test_slabs_step_like_the_whole_grid(R, ci):
         assert info[k] == iw[k], k
 
 
+def test_colella_sekora_faces_on_slabs(R):
+    """PPM with the Colella-Sekora limiter (its second differences reach two
+    cells beyond the face) on three slabs, FP64 and mixed, on a state whose
+    temperatures vary smoothly enough for the limiter (iid within 30 %)."""
+    shape = (14, 12, 15)
+    prob = I.base_problem(3, list(shape), [1 / 14] * 3, c=30.0, chat=10.0,
+                          reconstruction="ppm_cs", hll_mode="tau")
+    U = I.random_state(prob, 31, tau_range=(1e-2, 10.0), T_range=(1.0, 1.3))
+    dt = R.rhd_default_dt(R.params_from_problem(prob))
+    for precision in ("fp64", "mixed"):
+        Uw, iw = whole(R, prob, U, 3, dt, precision)
+        assert iw["status"] == R.RHD_OK
+        Us, infos, _ = slabs(R, prob, U, [0, 3, 9, 15], 3, dt, precision)
+        assert infos[0]["status"] == R.RHD_OK
+        for f in range(I.NFIELD):
+            assert np.array_equal(Us[f], Uw[f]), (precision, f)
+
+
 def test_inflow_and_reflecting_end_faces(R):
     """The outer z faces keep their own kind (an inflow source below, a wall
     above); the interior faces are HALO."""
@@ -228,6 +246,33 @@ def test_split_on_slabs_steps_like_the_whole_grid(R, rec, hll):
     Us, info, _ = run_slabs(R, prob, U, [0, 4, 7, 12], lambda c: R.step_split_slabs(c, 2))
     for k in ("steps_done", "n_solves", "sum_newton", "sum_outer", "dt"):
         assert info[k] == iw[k], k
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), f
+
+
+def test_split_on_slabs_in_mixed_precision(R):
+    """A mixed-precision split on slabs: the radiation update in the mixed
+    form, the hydrodynamic step in FP64, as on the whole grid."""
+    n = (10, 12, 12)
+    prob = I.base_problem(3, list(n), [1.0 / v for v in n], gamma=5 / 3, c=30.0, chat=10.0,
+                          reconstruction="ppm", hll_mode="tau",
+                          bc=[["periodic"] * 2, ["periodic"] * 2, ["reflect"] * 2])
+    U = random_gas(prob, 97, mach=0.3, kappa=2.0)
+    with R.RHDContext(prob, "mixed") as ctx:
+        ctx.set_state(U)
+        ctx.step_split(2)
+        Uw = ctx.get_state()
+    stream = torch.cuda.current_stream()
+    cuts = [0, 5, 12]
+    ctxs = [R.RHDContext(q, "mixed", stream=stream) for q in R.slab_problems(prob, cuts)]
+    try:
+        for c, z0, z1 in zip(ctxs, cuts, cuts[1:]):
+            c.set_state(np.ascontiguousarray(U[:, z0:z1]))
+        R.step_split_slabs(ctxs, 2)
+        Us = np.concatenate([c.get_state() for c in ctxs], axis=1)
+    finally:
+        for c in ctxs:
+            c.close()
     for f in range(I.NFIELD):
         assert np.array_equal(Us[f], Uw[f]), f
 
