@@ -344,9 +344,10 @@ rhd_status rhd_step_split(rhd_ctx* ctx, int nsteps, double dt_h, rhd_step_info* 
  * face, device to device (the calls a multi-GPU run would replace by
  * point-to-point sends); TAU-mode face factors at the slab faces are
  * computed from the neighbour's rho and kappa at the start of every call
- * (one TAU-factor kernel per slab).  Failure: all slabs stay at the last step that every slab
- * completed; info (nullable) reports as rhd_step with fail_cell counted in
- * the whole grid (cell index of slab s plus the cells of the slabs below).
+ * (one TAU-factor kernel per slab).  Failure: all slabs stay at the last
+ * step that every slab completed; info (nullable) reports as rhd_step with
+ * fail_cell counted in the whole grid (cell index of slab s plus the cells
+ * of the slabs below).
  * The first call allocates 27 * n[0] * n[1] doubles per slab.  A context
  * with a HALO face is refused (RHD_ERR_STATE) by every other stepping call
  * (rhd_step, rhd_step_async, rhd_transport, rhd_step_record, rhd_adjoint,
