@@ -355,6 +355,101 @@ def test_tau_correction_limits(oracle_mod):
     assert e["tau"] < e["none"]
 
 
+def _jump_face_energy_flux(O, mode, chi_l, chi_r, dx, axis=0, ndim=1,
+                           dxs=None, chat=3.0):
+    """Energy flux through the one face where E jumps, F = 0 everywhere.
+
+    E is E_L on the first half of the axis and E_R on the second; the MC
+    limiter gives zero slopes next to a step (one of its two differences is
+    zero), so both face states are the cell values, F = 0 gives D = I/3 and
+    S_R = -S_L = chat/sqrt(3), and the HLL energy flux of Sec. 4.3 is its
+    dissipative term alone: eps S_R S_L (E_R - E_L)/(S_R - S_L).  The face
+    above the first E_R cell sees uniform data and carries no energy flux,
+    so that cell's rate is the jump face's flux divided by dx.  chi is
+    chi_l on the left half and chi_r on the right (rho = 1)."""
+    n_ax = 8
+    n = [1, 1, 1]
+    n[axis] = n_ax
+    if dxs is None:
+        dxs = [dx] * 3
+    dxs = list(dxs)
+    dxs[axis] = dx
+    prob = I.base_problem(ndim, n[:ndim], dxs[:ndim], c=10.0, chat=chat,
+                          hll_mode=mode)
+    sh = (n[2], n[1], n[0])
+    U = I.equilibrium_state(prob, np.ones(sh), np.ones(sh),
+                            np.zeros((3,) + sh), np.ones(sh))
+    E_l, E_r = 1.0, 5.0
+    idx = [slice(None)] * 3
+    half = [slice(None)] * 3
+    half[2 - axis] = slice(0, n_ax // 2)
+    U[I.F_ERAD] = E_r
+    U[(I.F_ERAD,) + tuple(half)] = E_l
+    U[I.F_KAPPA] = chi_r
+    U[(I.F_KAPPA,) + tuple(half)] = chi_l
+    for d in range(3):
+        U[I.F_FX + d] = 0.0
+    rate = O.transport(prob, U)[0]
+    idx[2 - axis] = n_ax // 2
+    j = tuple(i if isinstance(i, int) else 0 for i in idx)
+    flux = rate[j] * dx            # rate = -(0 - flux)/dx
+    # the NONE flux of this face, from the formula (eps = 1)
+    none = -chat / np.sqrt(3.0) * (E_r - E_l) / 2.0
+    return flux, none
+
+
+def test_tau_factor_thin_and_thick_limits(oracle_mod):
+    """Sec. 4.3: the factor on the energy-flux dissipation goes to 1 in thin
+    faces and to 1/tau in thick ones, tau the face's optical depth.  With the
+    face's dissipative term isolated, tau * eps -> 1 for tau >> 1 and
+    eps -> 1 for tau << 1; doubling chi on both sides of a thick face halves
+    the term.  NONE carries exactly the formula's flux."""
+    O = oracle_mod
+    dx = 1.0 / 8
+    f_none, ref = _jump_face_energy_flux(O, "none", 400.0, 400.0, dx)
+    assert abs(f_none / ref - 1.0) < 1e-14
+    for chi in (200.0, 800.0, 8e4):           # tau = chi dx = 25 .. 1e4
+        tau = chi * dx
+        f_tau, ref = _jump_face_energy_flux(O, "tau", chi, chi, dx)
+        assert abs(f_tau * tau / ref - 1.0) < 1e-3, (chi, f_tau * tau / ref)
+        f_2, _ = _jump_face_energy_flux(O, "tau", 2 * chi, 2 * chi, dx)
+        assert abs(f_2 / f_tau - 0.5) < 1e-3
+    for chi in (8e-6, 8e-8):                  # tau = 1e-6, 1e-8
+        f_tau, ref = _jump_face_energy_flux(O, "tau", chi, chi, dx)
+        assert abs(f_tau / ref - 1.0) < 2 * chi * dx
+    # between the limits eps falls monotonically from 1 towards 1/tau
+    epss = [_jump_face_energy_flux(O, "tau", t / dx, t / dx, dx)[0] / ref
+            for t in (1e-3, 0.1, 1.0, 3.0, 10.0)]
+    assert all(0 < b < a <= 1 for a, b in zip(epss, epss[1:]))
+
+
+def test_tau_factor_face_optical_depth(oracle_mod):
+    """The face's optical depth is the mean of its two cells' chi times the
+    cell width along the face normal, tau = (chi_L + chi_R) dx_d / 2: with a
+    contrast chi_L != chi_R a thick face's term is 1/tau of NONE's for that
+    tau (a one-sided chi, a dropped 1/2 or a dropped dx each miss it by a
+    factor >= 1.5), halving dx at fixed chi halves tau, and in 3-D each
+    axis takes its own dx."""
+    O = oracle_mod
+    dx = 1.0 / 8
+    for chi_l, chi_r in ((400.0, 1200.0), (1200.0, 400.0), (100.0, 2900.0)):
+        tau = 0.5 * (chi_l + chi_r) * dx
+        f_tau, ref = _jump_face_energy_flux(O, "tau", chi_l, chi_r, dx)
+        assert abs(f_tau * tau / ref - 1.0) < 1e-3, (chi_l, chi_r, f_tau * tau / ref)
+    chi = 800.0
+    f1, ref = _jump_face_energy_flux(O, "tau", chi, chi, dx)
+    f2, ref2 = _jump_face_energy_flux(O, "tau", chi, chi, dx / 2)
+    assert ref == ref2
+    assert abs(f2 / f1 - 2.0) < 2e-3          # eps = 1/tau doubles
+    dxs = [1.0 / 8, 1.0 / 32, 1.0 / 128]
+    for axis in range(3):
+        chi_l, chi_r = 3000.0, 9000.0
+        tau = 0.5 * (chi_l + chi_r) * dxs[axis]
+        f_tau, ref = _jump_face_energy_flux(O, "tau", chi_l, chi_r, dxs[axis],
+                                            axis=axis, ndim=3, dxs=dxs)
+        assert abs(f_tau * tau / ref - 1.0) < 1e-3, (axis, f_tau * tau / ref)
+
+
 # ------------------------------ P6: uniform advecting medium (Sec. 5.5, Table 1)
 
 def _uniform(order, beta, closure="m1", tau_cell=1e3, c=1e3, ratio=1.0):
