@@ -417,7 +417,7 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
       if (!(T > 0.0) || !isfinite(T) || !isfinite(R)) return ORC_ERR_NONPHYSICAL;
       double aT4 = a * T * T * T * T; /* 4 pi B / c */
       /* eq. (G0): chi_0E = chi, chi_0P = rP chi, chi_0F = rF chi, all at the
-       * current temperature and held fixed in the Jacobian below */
+       * current temperature (their ratios are constant) */
       double chiE = chi_at(p, chi0, T), chiP = rP * chiE, chiF = rF * chiE;
       /* E as a function of (Egas, R): eq. (Rnew) solved for E, with
        * P = D E; order 1 keeps the O(v/c) terms only */
@@ -431,10 +431,20 @@ int orc_local_solve(const orc_params* p, double theta, double dt, double rho,
         break;
       }
       if (it >= p->newton_max_iter) break;
-      /* Jacobian of eq. (linear), the paper's simplified form */
+      /* Jacobian of eq. (linear), the paper's simplified form (v^2/c^2 terms
+       * dropped, chiP/chiE constant) */
       double J00 = 1.0;
       double J01 = c / chat;
       double J10 = (chiP / chiE) * 4.0 * a * T * T * T / Cv; /* (1/C_v) d(chiP/chiE aT^4)/dT */
+      /* reading: with chi = chi0 (T/T_ref)^p the -R/(chat theta dt den) term
+       * of E(Egas, R) above depends on T through den (proportional to
+       * chi_0E), which adds p R/(T chat theta dt den) to dE/dT.  The printed
+       * J10 is dE/dEgas at constant chi; Sec. 3.3 notes that the Jacobian
+       * sets only the rate of convergence, not the converged solution, and
+       * with the exact term the iteration converges quadratically instead of
+       * linearly. */
+      if (p->kappa_T_exp != 0.0)
+        J10 += p->kappa_T_exp * R / (T * chat * tdt * den) / Cv;
       double J11 = -1.0 / (chat * chiE * tdt) - 1.0;
       double det = J00 * J11 - J01 * J10;
       double dEg = (-FG * J11 + FR * J01) / det;

@@ -433,6 +433,92 @@ __device__ __forceinline__ bool hll_states(int d, R L[4], R Rr[4], R eps, R chat
   return true;
 }
 
+// Mixed precision: row d of the deviation P - (E/3) I of the closure tensor,
+// in single precision.  From the form above, P - (E/3) I =
+// (3 Ft Ft^T - |Ft|^2 I)/(2E + s) below the free-streaming limit (E n n - E/3 I
+// above it; zero for the Eddington closure).  It is O(|Ft|^2/E), so its
+// single-precision rounding is small next to the flux, where a rounded P_dd
+// ~ E/3 would carry an error of an ulp of E/3 into every face.
+__device__ __forceinline__ void m1_dev_row(int d, float E, const float Ft[3], int closure,
+                                           float D[3]) {
+  D[0] = D[1] = D[2] = 0.f;
+  if (closure == RHD_CLOSURE_EDDINGTON) return;
+  const float F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
+  const float E2 = E * E;
+  float hb, ha;
+  if (F2 > E2) {
+    hb = E / F2;
+    ha = -E * (1.f / 3.f);
+  } else {
+    const float s = sqrtf(4.f * E2 - 3.f * F2);
+    const float w = 1.f / (2.f * E + s);
+    hb = 3.f * w;
+    ha = -F2 * w;
+  }
+  const float t = hb * Ft[d];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) D[j] = t * Ft[j];
+  D[d] += ha;
+}
+
+// HLL flux of hll_states in mixed precision.  The isotropic part of the
+// normal momentum flux, hc (E_L + E_R)/3 (hc = chat/2), is linear in the face
+// states: it is returned in double (iso, from the exact single-precision face
+// energies and chat6 = chat/6 in double) and left out of out[1 + d], which
+// carries the single-precision rest.  The flux of F along d is out[1 + d] +
+// iso.  Rounding P_dd in single precision at every face gives each face an
+// independent error of an ulp of E/3, which the flux difference turns into
+// an error of the flux update of order 1e-7 E/|Ft| relative; near isotropy
+// (|Ft| << E) that is the dominant single-precision error.
+__device__ __forceinline__ bool hll_states_mixed(int d, float L[4], float Rr[4], float eps,
+                                                 float chat, int closure, double chat6,
+                                                 float out[4], double& iso) {
+  iso = 0.0;
+  if (!(L[0] > 0.f) || !(Rr[0] > 0.f)) {
+    out[0] = out[1] = out[2] = out[3] = 0.f;
+    return false;
+  }
+  {
+    float n2 = L[1] * L[1] + L[2] * L[2] + L[3] * L[3];
+    if (L[0] * L[0] < n2) {
+      const float sc = L[0] / sqrtf(n2);
+      L[1] *= sc; L[2] *= sc; L[3] *= sc;
+    }
+    n2 = Rr[1] * Rr[1] + Rr[2] * Rr[2] + Rr[3] * Rr[3];
+    if (Rr[0] * Rr[0] < n2) {
+      const float sc = Rr[0] / sqrtf(n2);
+      Rr[1] *= sc; Rr[2] *= sc; Rr[3] *= sc;
+    }
+  }
+  float DL[3], DR[3];
+  m1_dev_row(d, L[0], &L[1], closure, DL);
+  m1_dev_row(d, Rr[0], &Rr[1], closure, DR);
+  // D_dd = 1/3 + dev/E: the larger side and the 1/3 floor by the deviations
+  float num = DL[d], den = L[0];
+  if (DL[d] * Rr[0] < DR[d] * L[0]) { num = DR[d]; den = Rr[0]; }
+  const float S = num > 0.f ? chat * sqrtf(1.f / 3.f + num / den) : chat * sqrtf(1.f / 3.f);
+  const float hc = 0.5f * chat;
+  const float hS = 0.5f * S;
+  out[0] = hc * (L[1 + d] + Rr[1 + d]) - eps * hS * (Rr[0] - L[0]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) out[1 + j] = hc * (DL[j] + DR[j]) - hS * (Rr[1 + j] - L[1 + j]);
+  iso = chat6 * ((double)L[0] + (double)Rr[0]);
+  return true;
+}
+
+// The face flux in the transport precision R: hll_states for double (iso =
+// 0, unused), hll_states_mixed for float.
+template <typename R>
+__device__ __forceinline__ bool face_hll(int d, R L[4], R Rr[4], R eps, R chat, int closure,
+                                         double chat6, R out[4], double& iso) {
+  if constexpr (sizeof(R) == 8) {
+    iso = 0.0;
+    return hll_states<R>(d, L, Rr, eps, chat, closure, out);
+  } else {
+    return hll_states_mixed(d, L, Rr, eps, chat, closure, chat6, out, iso);
+  }
+}
+
 // Optical-depth factor of the HLL energy dissipation (reading of Sec. 4.3):
 // (1 - exp(-tau))/tau, 1 in the thin limit, 1/tau in the thick limit.
 __device__ __forceinline__ double tau_factor(double tau) {
@@ -480,7 +566,9 @@ __device__ __forceinline__ bool quartic_start(double a4, double rhs, double T0, 
 //   r1 = k g F_R = k g (aT^4 - E(t) - R) + k v.F/c^2 - R
 //   J  = [[1, c/chat], [g k 4 a T^3 / C_v, -g (1 + k)]]
 // converged when |r0| < eps E_tot and (c/chat)|r1| <= eps E_tot k g,
-// E_tot = Egas(t) + (c/chat) E(t).  The first pass starts from quartic_start.
+// E_tot = Egas(t) + (c/chat) E(t).  The first pass starts from quartic_start
+// (constant chi) or from (Egas(t), 0) (chi ~ T^p, whose J10 gains the term of
+// the T-dependence of k).
 // Energy closure: E = E(t) - (chat/c)(Egas - Egas(t)).
 // Outer stage: eq. (numF2) (order 2) or (numF1) (order 1) for F with P from
 // the new E and the previous outer flux, momentum m = m(t) - (F - F(t))/(c chat),
@@ -524,10 +612,14 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
   double w = (v[0] * F[0] + v[1] * F[1] + v[2] * F[2]) * ph.inv_c2;
   double Ekin = 0.5 * (m[0] * v[0] + m[1] * v[1] + m[2] * v[2]);
 
-  {
+  // With a temperature-dependent opacity the iteration starts from
+  // (Egas(t), 0) like the oracle's: the exact Jacobian below converges
+  // quadratically from there, and a common start keeps the two solves on
+  // the same iterates near a Marshak front, where the stopping point's
+  // rounding is amplified.
+  if (!vary) {
     double T0 = (Eg0 - Ekin) * inv_Cv;
     if (pos_finite(T0)) {
-      if (vary) k = k0 * pow(T0 * ph.inv_kappa_T_ref, ph.kappa_T_exp);
       double kg = k * g;
       double inv1 = rcp_pos(1.0 + kg);
       double a4 = cr * kg * a * inv1 * inv_Cv;
@@ -571,6 +663,10 @@ __device__ __forceinline__ int local_solve(const Physics& ph, double tdt, double
       }
       if (it >= ph.newton_max) break;
       double J10 = c4 * T2 * T;
+      // chi ~ T^p: the R/(k g) term of E(Egas, R) varies with T through k,
+      // which adds p R/(T C_v) to the scaled J10 (exact dE/dEgas; the
+      // paper's J10 holds chi fixed, Sec. 3.3, and converges linearly)
+      if (vary) J10 += ph.kappa_T_exp * R / (Eg - Ekin);
       double det = -gpk - cr * J10;  // < 0
       double inv_det = MIXED ? (double)(1.0f / (float)det) : -rcp_pos(-det);
       double dEg = (r0 * gpk + cr * r1) * inv_det;
@@ -706,7 +802,7 @@ __device__ int local_solve_nongrey(const Physics& ph, double tdt, double rho, do
   };
   auto kprime = [&]() { return kE * g - (o2 ? (kF - kE) * (beta2 + vDv) : 0.0); };
 
-  {  // start from the frozen-opacity quartic A T^4 + C_v T = C (see quartic_start)
+  if (!vary) {  // start from the frozen-opacity quartic A T^4 + C_v T = C (see quartic_start)
     const double T0 = (Eg0 - Ekin) * inv_Cv;
     if (pos_finite(T0)) {
       set_k(T0);
@@ -744,7 +840,8 @@ __device__ int local_solve_nongrey(const Physics& ph, double tdt, double rho, do
         break;
       }
       if (it >= ph.newton_max) break;
-      const double J10 = kp * rP * 4.0 * a * T2 * T * inv_Cv;
+      double J10 = kp * rP * 4.0 * a * T2 * T * inv_Cv;
+      if (vary) J10 += ph.kappa_T_exp * R / (Eg - Ekin);  // as in local_solve
       const double gpk = kp / kE + kp;
       const double det = -gpk - cr * J10;
       const double inv_det = MIXED ? (double)(1.0f / (float)det) : 1.0 / det;

@@ -67,7 +67,13 @@ struct SmemT {
   // PPM z march: each thread's carried right edge and interface value (kept
   // in shared memory: in registers they push the FP64 kernel past its budget)
   static constexpr int CZ = (T::PPM && T::NDIM == 3) ? 12 * T::NT : 0;
-  static constexpr size_t BYTES = sizeof(R) * (RING + FX + FY + CZ);
+  // mixed precision: the isotropic part of each x-/y-face's normal momentum
+  // flux in double (hll_states_mixed), after the R arrays (16-byte aligned)
+  static constexpr bool ISO = sizeof(R) == sizeof(float);
+  static constexpr int FXI = ISO ? T::TY * (T::TX + 1) : 0;
+  static constexpr int FYI = ISO && T::NDIM >= 2 ? (T::TY + 1) * T::TX : 0;
+  static constexpr size_t ISO_OFF = sizeof(R) * (RING + FX + FY + CZ);
+  static constexpr size_t BYTES = ISO_OFF + sizeof(double) * (FXI + FYI);
 };
 
 // Coordinate x >= -3 folded onto [0, n) by the boundary condition (padding
@@ -236,10 +242,11 @@ __device__ __forceinline__ void ppm_states(const R u[6][4], R L[4], R Rr[4], boo
 }
 
 // flux through the face between plane cells c - st and c (stride st); cs:
-// PPM tiles with the Colella-Sekora limiter
+// PPM tiles with the Colella-Sekora limiter; iso: see face_hll
 template <class T, typename R>
 __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R eps, R chat,
-                                           int closure, R out[4], bool cs = false) {
+                                           int closure, double chat6, R out[4], double& iso,
+                                           bool cs = false) {
   R L[4], Rr[4];
   if constexpr (T::PPM) {
     R u[6][4];
@@ -258,7 +265,7 @@ __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R 
       Rr[q] = b[q] - half_slope(a[q], b[q], bp[q]);
     }
   }
-  return hll_states<R>(d, L, Rr, eps, chat, closure, out);
+  return face_hll<R>(d, L, Rr, eps, chat, closure, chat6, out, iso);
 }
 
 // One cell (E, F/c) of the own column (cx, cy inside the grid) at plane zg,
@@ -321,10 +328,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   R* ring = reinterpret_cast<R*>(smem_raw);
   R* fxs = ring + S::RING;
   R* fys = fxs + S::FX;
+  double* fxi = reinterpret_cast<double*>(smem_raw + S::ISO_OFF);  // MIXED only
+  double* fyi = fxi + S::FXI;
 
   const Geometry& g = A.g;
   const Physics& ph = A.ph;
   const R chat = (R)ph.chat;
+  const double chat6 = ph.chat * (1.0 / 6.0);
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int ix = x0 + tx, iy = y0 + ty;
   const bool col = ix < g.n[0] && (NDIM < 2 || iy < g.n[1]);
@@ -336,6 +346,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   bool zbad = false;
 
   R zlo[4] = {R(0), R(0), R(0), R(0)};  // z-face flux below the current cell
+  double zlo_iso = 0.0;                 // its isotropic momentum part (MIXED)
   R hz[4] = {R(0), R(0), R(0), R(0)};   // half z-slope of the current cell (PLM)
   // PPM z march: the constrained right edge of the current cell and the
   // interface value above it, carried from plane to plane, so each plane
@@ -385,7 +396,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       }
     }
     R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
-    zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
+    zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zlo, zlo_iso);
     for (int o = 0; o <= 2; ++o)
       load_plane<T, R, GEN>(A, ring, ring_slot<T>(kbeg + o), kbeg + o, x0, y0);
   } else if constexpr (NDIM == 3) {
@@ -405,7 +416,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       Rr[q] = up[q] - hz[q];
     }
     R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
-    zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zlo);
+    zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zlo, zlo_iso);
     __syncthreads();  // plane kbeg-2's slot is reloaded by the first iteration
   }
 
@@ -422,6 +433,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 
     // ---- z-face k+1/2 of the own column
     R zhi[4] = {R(0), R(0), R(0), R(0)};
+    double zhi_iso = 0.0;
     R hz1[4] = {R(0), R(0), R(0), R(0)};
     if constexpr (NDIM == 3 && T::PPM) {
       // face k+1/2: the carried right edge of cell k | the left edge of
@@ -458,7 +470,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         }
       }
       R eps = (R)face_eps(A, 2, cx, cy, k);
-      zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
+      zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zhi, zhi_iso);
       bad = bad || zbad;
     } else if constexpr (NDIM == 3) {
       R u0[4], u1[4], u2[4];
@@ -473,7 +485,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         Rr[q] = u1[q] - hz1[q];
       }
       R eps = (R)face_eps(A, 2, cx, cy, k);
-      zbad = !hll_states<R>(2, L, Rr, eps, chat, ph.closure, zhi);
+      zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zhi, zhi_iso);
       bad = bad || zbad;
     }
 
@@ -486,13 +498,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       bool real = xl < g.n[0] && (NDIM < 2 || yr < g.n[1]);
       R eps = real ? (R)face_eps(A, 0, xl, yr, k) : R(1);
       R out[4];
-      if (!plane_face<T, R>(pl, c, 1, 0, eps, chat, ph.closure, out, cs) && real) {
+      double iso;
+      if (!plane_face<T, R>(pl, c, 1, 0, eps, chat, ph.closure, chat6, out, iso, cs) && real) {
         // a face with E <= 0 poisons both neighbours' fluxes
 #pragma unroll
         for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) fxs[q * TY * (TX + 1) + f] = out[q];
+      if constexpr (MIXED) fxi[f] = iso;
     }
     // ---- y-faces of plane k: face f lies between rows fj-1 and fj
     if (NDIM >= 2) {
@@ -503,12 +517,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         bool real = xr < g.n[0] && yl < g.n[1];
         R eps = real ? (R)face_eps(A, 1, xr, yl, k) : R(1);
         R out[4];
-        if (!plane_face<T, R>(pl, c, S::PW, 1, eps, chat, ph.closure, out, cs) && real) {
+        double iso;
+        if (!plane_face<T, R>(pl, c, S::PW, 1, eps, chat, ph.closure, chat6, out, iso, cs) &&
+            real) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) out[q] = (R)__longlong_as_double(0x7ff8000000000000ll);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) fys[q * (TY + 1) * TX + f] = out[q];
+        if constexpr (MIXED) fyi[f] = iso;
       }
     }
     __syncthreads();
@@ -522,20 +539,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const R* fq = fxs + q * TY * (TX + 1);
-        rate[q] = -((double)fq[fl + 1] - (double)fq[fl]) * g.inv_dx[0];
+        double df = (double)fq[fl + 1] - (double)fq[fl];
+        if (MIXED && q == 1) df += fxi[fl + 1] - fxi[fl];
+        rate[q] = -df * g.inv_dx[0];
       }
       if (NDIM >= 2) {
         const int fb = tx + ty * TX;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const R* fq = fys + q * (TY + 1) * TX;
-          rate[q] -= ((double)fq[fb + TX] - (double)fq[fb]) * g.inv_dx[1];
+          double df = (double)fq[fb + TX] - (double)fq[fb];
+          if (MIXED && q == 2) df += fyi[fb + TX] - fyi[fb];
+          rate[q] -= df * g.inv_dx[1];
         }
       }
       if (NDIM == 3) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          rate[q] -= ((double)zhi[q] - (double)zlo[q]) * g.inv_dx[2];
+        for (int q = 0; q < 4; ++q) {
+          double df = (double)zhi[q] - (double)zlo[q];
+          if (MIXED && q == 3) df += zhi_iso - zlo_iso;
+          rate[q] -= df * g.inv_dx[2];
+        }
       }
       bad = bad || !isfinite(rate[0]) || !isfinite(rate[1]) || !isfinite(rate[2]) ||
             !isfinite(rate[3]);
@@ -601,6 +625,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         zlo[q] = zhi[q];
         hz[q] = hz1[q];
       }
+      zlo_iso = zhi_iso;
     }
     __syncthreads();
   }

@@ -119,3 +119,27 @@ def test_autotuner_picks_and_caches(R, tmp_path):
     assert len(res["timings_ms"]) == len(autotune.CANDIDATES)
     again = autotune.tune(problems, "mixed", nsteps=2, cache_path=cache)
     assert again["cached"] and again["tile2d"] == res["tile2d"]
+
+
+def test_batch_mixed_workload_subset_matches_oracle(R, oracle_mod):
+    """The batched workload as the benchmark runs it (mixed precision, the
+    persistent graph-captured kernel): its first 16 problems (the generator
+    draws problems in sequence, so these are the 512-problem workload's
+    first 16: 1-D up to 4096 cells and 2-D up to 256^2, log10 tau_cell iid
+    U[-3, 3], |v|/c up to 1e-3) over 50 steps, each against the FP64 oracle
+    to the mixed-precision bound 1e-5 per field."""
+    problems = I.batched_problems(nprob=16, seed=11)
+    nsteps = 50
+    with R.RHDBatch([p for p, _ in problems], "mixed") as b:
+        for i, (_, U) in enumerate(problems):
+            b.set_state(i, U)
+        info = b.step(nsteps)
+        assert info["steps_done"] == nsteps
+        got = [b.get_state(i) for i in range(len(problems))]
+    worst = 0.0
+    for i, (p, U) in enumerate(problems):
+        Uo = U.copy()
+        oracle_mod.step(p, Uo, nsteps=nsteps)
+        errs = assert_parity(got[i], Uo, 1e-5, "problem %d (%s cells)" % (i, p["n"]))
+        worst = max(worst, max(errs.values()))
+    print("worst per-field error over the 16 problems: %.2e" % worst)

@@ -70,30 +70,20 @@ def test_mixed_static_diffusion_1d(R, oracle_mod):
 
 
 def test_mixed_regime_sweep_1d(R, oracle_mod):
-    """4096 cells, three optical-depth bands, chat = c/10.  Pointwise within
-    1e-5 for 1000 steps.  At the full 2000 steps the streaming front of the
-    thin band's pulse has crossed ~800 cells; single-precision rounding moves a
-    front by a minute fraction of a cell, which a pointwise relative metric
-    turns into ~2e-5 at the front cell, so there the bound is on the field
-    norm (L2 relative <= 1e-5) with the pointwise error reported."""
+    """4096 cells, three optical-depth bands, chat = c/10, the full 2000
+    steps (and 1000): every field pointwise within 1e-5 of the FP64 oracle.
+    Near isotropy (|F| ~ 1e-3 cE) the flux of F is dominated by P ~ E/3; the
+    mixed kernel carries that isotropic part in double (hll_states_mixed),
+    so single-precision rounding of P_dd at every face does not drive F."""
     prob, U, nsteps = I.regime_sweep_1d()
-    half = nsteps // 2
-    Ug, info, t0, t1 = run(R, prob, U, half, "mixed")
-    Uo = U.copy()
-    oracle_mod.step(prob, Uo, nsteps=half)
-    errs = field_errors(Ug, Uo)
-    assert max(errs.values()) <= TOL_MIXED, errs
-    check_conservation(prob, Ug, t0, t1)
-    Ug, info, t0, t1 = run(R, prob, U, nsteps, "mixed")
-    Uo = U.copy()
-    oracle_mod.step(prob, Uo, nsteps=nsteps)
-    for f in range(I.NFIELD):
-        a, b = Ug[f].ravel(), Uo[f].ravel()
-        nb = np.linalg.norm(b)
-        l2 = np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
-        assert l2 <= TOL_MIXED, (I.FIELDS[f], l2)
-    assert max(field_errors(Ug, Uo).values()) <= 1e-4
-    check_conservation(prob, Ug, t0, t1)
+    for n in (nsteps // 2, nsteps):
+        Ug, info, t0, t1 = run(R, prob, U, n, "mixed")
+        Uo = U.copy()
+        oracle_mod.step(prob, Uo, nsteps=n)
+        errs = field_errors(Ug, Uo)
+        print("regime sweep, %d steps:" % n, {k: "%.2e" % v for k, v in errs.items()})
+        assert max(errs.values()) <= TOL_MIXED, (n, errs)
+        check_conservation(prob, Ug, t0, t1)
 
 
 @pytest.mark.parametrize("var", range(3))

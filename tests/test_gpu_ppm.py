@@ -8,7 +8,8 @@ import pytest
 
 from paper_2404_08247_gb300 import inputs as I
 from parity import assert_parity, field_errors
-from test_gpu_schemes import inflow_bc, marshak_errors
+from parity import MARSHAK_CFL10_TOL, marshak_errors
+from test_gpu_schemes import inflow_bc
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -134,16 +135,19 @@ def test_ppm_refuses_a_negative_stage_state(R):
 def test_ppm_marshak_wave_matches_oracle(R, oracle_mod, cfl):
     """The asymptotic Marshak wave of Sec. 5.2 with the paper's PPM faces
     (60 cells, to 3e-9 s), with the metric of the PLM Marshak parity test:
-    E against the local E_tot to 1e-11, E_gas, m and F to 1e-8."""
+    E against the local E_tot to 1e-11, E_gas, m and F to 1e-11 at CFL 0.9
+    and to ten times the oracle's own rounding floor at CFL 10."""
     prob, U = I.marshak_wave_1d(60, scheme="imex", cfl=cfl, reconstruction="ppm")
     dt = oracle_mod.dt(prob)
     nsteps = int(round(3e-9 / dt))
+    tol = TOL if cfl < 1.0 else MARSHAK_CFL10_TOL["ppm"]
     for n in sorted({min(500, nsteps), nsteps}):
         Ug, _, _, _ = run_gpu(R, prob, U, n, dt)
         Uo = run_oracle(oracle_mod, prob, U, n, dt)
         e = marshak_errors(Ug, Uo)
+        print("ppm", cfl, n, e)
         assert e["erad_vs_etot"] <= TOL, (n, e)
-        assert max(e["egas"], e["mx"], e["fx"]) <= 1e-8, (n, e)
+        assert max(e["egas"], e["mx"], e["fx"]) <= tol, (n, e)
 
 
 def test_batch_with_ppm_problems_equals_single_grids(R):

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2404_08247_gb300 import inputs as I
-from parity import assert_parity
+from parity import MARSHAK_CFL10_TOL, assert_parity, marshak_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -120,20 +120,6 @@ def test_rk2ssp_solves_once_per_step(R):
     assert info["n_solves"] == 3 * 20 * 16
 
 
-def marshak_errors(G, Uo):
-    """E measured against the local E_tot = E_gas + (c/chat) E (chat = c here),
-    the scale of the Newton stopping test of Sec. 3.3; E_gas pointwise; m and
-    F against their largest value."""
-    eg, er = Uo[I.F_EGAS, 0, 0], Uo[I.F_ERAD, 0, 0]
-    etot = eg + er
-    return {
-        "erad_vs_etot": float(np.max(np.abs(G[I.F_ERAD, 0, 0] - er) / etot)),
-        "egas": float(np.max(np.abs(G[I.F_EGAS, 0, 0] - eg) / eg)),
-        "mx": float(np.max(np.abs(G[I.F_MX] - Uo[I.F_MX])) / np.max(np.abs(Uo[I.F_MX]))),
-        "fx": float(np.max(np.abs(G[I.F_FX] - Uo[I.F_FX])) / np.max(np.abs(Uo[I.F_FX]))),
-    }
-
-
 @pytest.mark.parametrize("scheme,cfl", [("imex", 0.9), ("rk2ssp", 0.9), ("imex", 10.0)])
 def test_marshak_wave_matches_oracle(R, oracle_mod, scheme, cfl):
     """The asymptotic Marshak wave (60 cells, chi ~ T^-3, 1 keV inflow face)
@@ -142,21 +128,24 @@ def test_marshak_wave_matches_oracle(R, oracle_mod, scheme, cfl):
 
     Ahead of the front E = a T^4 is 1e-10 of E_gas = C_v T, and the Newton
     stop of Sec. 3.3 (|F| < 1e-13 E_tot) fixes E there only to ~1e-13 E_tot:
-    E is compared against E_tot (1e-11).  At the front chi changes by nine
-    decades within a few cells; two correct solvers that stop anywhere inside
-    the tolerance (the oracle starts Newton at (E_gas, 0), the kernel at the
-    root of the frozen-opacity quartic) drift apart there by up to 5e-11 at
-    CFL 0.9 and 1.5e-9 at CFL 10 in E_gas (1e-12 at CFL 0.9 when the kernel
-    is started like the oracle): E_gas, m and F are compared to 1e-8."""
+    E is compared against E_tot (1e-11).  Kernel and oracle start Newton at
+    (E_gas, 0) and take dE/dE_gas with the T-dependence of chi, so both
+    converge quadratically to the same root: E_gas, m and F to 1e-11 at CFL
+    0.9.  At CFL 10 a cell heating through the front amplifies rounding
+    beyond 1e-11 (the oracle's own half-ulp-noise spread,
+    tests/test_oracle_schemes.py): there E_gas, m and F take ten times
+    that floor."""
     prob, U = I.marshak_wave_1d(60, scheme=scheme, cfl=cfl)
     dt = oracle_mod.dt(prob)
     nsteps = int(round(3e-9 / dt))
+    tol = TOL if cfl < 1.0 else MARSHAK_CFL10_TOL["plm"]
     for n in sorted({min(500, nsteps), min(2000, nsteps), nsteps}):
         Ug, _ = run_gpu(R, prob, U, n, dt)
         Uo = run_oracle(oracle_mod, prob, U, n, dt)
         e = marshak_errors(Ug, Uo)
+        print(scheme, cfl, n, e)
         assert e["erad_vs_etot"] <= TOL, (n, e)
-        assert max(e["egas"], e["mx"], e["fx"]) <= 1e-8, (n, e)
+        assert max(e["egas"], e["mx"], e["fx"]) <= tol, (n, e)
 
 
 def test_batch_with_schemes_and_inflow_equals_single_grids(R):
