@@ -14,6 +14,8 @@
 // plane; 1-D grids use rows of TX cells.
 #pragma once
 
+#include <type_traits>
+
 #include "rhd_internal.cuh"
 
 namespace rhd {
@@ -61,7 +63,11 @@ struct SmemT {
   static constexpr int PW = T::TX + 2 * T::HX;
   static constexpr int PH = T::TY + 2 * T::HY;
   static constexpr int PS = PW * PH;                   // cells per plane
-  static constexpr int RING = T::NPL * 4 * PS;         // doubles
+  // values per cell: E, Ft (FP64); mixed: their hi and lo single-precision
+  // parts, E_hi .. Fz_hi then E_lo .. Fz_lo (split_hilo)
+  static constexpr int NV = sizeof(R) == sizeof(float) ? 8 : 4;
+  static constexpr int PLANE = NV * PS;                // R values per ring plane
+  static constexpr int RING = T::NPL * PLANE;
   static constexpr int FX = 4 * T::TY * (T::TX + 1);   // x-face fluxes
   static constexpr int FY = T::NDIM >= 2 ? 4 * (T::TY + 1) * T::TX : 0;
   // PPM z march: each thread's carried right edge and interface value (kept
@@ -153,15 +159,35 @@ __device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, in
   return eps_direct(A, il, il + (xb - c[d]) * g.stride[d], d);
 }
 
+// Mixed precision: x as a pair of floats with hi + lo = x to 2^-47 |x|.  hi
+// is x with its mantissa cut to 24 bits (integer operations; exact in float
+// within the float exponent range), lo = x - hi rounded to float.  A
+// difference of two neighbours, (b_hi - a_hi) + (b_lo - a_lo), is then good
+// to single precision of the difference itself, where the difference of the
+// rounded values would carry an error of an ulp of the values: the MC slopes
+// and face states of the mixed transport are formed that way.
+__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e >= 1023 - 126 && e <= 1023 + 127) {
+    const double xt = __longlong_as_double(b & ~((1ll << 29) - 1));
+    hi = __uint_as_float((unsigned)((b >> 32) & 0x80000000ll) |
+                         ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+    lo = (float)(x - xt);
+  } else {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  }
+}
+
 // load plane zg (global z, may be a ghost plane) into ring slot `slot`,
-// converting to the transport precision R
+// converting to the transport precision R (mixed: hi/lo pairs)
 template <class T, typename R, bool GEN>
 __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot, int zg,
                                            int x0, int y0) {
   constexpr int NDIM = T::NDIM;
   using S = SmemT<T, R>;
   const Geometry& g = A.g;
-  const R inv_c = (R)A.ph.inv_c;
   bool fz = false;
   int zf = NDIM == 3 ? fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz, T::HX - 1) : 0;
   const int zin = GEN && NDIM == 3 ? inflow_side(g, 2, zg) : -1;
@@ -170,26 +196,29 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
   const double* hp = hs >= 0 ? halo_plane(A, hs, zg) : nullptr;
   const size_t hq = (size_t)HALO_PLANES * g.n[0] * g.n[1];
   if (hs >= 0) fz = false;
-  R* pl = ring + slot * 4 * S::PS;
+  R* pl = ring + slot * S::PLANE;
   for (int c = threadIdx.x; c < S::PS; c += T::TX * T::TY) {
     int ii = c % S::PW, jj = c / S::PW;
     bool fx = false, fy = false;
     int xf = fold(x0 + ii - T::HX, g.n[0], g.bc[0][0], g.bc[0][1], fx, T::HX - 1);
     int yf = NDIM >= 2 ? fold(y0 + jj - T::HY, g.n[1], g.bc[1][0], g.bc[1][1], fy, T::HX - 1)
                        : 0;
-    R E, Fx, Fy, Fz;
+    // the values in double (mixed: split into hi/lo pairs below); F/c is
+    // rounded explicitly, like column_cell's
+    const double wic = A.ph.inv_c;
+    double E, Fx, Fy, Fz;
     if (hs >= 0) {
       const int pidx = xf + g.n[0] * yf;
-      E = (R)__ldg(hp + pidx);
-      Fx = (R)__ldg(hp + hq + pidx) * inv_c;
-      Fy = (R)__ldg(hp + 2 * hq + pidx) * inv_c;
-      Fz = (R)__ldg(hp + 3 * hq + pidx) * inv_c;
+      E = __ldg(hp + pidx);
+      Fx = __dmul_rn(__ldg(hp + hq + pidx), wic);
+      Fy = __dmul_rn(__ldg(hp + 2 * hq + pidx), wic);
+      Fz = __dmul_rn(__ldg(hp + 3 * hq + pidx), wic);
     } else {
       int idx = xf + g.n[0] * (yf + g.n[1] * zf);
-      E = (R)__ldg(A.yt[Y_ERAD] + idx);
-      Fx = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
-      Fy = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
-      Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
+      E = __ldg(A.yt[Y_ERAD] + idx);
+      Fx = __dmul_rn(__ldg(A.yt[Y_FX] + idx), wic);
+      Fy = __dmul_rn(__ldg(A.yt[Y_FY] + idx), wic);
+      Fz = __dmul_rn(__ldg(A.yt[Y_FZ] + idx), wic);
     }
     Fx = fx ? -Fx : Fx;
     Fy = fy ? -Fy : Fy;
@@ -206,15 +235,26 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
     }
     if (ax >= 0) {
       const double* st = g.bc_state[ax][side];
-      E = (R)st[0];
-      Fx = (R)(st[1] * A.ph.inv_c);
-      Fy = (R)(st[2] * A.ph.inv_c);
-      Fz = (R)(st[3] * A.ph.inv_c);
+      E = st[0];
+      Fx = __dmul_rn(st[1], wic);
+      Fy = __dmul_rn(st[2], wic);
+      Fz = __dmul_rn(st[3], wic);
     }
-    pl[0 * S::PS + c] = E;
-    pl[1 * S::PS + c] = Fx;
-    pl[2 * S::PS + c] = Fy;
-    pl[3 * S::PS + c] = Fz;
+    if constexpr (S::NV == 8) {
+      const double v[4] = {E, Fx, Fy, Fz};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float hi, lo;
+        split_hilo(v[q], hi, lo);
+        pl[q * S::PS + c] = hi;
+        pl[(4 + q) * S::PS + c] = lo;
+      }
+    } else {
+      pl[0 * S::PS + c] = (R)E;
+      pl[1 * S::PS + c] = (R)Fx;
+      pl[2 * S::PS + c] = (R)Fy;
+      pl[3 * S::PS + c] = (R)Fz;
+    }
   }
 }
 
@@ -223,6 +263,29 @@ __device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
   using S = SmemT<T, R>;
 #pragma unroll
   for (int q = 0; q < 4; ++q) u[q] = pl[q * S::PS + c];
+}
+
+// mixed: the hi/lo parts of cell c of a ring plane
+template <class T>
+__device__ __forceinline__ void cell_hl(const float* pl, int c, float hi[4], float lo[4]) {
+  using S = SmemT<T, float>;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hi[q] = pl[q * S::PS + c];
+    lo[q] = pl[(4 + q) * S::PS + c];
+  }
+}
+
+// difference b - a of two hi/lo values
+__device__ __forceinline__ float diff_hl(float bh, float bl, float ah, float al) {
+  return (bh - ah) + (bl - al);
+}
+
+// half of the MC-limited slope from the differences dm = u0 - um, dp = up - u0
+// (the limiter of half_slope)
+__device__ __forceinline__ float half_slope_d(float dm, float dp) {
+  const float m = fminf(fminf(fabsf(dm), fabsf(dp)), 0.25f * fabsf(dm + dp));
+  return (dm > 0.f && dp > 0.f) ? m : ((dm < 0.f && dp < 0.f) ? -m : 0.f);
 }
 
 // PPM states of the face between cells u[2] and u[3] of the six cells u
@@ -253,6 +316,21 @@ __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R 
 #pragma unroll
     for (int o = 0; o < 6; ++o) cell_of<T, R>(pl, c + (o - 3) * st, u[o]);
     ppm_states(u, L, Rr, cs);
+  } else if constexpr (sizeof(R) == sizeof(float)) {
+    // face states from the hi/lo differences of the four cells
+    float hm[4], lm[4], ha[4], la[4], hb[4], lb[4], hp[4], lp[4];
+    cell_hl<T>(pl, c - 2 * st, hm, lm);
+    cell_hl<T>(pl, c - st, ha, la);
+    cell_hl<T>(pl, c, hb, lb);
+    cell_hl<T>(pl, c + st, hp, lp);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float d0 = diff_hl(ha[q], la[q], hm[q], lm[q]);
+      const float d1 = diff_hl(hb[q], lb[q], ha[q], la[q]);
+      const float d2 = diff_hl(hp[q], lp[q], hb[q], lb[q]);
+      L[q] = ha[q] + (la[q] + half_slope_d(d0, d1));
+      Rr[q] = hb[q] + (lb[q] - half_slope_d(d1, d2));
+    }
   } else {
     R am[4], a[4], b[4], bp[4];
     cell_of<T, R>(pl, c - 2 * st, am);
@@ -274,33 +352,48 @@ __device__ __forceinline__ bool plane_face(const R* pl, int c, int st, int d, R 
 template <class T, typename R, bool GEN>
 __device__ __forceinline__ void column_cell(const StageArgs& A, int cx, int cy, int zg,
                                             R u[4]) {
+  // the values load_plane puts in the ring: double, or the hi part of a
+  // mixed-precision hi/lo pair (a face shared by two z-chunks is then
+  // computed from the same inputs by both, and the flux telescopes); the
+  // products F/c are rounded explicitly, as the ring's stores round them,
+  // so that no contraction into a later operation can make them differ
   const Geometry& g = A.g;
-  const R inv_c = (R)A.ph.inv_c;
+  const double inv_c = A.ph.inv_c;
   bool fz = false;
   const int zf = fold(zg, g.n[2], g.bc[2][0], g.bc[2][1], fz, T::HX - 1);
   const int hs = halo_side(g, zg);
+  double w[4];
   if (hs >= 0) {
     const double* hp = halo_plane(A, hs, zg) + cx + g.n[0] * cy;
     const size_t hq = (size_t)HALO_PLANES * g.n[0] * g.n[1];
-    u[0] = (R)__ldg(hp);
-    u[1] = (R)__ldg(hp + hq) * inv_c;
-    u[2] = (R)__ldg(hp + 2 * hq) * inv_c;
-    u[3] = (R)__ldg(hp + 3 * hq) * inv_c;
+    w[0] = __ldg(hp);
+    w[1] = __dmul_rn(__ldg(hp + hq), inv_c);
+    w[2] = __dmul_rn(__ldg(hp + 2 * hq), inv_c);
+    w[3] = __dmul_rn(__ldg(hp + 3 * hq), inv_c);
   } else {
     const int idx = cx + g.n[0] * (cy + g.n[1] * zf);
-    u[0] = (R)__ldg(A.yt[Y_ERAD] + idx);
-    u[1] = (R)__ldg(A.yt[Y_FX] + idx) * inv_c;
-    u[2] = (R)__ldg(A.yt[Y_FY] + idx) * inv_c;
-    const R Fz = (R)__ldg(A.yt[Y_FZ] + idx) * inv_c;
-    u[3] = fz ? -Fz : Fz;
+    w[0] = __ldg(A.yt[Y_ERAD] + idx);
+    w[1] = __dmul_rn(__ldg(A.yt[Y_FX] + idx), inv_c);
+    w[2] = __dmul_rn(__ldg(A.yt[Y_FY] + idx), inv_c);
+    const double Fz = __dmul_rn(__ldg(A.yt[Y_FZ] + idx), inv_c);
+    w[3] = fz ? -Fz : Fz;
   }
   const int side = GEN ? inflow_side(g, 2, zg) : -1;
   if (side >= 0) {
     const double* st = g.bc_state[2][side];
-    u[0] = (R)st[0];
-    u[1] = (R)(st[1] * A.ph.inv_c);
-    u[2] = (R)(st[2] * A.ph.inv_c);
-    u[3] = (R)(st[3] * A.ph.inv_c);
+    w[0] = st[0];
+    w[1] = __dmul_rn(st[1], inv_c);
+    w[2] = __dmul_rn(st[2], inv_c);
+    w[3] = __dmul_rn(st[3], inv_c);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if constexpr (sizeof(R) == sizeof(float)) {
+      float lo;
+      split_hilo(w[q], u[q], lo);
+    } else {
+      u[q] = w[q];
+    }
   }
 }
 
@@ -403,17 +496,34 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
     for (int o = -2; o <= 1; ++o)
       load_plane<T, R, GEN>(A, ring, (kbeg + o) & 3, kbeg + o, x0, y0);
     __syncthreads();
-    R um[4], u0[4], up[4], upp[4];
-    cell_of<T, R>(ring + ((kbeg - 2) & 3) * 4 * S::PS, own, um);
-    cell_of<T, R>(ring + ((kbeg - 1) & 3) * 4 * S::PS, own, u0);
-    cell_of<T, R>(ring + ((kbeg + 0) & 3) * 4 * S::PS, own, up);
-    cell_of<T, R>(ring + ((kbeg + 1) & 3) * 4 * S::PS, own, upp);
     R L[4], Rr[4];
+    if constexpr (MIXED) {
+      float hm[4], lm[4], h0[4], l0[4], hp[4], lp[4], hpp[4], lpp[4];
+      cell_hl<T>(ring + ((kbeg - 2) & 3) * S::PLANE, own, hm, lm);
+      cell_hl<T>(ring + ((kbeg - 1) & 3) * S::PLANE, own, h0, l0);
+      cell_hl<T>(ring + ((kbeg + 0) & 3) * S::PLANE, own, hp, lp);
+      cell_hl<T>(ring + ((kbeg + 1) & 3) * S::PLANE, own, hpp, lpp);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      hz[q] = half_slope(u0[q], up[q], upp[q]);
-      L[q] = u0[q] + half_slope(um[q], u0[q], up[q]);
-      Rr[q] = up[q] - hz[q];
+      for (int q = 0; q < 4; ++q) {
+        const float d0 = diff_hl(h0[q], l0[q], hm[q], lm[q]);
+        const float d1 = diff_hl(hp[q], lp[q], h0[q], l0[q]);
+        const float d2 = diff_hl(hpp[q], lpp[q], hp[q], lp[q]);
+        hz[q] = half_slope_d(d1, d2);
+        L[q] = h0[q] + (l0[q] + half_slope_d(d0, d1));
+        Rr[q] = hp[q] + (lp[q] - hz[q]);
+      }
+    } else {
+      R um[4], u0[4], up[4], upp[4];
+      cell_of<T, R>(ring + ((kbeg - 2) & 3) * S::PLANE, own, um);
+      cell_of<T, R>(ring + ((kbeg - 1) & 3) * S::PLANE, own, u0);
+      cell_of<T, R>(ring + ((kbeg + 0) & 3) * S::PLANE, own, up);
+      cell_of<T, R>(ring + ((kbeg + 1) & 3) * S::PLANE, own, upp);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        hz[q] = half_slope(u0[q], up[q], upp[q]);
+        L[q] = u0[q] + half_slope(um[q], u0[q], up[q]);
+        Rr[q] = up[q] - hz[q];
+      }
     }
     R eps = (R)face_eps(A, 2, cx, cy, kbeg - 1);
     zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zlo, zlo_iso);
@@ -428,7 +538,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       load_plane<T, R, GEN>(A, ring, 0, 0, x0, y0);
     }
     __syncthreads();
-    const R* pl = ring + (NDIM == 3 ? ring_slot<T>(k) : 0) * 4 * S::PS;
+    const R* pl = ring + (NDIM == 3 ? ring_slot<T>(k) : 0) * S::PLANE;
     bool bad = zbad;
 
     // ---- z-face k+1/2 of the own column
@@ -440,9 +550,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       // cell k+1, whose edges come from a(k+1/2) and a new a(k+3/2)
       R v0[4], v1[4], v2[4], v3[4];
       cell_of<T, R>(pl, own, v0);
-      cell_of<T, R>(ring + ring_slot<T>(k + 1) * 4 * S::PS, own, v1);
-      cell_of<T, R>(ring + ring_slot<T>(k + 2) * 4 * S::PS, own, v2);
-      cell_of<T, R>(ring + ring_slot<T>(k + 3) * 4 * S::PS, own, v3);
+      cell_of<T, R>(ring + ring_slot<T>(k + 1) * S::PLANE, own, v1);
+      cell_of<T, R>(ring + ring_slot<T>(k + 2) * S::PLANE, own, v2);
+      cell_of<T, R>(ring + ring_slot<T>(k + 3) * S::PLANE, own, v3);
       R L[4], Rr[4];
       if (cs) {
         // the cell k+1 needs the second difference of cell k, carried
@@ -473,16 +583,30 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zhi, zhi_iso);
       bad = bad || zbad;
     } else if constexpr (NDIM == 3) {
-      R u0[4], u1[4], u2[4];
-      cell_of<T, R>(pl, own, u0);
-      cell_of<T, R>(ring + ((k + 1) & 3) * 4 * S::PS, own, u1);
-      cell_of<T, R>(ring + ((k + 2) & 3) * 4 * S::PS, own, u2);
       R L[4], Rr[4];
+      if constexpr (MIXED) {
+        float h0[4], l0[4], h1[4], l1[4], h2[4], l2[4];
+        cell_hl<T>(pl, own, h0, l0);
+        cell_hl<T>(ring + ((k + 1) & 3) * S::PLANE, own, h1, l1);
+        cell_hl<T>(ring + ((k + 2) & 3) * S::PLANE, own, h2, l2);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        hz1[q] = half_slope(u0[q], u1[q], u2[q]);
-        L[q] = u0[q] + hz[q];
-        Rr[q] = u1[q] - hz1[q];
+        for (int q = 0; q < 4; ++q) {
+          hz1[q] = half_slope_d(diff_hl(h1[q], l1[q], h0[q], l0[q]),
+                                diff_hl(h2[q], l2[q], h1[q], l1[q]));
+          L[q] = h0[q] + (l0[q] + hz[q]);
+          Rr[q] = h1[q] + (l1[q] - hz1[q]);
+        }
+      } else {
+        R u0[4], u1[4], u2[4];
+        cell_of<T, R>(pl, own, u0);
+        cell_of<T, R>(ring + ((k + 1) & 3) * S::PLANE, own, u1);
+        cell_of<T, R>(ring + ((k + 2) & 3) * S::PLANE, own, u2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          hz1[q] = half_slope(u0[q], u1[q], u2[q]);
+          L[q] = u0[q] + hz[q];
+          Rr[q] = u1[q] - hz1[q];
+        }
       }
       R eps = (R)face_eps(A, 2, cx, cy, k);
       zbad = !face_hll<R>(2, L, Rr, eps, chat, ph.closure, chat6, zhi, zhi_iso);
