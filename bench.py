@@ -13,13 +13,18 @@ stages of one step.  Default run: one GPU, FP64, HLL TAU mode.
 * e2e: the same metric through the public API with host buffers: every step
   copies the full input state from pinned host memory, runs one step and
   reads the full state back (wall clock, synchronised).
-* roofline: the dominant kernel's algorithmic HBM bytes per launch divided by
-  its mean event-timed duration inside the timed region, against the measured
-  copy bandwidth.
-* cpu_baseline: the CPU oracle (serial C, one core) on a bounded sample: a
-  periodic sub-box of the same initial state with the same dt.
+* roofline: the dominant stage kernel is bound by the FP64 pipe: its FP64
+  flops per launch (ncu thread counts per cell, profiles/kernel_counts.json,
+  times the cells) over its mean event-timed duration inside the timed
+  region, against the FP64 multiply-add throughput measured on this GPU by
+  the library's probe (rhd_fma_probe); the HBM view beside it.  Every form
+  (mixed, PPM, batched, adjoint) carries the same views, mixed precision also
+  the FP32 pipe's.
+* cpu_baseline: the CPU oracle (serial C) on every host core at once: one
+  oracle process per core, each on its own periodic sub-box of the same
+  initial state with the same dt; the one-core rate beside it.
 * --impl reference: the CPU oracle is the reference arm; each step is one
-  oracle step on a sub-box of the workload.
+  oracle step on a sub-box of the workload per host core, all at once.
 * Several GPUs (torchrun): every rank advances its own independent box (weak
   scaling, no data-path collective); value = all ranks' cell-updates / the
   slowest rank's time.
@@ -71,7 +76,9 @@ def parse(argv=None):
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=96,
-                    help="edge of the oracle's sub-box for cpu_baseline")
+                    help="edge of the oracle's sub-box for the one-core cpu_baseline")
+    ap.add_argument("--cpu-edge", type=int, default=64,
+                    help="edge of each host core's sub-box for the all-cores cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=48,
                     help="edge of the oracle's sub-box per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -88,6 +95,9 @@ def parse(argv=None):
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the 512-problem batched workload (for profiling); "
                          "prints its own JSON line")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="batched workload: enqueue the launches instead of replaying a "
+                         "CUDA graph (for profilers that do not see graph nodes)")
     ap.add_argument("--hydro-only", action="store_true",
                     help="time only the hydrodynamic step on the --n^3 box (for "
                          "profiling); prints its own JSON line")
@@ -105,12 +115,13 @@ def dist_env():
     return ws, rank, local
 
 
-def stage_traffic_record():
-    """DRAM bytes per cell of the stage kernels from the committed ncu summary
-    (profiles/stage_kernel_traffic.json), or None if the kernel sources have
-    changed since that capture."""
+def kernel_counts_record():
+    """Per-cell ncu counts (FP64/FP32 flops, DRAM bytes, pipe utilisation) of
+    the stage, batch and adjoint kernels from the committed summary
+    (profiles/kernel_counts.json), or None if the kernel sources have changed
+    since those captures."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", "kernel_counts.json")
     try:
         rec = json.load(open(path))
         h = hashlib.sha256()
@@ -119,6 +130,67 @@ def stage_traffic_record():
         return rec if h.hexdigest()[:16] == rec["sources_sha256_16"] else None
     except (OSError, ValueError, KeyError):
         return None
+
+
+def measure_fma_peaks(rhd, torch):
+    """FP64 and FP32 multiply-add throughput of this GPU in TFLOP/s: the
+    library's probe (rhd_fma_probe, 8 independent chains per thread, 8 blocks
+    of 256 threads per SM), best of 5 CUDA-event-timed launches after one
+    warm-up."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    stream = torch.cuda.current_stream()
+    out = {"method": "rhd_fma_probe: %d blocks x 256 threads x 8 independent FMA chains, "
+                     "best of 5 event-timed launches" % (8 * sms), "sms": sms}
+    for prec, iters in (("fp64", 2048), ("fp32", 32768)):
+        best = 0.0
+        for rep in range(6):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flops = rhd.fma_probe(prec, 8 * sms, iters, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[prec + "_tflops"] = best
+    return out
+
+
+def pipe_views(rec, n_cells, ms_per_launch, peaks, hbm_peak, alg_bytes):
+    """Roofline views of one launch over n_cells cells lasting ms_per_launch:
+    FP64 flops (and FP32 flops where the kernel has them) per cell from the
+    counts record against the measured pipe peaks, algorithmic bytes against
+    the copy bandwidth, and the DRAM traffic per launch."""
+    sec = ms_per_launch * 1e-3
+    v = {"hbm": {"achieved": alg_bytes * n_cells / sec / 1e9, "peak": hbm_peak,
+                 "unit": "GB/s", "frac": alg_bytes * n_cells / sec / 1e9 / hbm_peak,
+                 "alg_bytes_per_cell": alg_bytes}}
+    if rec is None:
+        return v
+    f64 = rec["fp64_flop"] * n_cells / sec / 1e12
+    v["fp64"] = {"achieved": f64, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                 "frac": f64 / peaks["fp64_tflops"], "flop_per_cell": rec["fp64_flop"]}
+    if rec.get("fp32_flop", 0.0) > 1.0:
+        f32 = rec["fp32_flop"] * n_cells / sec / 1e12
+        v["fp32"] = {"achieved": f32, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": f32 / peaks["fp32_tflops"], "flop_per_cell": rec["fp32_flop"]}
+    v["traffic_per_launch"] = rec["dram_bytes"] * n_cells
+    v["dram_bytes_per_cell"] = rec["dram_bytes"]
+    return v
+
+
+def step_record(rec):
+    """Counts of one whole step from per-stage counts (stage1 + stage2)."""
+    if rec is None:
+        return None
+    return {k: rec["stage1"][k] + rec["stage2"][k] for k in ("fp64_flop", "fp32_flop",
+                                                             "dram_bytes")}
+
+
+# algorithmic HBM bytes per cell of one adjoint step: the tape's y(n) and
+# y(n+1/2) (16 fields) and rho, kappa read; the cotangent of the state (8
+# fields) read and written; the opacity cotangent read and written
+ADJ_ALG_BYTES = 8 * (16 + 2 + 16 + 2)
 
 
 def measured_peaks():
@@ -208,6 +280,58 @@ def oracle_rate(prob, U, edge, nsteps, dt):
     return edge ** 3 * nsteps / (t1 - t0) / 1e6, t1 - t0
 
 
+def _oracle_ready(_):
+    """Pool warm-up: import and build the oracle in the worker process."""
+    from oracle import oracle as O
+    O.build()
+    O.lib()
+    time.sleep(0.3)  # so that every worker takes one warm-up task
+    return os.getpid()
+
+
+def _oracle_box(payload):
+    """One worker's timed oracle steps on its sub-box: (cell-updates, seconds)."""
+    prob, box, nsteps, dt = payload
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.step(prob, box, nsteps=nsteps, dt=dt)
+    return box[0].size * nsteps, time.perf_counter() - t0
+
+
+class OraclePool:
+    """The serial CPU oracle on every host core at once: one process per core
+    (spawned, so it is safe after CUDA initialisation), each advancing its
+    own periodic edge^3 sub-box of the workload, taken at a different offset."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_ready, range(self.cores), chunksize=1)
+
+    def boxes(self, prob, U, edge):
+        sub = dict(prob)
+        sub["n"] = [edge, edge, edge]
+        n = U.shape[1]
+        out = []
+        for i in range(self.cores):
+            o = (i * edge) % max(n - edge + 1, 1)
+            out.append((sub, np.ascontiguousarray(U[:, o:o + edge, :edge, :edge])))
+        return out
+
+    def rate(self, prob, U, edge, nsteps, dt):
+        """Mcell-updates/s of all processes together over the wall time."""
+        payloads = [(p, b.copy(), nsteps, dt) for p, b in self.boxes(prob, U, edge)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_box, payloads, chunksize=1)
+        t1 = time.perf_counter()
+        return sum(c for c, _ in res) / (t1 - t0) / 1e6, t1 - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def workload(args, rank=0):
     from paper_2404_08247_gb300 import inputs as I
     prob, U, _ = I.turbulent_box_3d(n=args.n, seed_rho=3 + 100 * rank,
@@ -244,24 +368,29 @@ def run_reference(args):
     prob, U = workload(args)
     dt = O.dt(prob)
     edge = args.ref_sample
-    for _ in range(args.warmup):
-        oracle_rate(prob, U, edge, 1, dt)
-    t = 0.0
-    for _ in range(args.steps):
-        _, dtime = oracle_rate(prob, U, edge, 1, dt)
-        t += dtime
-    cells = edge ** 3 * args.steps
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.rate(prob, U, edge, 1, dt)
+        t = 0.0
+        for _ in range(args.steps):
+            _, dtime = pool.rate(prob, U, edge, 1, dt)
+            t += dtime
+    finally:
+        pool.close()
+    cells = edge ** 3 * args.steps * pool.cores
     value = cells / t / 1e6
-    sample = "each step: one oracle step on a periodic %d^3 sub-box of the %d^3 state" % (
-        edge, args.n)
+    sample = ("each step: one oracle step on each of %d periodic %d^3 sub-boxes of the "
+              "%d^3 state, one serial oracle process per host core, all at once"
+              % (pool.cores, edge, args.n))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args, prob),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -301,7 +430,7 @@ def time_form(args, rhd, torch, prob, Ud, precision, barrier, stream, local):
                  "clocks": clk, "info": info}
 
 
-def run_batched(args, rhd, torch, rank, ws, dist, barrier):
+def run_batched(args, rhd, torch, rank, ws, dist, barrier, roof=None):
     """512 independent 1-D/2-D problems (mixed precision) in the persistent,
     graph-captured kernel; launch configuration from the autotuner."""
     from paper_2404_08247_gb300 import autotune
@@ -312,6 +441,8 @@ def run_batched(args, rhd, torch, rank, ws, dist, barrier):
     probs = [p for p, _ in problems]
     with rhd.RHDBatch(probs, "mixed", stream=stream) as b:
         b.configure(tuned["tile2d"], tuned["blocks_per_sm"])
+        if args.no_graph:
+            b.use_graphs(False)
         for i, (_, U) in enumerate(problems):
             b.set_state(i, U)
         cells = b.cells()
@@ -325,7 +456,16 @@ def run_batched(args, rhd, torch, rank, ws, dist, barrier):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    views = None
+    if roof is not None:
+        rec = roof["counts"]["batched"] if roof["counts"] else None
+        views = pipe_views(step_record(rec), cells, ms / args.steps, roof["peaks"],
+                           roof["hbm"], ALG_BYTES[0] + ALG_BYTES[1])
+        views["note"] = ("one whole step (both stage launches) of the pooled cells; "
+                         "flops per cell from ncu counts of the batch kernel's graph "
+                         "nodes on this workload (profiles/kernel_counts.json)")
     return {"value": whole_job_rate(cells, args.steps, ws, ms * 1e-3), "unit": UNIT,
+            "roofline": views,
             "ms_per_step": ms / args.steps, "steps": args.steps, "problems": len(probs),
             "cells": int(cells), "precision": "mixed",
             "n_1d": sum(1 for p in probs if p["ndim"] == 1),
@@ -337,7 +477,7 @@ def run_batched(args, rhd, torch, rank, ws, dist, barrier):
                         "c=1e3, chat=100 (seed 11)"}
 
 
-def run_adjoint(args, rhd, torch, rank, ws, dist, barrier):
+def run_adjoint(args, rhd, torch, rank, ws, dist, barrier, roof=None):
     """Differentiation workload: a radiation pulse through a log-normal opacity
     field on a periodic 512^2 grid, L = sum (E(200) - E_tgt)^2, gradient with
     respect to the initial temperature and log opacity by the hand-written
@@ -418,7 +558,15 @@ def run_adjoint(args, rhd, torch, rank, ws, dist, barrier):
     adj_ms = e0.elapsed_time(e1) / every
     launches = ctx.launch_count()
     ctx.close()
+    views = None
+    if roof is not None:
+        rec = roof["counts"]["adjoint"]["per_step"] if roof["counts"] else None
+        views = pipe_views(rec, N, adj_ms, roof["peaks"], roof["hbm"], ADJ_ALG_BYTES)
+        views["note"] = ("the four adjoint kernels of one step (face_vjp_kernel and "
+                         "cell_adj_kernel, both stages) against their event time; "
+                         "counts from profiles/kernel_counts.json")
     return {
+        "roofline": views,
         "value": whole_job_rate(N, nsteps, ws, bwd_ms * nsteps * 1e-3), "unit": UNIT,
         "what": "backward cell-updates/s (re-run with recording + adjoint)",
         "fwd_ms_per_step": fwd_ms, "bwd_ms_per_step": bwd_ms,
@@ -595,6 +743,9 @@ def run_ours(args):
     def max_over_ranks(x):
         return reduce_max(x, dist, "cuda")
 
+    # pipe peaks of this GPU (outside any timed region)
+    fma_peaks = measure_fma_peaks(rhd, torch)
+
     forms = [args.precision] + [f for f in ("fp64", "mixed") if f != args.precision
                                 and not args.single_form]
     if not args.single_form:
@@ -624,43 +775,43 @@ def run_ours(args):
     ms = head["ms"]
     value = whole_job_rate(N, args.steps, ws, ms * 1e-3)
 
-    # dominant kernel roofline: the FP64 pipe (its bound) when the committed
-    # ncu counts belong to these kernel sources, with the HBM view beside it
-    peaks, peak_src = measured_peaks()
+    # dominant kernel roofline: the FP64 pipe (its bound), from the committed
+    # ncu counts when they belong to these kernel sources, against the FP64
+    # peak measured above; the HBM view beside it
+    peaks_file, peak_src = measured_peaks()
+    hbm_peak = float(peaks_file.get("hbm_gbs", FALLBACK_HBM_GBS))
+    counts = kernel_counts_record()
     kms, klaunch = head["kms"], head["klaunch"]
     dom = max((0, 1), key=lambda k: kms[k])
-    avg_ms = kms[dom] / max(klaunch[dom], 1)
-    hbm_achieved = ALG_BYTES[dom] * N / (avg_ms * 1e-3) / 1e9
-    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    rec = stage_traffic_record() if args.precision == "fp64" else None
     kname = KERNEL_NAMES[dom]
-    traffic = rec["dram_bytes_per_cell"][kname] * N if rec else None
-    hbm_view = {
-        "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-        "frac": hbm_achieved / hbm_peak, "alg_bytes_per_cell": ALG_BYTES[dom],
-        "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
-        if peak_src == "measured" else "fallback",
-    }
+    avg_ms = kms[dom] / max(klaunch[dom], 1)
+    head_form = args.precision if args.reconstruction == "plm" else \
+        "%s-%s" % (args.precision, args.reconstruction)
+    head_rec = None
+    if counts and head_form in counts["stage_kernels"]:
+        head_rec = counts["stage_kernels"][head_form][kname]
+    views = pipe_views(head_rec, N, avg_ms, fma_peaks, hbm_peak, ALG_BYTES[dom])
+    hbm_view = dict(views["hbm"], peak_source="%s (MEASURED_PEAKS.json hbm_gbs)" % peak_src
+                    if peak_src == "measured" else "fallback")
     common = {
-        "kernel": kname, "traffic": traffic,
-        "traffic_source": ("ncu dram__bytes_read+write per cell at 128^3 x cells "
-                           "(profiles/stage_kernel_traffic.json)") if rec else None,
-        "fp64_pipe_busy": ({"while_active": rec["fp64_pipe_busy_active"][kname],
-                            "of_elapsed_128": rec["fp64_pipe_busy_elapsed"][kname]}
-                           if rec else None),
-        "avg_launch_ms": avg_ms,
+        "kernel": kname, "avg_launch_ms": avg_ms,
         "kernel_ms": {KERNEL_NAMES[k]: kms[k] / max(klaunch[k], 1) for k in (0, 1)},
+        "traffic": views.get("traffic_per_launch"),
+        "traffic_source": ("ncu dram__bytes_read+write per cell at 128^3 x cells "
+                           "(profiles/kernel_counts.json)") if head_rec else None,
+        "fp64_pipe_busy": ({"while_active": head_rec["fp64_pipe_active"],
+                            "of_elapsed_128": head_rec["fp64_pipe_elapsed"],
+                            "lanes_per_inst": head_rec["lanes"]} if head_rec else None),
     }
-    if rec and "fp64_flop_per_cell" in rec:
-        flops = rec["fp64_flop_per_cell"][kname]
-        achieved = flops * N / (avg_ms * 1e-3) / 1e12
+    if "fp64" in views and args.precision == "fp64":
         roofline = dict(
-            {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-             "flop_per_cell": flops,
+            {"bound": "alu", "achieved": views["fp64"]["achieved"],
+             "peak": fma_peaks["fp64_tflops"], "unit": "TFLOP/s",
+             "frac": views["fp64"]["frac"], "flop_per_cell": head_rec["fp64_flop"],
              "flop_source": "ncu thread counts dadd + dmul + 2 dfma per cell at 128^3 "
-                            "(profiles/stage_kernel_traffic.json) x cells",
-             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
+                            "(profiles/kernel_counts.json) x cells",
+             "peak_source": "measured on this GPU: " + fma_peaks["method"],
+             "peak_nominal": FP64_PEAK_TFLOPS,
              "hbm_view": hbm_view,
              "note": "FP64-pipe bound: the fraction of the FP64 flop peak also loses "
                      "the lanes idle in the per-cell iterations and the FP64-pipe "
@@ -668,11 +819,12 @@ def run_ours(args):
             **common)
     else:
         roofline = dict(
-            {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-             "frac": hbm_achieved / hbm_peak, "alg_bytes_per_cell": ALG_BYTES[dom],
-             "peak_source": hbm_view["peak_source"],
-             "note": "the stage kernels are bound by the FP64 pipe (ncu: 85 % busy while "
-                     "active), not by HBM; see profiles/stage_kernel_fp64_turbulent_box.md"},
+            {"bound": "hbm", "achieved": views["hbm"]["achieved"], "peak": hbm_peak,
+             "unit": "GB/s", "frac": views["hbm"]["frac"],
+             "alg_bytes_per_cell": ALG_BYTES[dom], "peak_source": hbm_view["peak_source"],
+             "pipe_views": {k: views[k] for k in ("fp64", "fp32") if k in views},
+             "note": "the stage kernels are bound by the FP64 pipe, not by HBM; see "
+                     "profiles/stage_kernel_fp64_turbulent_box.md"},
             **common)
 
     # end to end through the public API with pinned host buffers
@@ -711,13 +863,14 @@ def run_ours(args):
     if not args.no_slabs and prob["ndim"] == 3 and prob["n"][2] >= 6:
         slabs = run_slabs(args, rhd, torch, prob, U, ws, dist, barrier, ms)
 
+    roof = {"counts": counts, "peaks": fma_peaks, "hbm": hbm_peak}
     batched = None
     if not args.no_batched:
-        batched = run_batched(args, rhd, torch, rank, ws, dist, barrier)
+        batched = run_batched(args, rhd, torch, rank, ws, dist, barrier, roof)
 
     adjoint = None
     if not args.no_adjoint:
-        adjoint = run_adjoint(args, rhd, torch, rank, ws, dist, barrier)
+        adjoint = run_adjoint(args, rhd, torch, rank, ws, dist, barrier, roof)
 
     split = None
     if not args.no_split:
@@ -726,16 +879,35 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
-        rate, secs = oracle_rate(prob, U, args.cpu_sample, 2, O.dt(prob))
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "2 oracle steps of a periodic %d^3 sub-box of the %d^3 initial "
-                         "state, same dt (%.1f s)" % (args.cpu_sample, args.n, secs)}
+        odt = O.dt(prob)
+        pool = OraclePool()
+        try:
+            prate, psecs = pool.rate(prob, U, args.cpu_edge, 2, odt)
+        finally:
+            pool.close()
+        rate, secs = oracle_rate(prob, U, args.cpu_sample, 2, odt)
+        cpu = {"value": prate, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+               "sample": "2 oracle steps on each of %d periodic %d^3 sub-boxes of the %d^3 "
+                         "initial state, same dt, one serial oracle process per host core "
+                         "(%.1f s wall)" % (pool.cores, args.cpu_edge, args.n, psecs),
+               "single_core": {"value": rate, "unit": UNIT, "cores": 1,
+                               "sample": "2 oracle steps of a periodic %d^3 sub-box "
+                                         "(%.1f s)" % (args.cpu_sample, secs)}}
 
     if rank == 0:
         form_lines = {}
         for form, r in results.items():
             inf = r["info"]
+            fviews = {}
+            for k in (0, 1):
+                frec = None
+                if counts and form in counts["stage_kernels"]:
+                    frec = counts["stage_kernels"][form][KERNEL_NAMES[k]]
+                fviews[KERNEL_NAMES[k]] = pipe_views(
+                    frec, N, r["kms"][k] / max(r["klaunch"][k], 1), fma_peaks, hbm_peak,
+                    ALG_BYTES[k])
             form_lines[form] = {
+                "roofline": fviews,
                 "value": whole_job_rate(N, args.steps, ws, r["ms"] * 1e-3),
                 "ms_per_step": r["ms"] / args.steps,
                 "kernel_ms": {KERNEL_NAMES[k]: r["kms"][k] / max(r["klaunch"][k], 1)
@@ -753,6 +925,7 @@ def run_ours(args):
             "data": "synthetic", "config": config_of(args, prob),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(head["launches"]), "clocks": head["clocks"],
+            "peaks": dict(fma_peaks, hbm_gbs=hbm_peak, fp64_nominal_tflops=FP64_PEAK_TFLOPS),
             "forms": form_lines,
             "batched": batched,
             "adjoint": adjoint,

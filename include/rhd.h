@@ -410,6 +410,12 @@ rhd_status rhd_batch_set_stream(rhd_batch* b, void* cuda_stream);
  * picks it from timings). */
 rhd_status rhd_batch_configure(rhd_batch* b, int tile2d, int blocks_per_sm);
 
+/* enable = 0: rhd_batch_step enqueues its launches directly instead of
+ * replaying a captured CUDA graph (results are identical; for tools that do
+ * not see the nodes of a graph, such as some profiler configurations).
+ * enable != 0 (the default): graphs. */
+rhd_status rhd_batch_use_graphs(rhd_batch* b, int enable);
+
 /* Cells of problem prob, or of the whole batch for prob < 0 (-1 on error). */
 int64_t rhd_batch_cells(const rhd_batch* b, int prob);
 
@@ -440,6 +446,19 @@ void rhd_batch_destroy(rhd_batch* b);
  * against IEEE results.  Runs on the legacy default stream and synchronises
  * the device.  Messages: rhd_last_error(NULL). */
 rhd_status rhd_eval_recip(const double* x, int64_t n, double* rcp, double* rsqrt);
+
+/* Diagnostic, with no counterpart in the paper: a throughput probe of the
+ * fused multiply-add pipe of the FP64 arithmetic (precision RHD_PREC_FP64)
+ * or of the single-precision arithmetic (RHD_PREC_MIXED), used to measure
+ * the roofline denominators of the stage kernels on the GPU in use.
+ * Launches nblocks blocks of 256 threads on `stream` (a cudaStream_t; NULL:
+ * the legacy default stream), each thread running 8 independent chains of
+ * iters multiply-adds, and returns without synchronising; *flops receives
+ * the floating-point operations of the launch (2 per multiply-add), so that
+ * a CUDA-event time around the call gives FLOP/s.  RHD_ERR_ARG for another
+ * precision, nblocks or iters <= 0 or flops NULL.  Messages:
+ * rhd_last_error(NULL). */
+rhd_status rhd_fma_probe(int precision, int nblocks, int iters, void* stream, double* flops);
 
 /* Largest grid, in cells, that rhd_step_noalloc accepts. */
 #define RHD_NOALLOC_MAX_CELLS 262144

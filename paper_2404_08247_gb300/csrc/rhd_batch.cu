@@ -206,6 +206,7 @@ struct rhd_batch {
   std::vector<char> eps_dirty;
   int tile2d = 0;
   int blocks_per_sm = 2;
+  bool use_graphs = true;  // rhd_batch_use_graphs
   bool general = false;  // some problem needs the general kernels
   bool ppm = false;      // some problem has PPM faces
   int items_tile = -1;  // tile shape the work list was built for
@@ -466,9 +467,9 @@ rhd_status rhd_batch_state_get(rhd_batch* b, int prob, double* dst, int64_t coun
   return RHD_OK;
 }
 
-// Capture nsteps steps (status reset, then per stage a counter reset and one
-// persistent launch) starting from ping-pong buffer cur0.
-static rhd_status capture(rhd_batch* b, int nsteps, int cur0, cudaGraphExec_t* exec) {
+// Enqueue nsteps steps on stream cs (status reset, then per stage a counter
+// reset and one persistent launch) starting from ping-pong buffer cur0.
+static cudaError_t enqueue_steps(rhd_batch* b, int nsteps, int cur0, cudaStream_t cs) {
   BatchArgs B;
   B.probs = b->d_desc;
   B.items = b->d_items;
@@ -482,9 +483,6 @@ static rhd_status capture(rhd_batch* b, int nsteps, int cur0, cudaGraphExec_t* e
   B.st = b->d_status;
   int grid = b->num_sms * b->blocks_per_sm;
   if (grid > b->nitems) grid = b->nitems;
-  cudaGraph_t graph = nullptr;
-  cudaStream_t cs = b->stream ? b->stream : b->own;  // the legacy stream cannot capture
-  BTRY(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_status_reset(b->d_status, cs);
   int cur = cur0;
   for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
@@ -502,6 +500,15 @@ static rhd_status capture(rhd_batch* b, int nsteps, int cur0, cudaGraphExec_t* e
       e = launch_batch(2, b->precision, b->general, b->ppm, b->tile2d, B, grid, cs);
     cur ^= 1;
   }
+  return e;
+}
+
+// Capture the launches of enqueue_steps into a graph.
+static rhd_status capture(rhd_batch* b, int nsteps, int cur0, cudaGraphExec_t* exec) {
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cs = b->stream ? b->stream : b->own;  // the legacy stream cannot capture
+  BTRY(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_steps(b, nsteps, cur0, cs);
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -521,20 +528,25 @@ rhd_status rhd_batch_step(rhd_batch* b, int nsteps, rhd_step_info* info) {
     if (!b->set_mask[p]) return bfail(b, RHD_ERR_STATE, "problem %d has no state", p);
   BTRY(b, cudaSetDevice(b->device));
   cudaGraphExec_t exec = nullptr;
-  for (auto& g : b->graphs)
-    if (g.nsteps == nsteps && g.cur0 == b->cur && g.tile2d == b->tile2d &&
-        g.bps == b->blocks_per_sm)
-      exec = g.exec;
-  if (!exec) {
-    rhd_status s = capture(b, nsteps, b->cur, &exec);
-    if (s != RHD_OK) return s;
-    b->graphs.push_back({nsteps, b->cur, b->tile2d, b->blocks_per_sm, exec});
+  if (b->use_graphs) {
+    for (auto& g : b->graphs)
+      if (g.nsteps == nsteps && g.cur0 == b->cur && g.tile2d == b->tile2d &&
+          g.bps == b->blocks_per_sm)
+        exec = g.exec;
+    if (!exec) {
+      rhd_status s = capture(b, nsteps, b->cur, &exec);
+      if (s != RHD_OK) return s;
+      b->graphs.push_back({nsteps, b->cur, b->tile2d, b->blocks_per_sm, exec});
+    }
   }
   // graphs run on the batch stream, or on the private stream (after the
   // legacy stream's earlier work) when the batch stream is the legacy one
   cudaStream_t rs = b->stream ? b->stream : b->own;
   if (!b->stream) BTRY(b, cudaStreamSynchronize(nullptr));
-  BTRY(b, cudaGraphLaunch(exec, rs));
+  if (exec)
+    BTRY(b, cudaGraphLaunch(exec, rs));
+  else
+    BTRY(b, enqueue_steps(b, nsteps, b->cur, rs));
   BTRY(b, cudaMemcpyAsync(b->h_status, b->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                           rs));
   BTRY(b, cudaStreamSynchronize(rs));
@@ -567,6 +579,12 @@ rhd_status rhd_batch_step(rhd_batch* b, int nsteps, rhd_step_info* info) {
   if (code != RHD_OK)
     return bfail(b, code, "step %d stage %d failed at pooled cell %lld (status %d)",
                  st.fail_step, st.fail_stage, (long long)cell, (int)code);
+  return RHD_OK;
+}
+
+rhd_status rhd_batch_use_graphs(rhd_batch* b, int enable) {
+  if (!b) return bfail(nullptr, RHD_ERR_ARG, "batch is NULL");
+  b->use_graphs = enable != 0;
   return RHD_OK;
 }
 

@@ -131,6 +131,7 @@ SIGNATURES = {
                                        ctypes.POINTER(rhd_step_info)]),
     "rhd_adjoint": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int, ctypes.c_double, _V, _V]),
     "rhd_eval_recip": (ctypes.c_int, [_V, _I64, _V, _V]),
+    "rhd_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _V, _D]),
     "rhd_hydro_dt": (ctypes.c_int, [_V, _D]),
     "rhd_hydro_step": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(rhd_step_info)]),
@@ -147,6 +148,7 @@ SIGNATURES = {
     "rhd_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_V)]),
     "rhd_batch_set_stream": (ctypes.c_int, [_V, _V]),
     "rhd_batch_configure": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+    "rhd_batch_use_graphs": (ctypes.c_int, [_V, ctypes.c_int]),
     "rhd_batch_cells": (_I64, [_V, ctypes.c_int]),
     "rhd_batch_state_set": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
     "rhd_batch_state_get": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
@@ -271,6 +273,19 @@ def eval_recip(x):
     _check(load().rhd_eval_recip(ctypes.c_void_p(x.data_ptr()), int(x.numel()),
                                  ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(q.data_ptr())))
     return r, q
+
+
+def fma_probe(precision: str, nblocks: int, iters: int, stream=None) -> float:
+    """rhd_fma_probe: launch the multiply-add throughput probe of the FP64
+    ("fp64") or single-precision ("fp32") pipe on `stream` (a torch stream;
+    None: the current one) without synchronising; returns its flop count."""
+    import torch
+    prec = {"fp64": RHD_PREC_FP64, "fp32": RHD_PREC_MIXED}[precision]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    flops = ctypes.c_double(0.0)
+    _check(load().rhd_fma_probe(prec, int(nblocks), int(iters), ctypes.c_void_p(st.cuda_stream),
+                                ctypes.byref(flops)))
+    return flops.value
 
 
 class RHDContext:
@@ -554,6 +569,11 @@ class RHDBatch:
 
     def configure(self, tile2d: int, blocks_per_sm: int):
         self._check(self.lib.rhd_batch_configure(self.h, int(tile2d), int(blocks_per_sm)))
+
+    def use_graphs(self, enable: bool):
+        """rhd_batch_use_graphs: replay captured CUDA graphs (default) or
+        enqueue each step's launches directly."""
+        self._check(self.lib.rhd_batch_use_graphs(self.h, int(bool(enable))))
 
     def cells(self, prob: int = -1) -> int:
         return int(self.lib.rhd_batch_cells(self.h, prob))

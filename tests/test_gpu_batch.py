@@ -143,3 +143,19 @@ def test_batch_mixed_workload_subset_matches_oracle(R, oracle_mod):
         errs = assert_parity(got[i], Uo, 1e-5, "problem %d (%s cells)" % (i, p["n"]))
         worst = max(worst, max(errs.values()))
     print("worst per-field error over the 16 problems: %.2e" % worst)
+
+
+def test_direct_launches_equal_graph_replays(R):
+    """rhd_batch_use_graphs(0) enqueues each step's launches directly: the
+    same bits as the captured graphs."""
+    problems = small_batch(6, seed=23)
+    out = []
+    for graphs in (True, False):
+        with R.RHDBatch([p for p, _ in problems], "mixed") as b:
+            b.use_graphs(graphs)
+            for i, (_, U) in enumerate(problems):
+                b.set_state(i, U)
+            b.step(3)
+            out.append([b.get_state(i) for i in range(len(problems))])
+    for i in range(len(problems)):
+        assert np.array_equal(out[0][i], out[1][i]), i
