@@ -693,6 +693,51 @@ def run_slabs(args, rhd, torch, prob, U, ws, dist, barrier, whole_ms):
                     "boundary planes; the TAU factors are recomputed once per call"}
 
 
+def run_decomposed(args, rhd, torch, prob, U, ws, rank, dist, barrier):
+    """One box decomposed in z across the ranks, one slab per rank (strong
+    scaling: the total work is the box's), stepped stage by stage through
+    paper_2404_08247_gb300.decomp with the ghost planes exchanged between
+    ranks by NCCL point-to-point transfers before each stage (one rank: the
+    whole periodic box as one slab exchanging with itself).  Every rank holds
+    the same initial box and takes its z range."""
+    from paper_2404_08247_gb300 import decomp
+    stream = torch.cuda.current_stream()
+    nz = prob["n"][2]
+    cuts = [round(i * nz / ws) for i in range(ws + 1)]
+    q = rhd.slab_problems(prob, cuts)[rank]
+    ctx = rhd.RHDContext(q, args.precision, stream=stream)
+    try:
+        ctx.set_state(np.ascontiguousarray(U[:, cuts[rank]:cuts[rank + 1]]))
+        slab = decomp.CtxSlab(ctx, "cuda")
+        dt = rhd.rhd_default_dt(rhd.params_from_problem(prob, args.precision))
+        decomp.exchange_material(slab, dist)
+        decomp.step(slab, dist, args.warmup, dt)
+        l0 = ctx.launch_count()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = decomp.step(slab, dist, args.steps, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+        launches = ctx.launch_count() - l0
+    finally:
+        ctx.close()
+    N = int(np.prod(prob["n"]))
+    P = prob["n"][0] * prob["n"][1]
+    depth = 2 if prob.get("reconstruction", "plm") == "plm" else 3
+    return {"value": N * args.steps / (ms * 1e-3) / 1e6, "unit": UNIT,
+            "ms_per_step": ms / args.steps, "steps": args.steps, "ranks": ws,
+            "slab_planes": cuts, "status": res["status"], "scaling": "strong",
+            "exchange_bytes_per_rank_per_step": 2 * 2 * 4 * depth * P * 8,
+            "gpu_launches_rank0": int(launches),
+            "note": "one box in z-slabs, one per rank, ghost planes of E and F exchanged "
+                    "before each stage (NCCL send/recv between ranks; one rank: its own "
+                    "planes), the statuses max-reduced before each commit"}
+
+
 def run_hydro_only(args):
     """2 + 3 hydrodynamic steps of the --n^3 box at its CFL step; one line."""
     import torch
@@ -732,6 +777,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     rhd.load()
     prob, U = workload(args, rank)
+    # the decomposed box: every rank the same box (rank 0's seeds)
+    prob0, U0 = (prob, U) if rank == 0 else workload(args, 0)
     N = U[0].size
     stream = torch.cuda.current_stream()
     Ud = torch.from_numpy(U).cuda()
@@ -863,6 +910,10 @@ def run_ours(args):
     if not args.no_slabs and prob["ndim"] == 3 and prob["n"][2] >= 6:
         slabs = run_slabs(args, rhd, torch, prob, U, ws, dist, barrier, ms)
 
+    decomposed = None
+    if not args.no_slabs and prob["ndim"] == 3 and prob["n"][2] >= 3 * ws:
+        decomposed = run_decomposed(args, rhd, torch, prob0, U0, ws, rank, dist, barrier)
+
     roof = {"counts": counts, "peaks": fma_peaks, "hbm": hbm_peak}
     batched = None
     if not args.no_batched:
@@ -931,6 +982,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "hydro_split": split,
             "slabs": slabs,
+            "decomposed": decomposed,
         }
         print(json.dumps(line))
     if dist is not None:

@@ -52,7 +52,10 @@ typedef enum {
   RHD_ERR_OUTER = 4,        /* outer iteration did not converge (Sec. 3.3) */
   RHD_ERR_NONPHYSICAL = 5,  /* T <= 0, E <= 0 or a non-finite value */
   RHD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
-  RHD_ERR_STATE = 7         /* call out of order (e.g. step before all fields set) */
+  RHD_ERR_STATE = 7,        /* call out of order (e.g. step before all fields set) */
+  RHD_ERR_BOUNDS = 8        /* a library built with -DRHD_BOUNDS_CHECK caught an index
+                               outside its array in a stage kernel (fail_cell holds
+                               the index); never returned by the default build */
 } rhd_status;
 
 /* Boundaries of the radiation transport.  PERIODIC: wrap; REFLECT: mirror
@@ -370,6 +373,73 @@ rhd_status rhd_hydro_step_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, do
 rhd_status rhd_step_split_slabs(rhd_ctx* const* slabs, int nslab, int nsteps, double dt_h,
                                 rhd_step_info* info);
 
+/* ---- Domain decomposition across processes: one z-slab per process ----
+ * The stage-by-stage form of rhd_step_slabs for slabs that live in different
+ * processes or on different GPUs (Sec. 3.2: a stage of the scheme needs the
+ * face neighbours' ghost planes and nothing else).  Each process holds one
+ * slab context (params as rhd_step_slabs wants them: HALO faces between
+ * slabs, the same grid otherwise) and the caller carries the planes between
+ * neighbours, by NCCL send/receive or any other route.  One step:
+ *   rhd_slab_planes_get(BOUNDARY_LOW and _HIGH, stage 1) -> send to the
+ *     slabs below and above; rhd_slab_planes_set(GHOSTS_HIGH and _LOW) with
+ *     what they sent; rhd_slab_stage(1, dt);
+ *   the same with stage 2 planes; rhd_slab_stage(2, dt);
+ *   rhd_slab_status; combine the statuses of all slabs; rhd_slab_commit(1)
+ *     only if every slab succeeded (else 0: every slab keeps y(n)).
+ * With HLL mode TAU, whenever rho or kappa of any slab changes: send
+ * MATERIAL_LOW down and set it as MATERIAL_ABOVE, then send EPS_HIGH up and
+ * set it as EPS_BELOW.  The slabs then evolve bit for bit like the whole grid
+ * and like rhd_step_slabs.  Failed cells are numbered within the slab. */
+enum {
+  RHD_SLAB_BOUNDARY_LOW = 0,   /* get: E, Fx, Fy, Fz of the lowest `depth` planes of the
+                                  stage's input state (stage 1 y(n), stage 2 y(n+1/2)) */
+  RHD_SLAB_BOUNDARY_HIGH = 1,  /* get: the same of the highest `depth` planes */
+  RHD_SLAB_GHOSTS_LOW = 2,     /* set: the ghost planes below (the BOUNDARY_HIGH of the
+                                  slab below) */
+  RHD_SLAB_GHOSTS_HIGH = 3,    /* set: the ghost planes above (the BOUNDARY_LOW of the
+                                  slab above) */
+  RHD_SLAB_MATERIAL_LOW = 4,   /* get: kappa, then rho, of plane 0 */
+  RHD_SLAB_MATERIAL_ABOVE = 5, /* set: the MATERIAL_LOW of the slab above */
+  RHD_SLAB_EPS_HIGH = 6,       /* get: TAU factors of the top face (needs MATERIAL_ABOVE) */
+  RHD_SLAB_EPS_BELOW = 7       /* set: the EPS_HIGH of the slab below */
+};
+
+/* Doubles that a plane kind holds for this slab: 4 depth n0 n1 for the
+ * boundary and ghost planes (depth 2 with PLM faces, 3 with PPM), laid out
+ * [field E, Fx, Fy, Fz][plane, in z order][n0 n1]; 2 n0 n1 for the material
+ * planes; n0 n1 for the TAU factors.  -1 for a bad kind or a grid that is not
+ * 3-D. */
+int64_t rhd_slab_plane_doubles(const rhd_ctx* ctx, int what);
+
+/* Copy planes of kind `what` (a get kind) into dst (count doubles, host or
+ * device, caller-owned); `stage` (1 or 2) selects the input state of the
+ * boundary planes and is ignored otherwise.  Host copies synchronise the
+ * stream.  RHD_ERR_ARG for a context without a HALO face, a bad kind or
+ * count; RHD_ERR_STATE for stage-2 planes before stage 1. */
+rhd_status rhd_slab_planes_get(rhd_ctx* ctx, int what, int stage, double* dst, int64_t count,
+                               int dst_on_device);
+
+/* Store planes of kind `what` (a set kind) from src (count doubles, host or
+ * device) in the slab's halo buffer; the face they belong to must be HALO. */
+rhd_status rhd_slab_planes_set(rhd_ctx* ctx, int what, const double* src, int64_t count,
+                               int src_on_device);
+
+/* Run stage 1 (eq. imex1) or stage 2 (eq. imex2) of one step on the slab's
+ * stream with the ghost planes set last (does not synchronise).  Stage 1
+ * takes dt (<= 0: rhd_default_dt) and starts the step; stage 2 uses the same
+ * dt.  RHD_ERR_STATE out of order, or with TAU factors whose neighbour planes
+ * are not set for the current rho and kappa. */
+rhd_status rhd_slab_stage(rhd_ctx* ctx, int stage, double dt);
+
+/* After stage 2: wait for the slab's stream and return the slab's status
+ * (info, nullable, as by rhd_step with fail_cell within the slab).  The step
+ * is not applied until rhd_slab_commit. */
+rhd_status rhd_slab_status(rhd_ctx* ctx, rhd_step_info* info);
+
+/* After rhd_slab_status: commit != 0 makes y(n+1) the state and advances the
+ * time by dt; 0 keeps y(n) (another slab failed). */
+rhd_status rhd_slab_commit(rhd_ctx* ctx, int commit);
+
 /* Number of kernels this context has launched since rhd_init. */
 int64_t rhd_launch_count(const rhd_ctx* ctx);
 
@@ -472,20 +542,25 @@ rhd_status rhd_fma_probe(int precision, int nblocks, int iters, void* stream, do
  * state_in, state_out: device pointers on the current device, each holding
  * RHD_NFIELDS*ncell doubles, field-major as in rhd_state_set_all; they must
  * not overlap.  state_out receives y(n+1) (rho and kappa are copied).  Input
- * values are not checked.  dt <= 0 selects rhd_default_dt(p); stream is a
- * cudaStream_t (NULL: the legacy default stream).  The caller owns both
- * buffers.
+ * values are not checked.  dt <= 0 selects rhd_default_dt(p); a dt that is
+ * not finite returns RHD_ERR_ARG.  stream is a cudaStream_t (NULL: the
+ * legacy default stream).  The caller owns both buffers.  When the step
+ * fails (a status other than RHD_OK from a stage), state_in is unchanged and
+ * the evolved fields of state_out are unspecified.
  *
  * The stage buffer y(n+1/2) and the status block live in file-scope device
  * arrays sized for RHD_NOALLOC_MAX_CELLS cells (16 MiB), which every GPU that
  * loads the library holds until the process exits; a larger grid returns
  * RHD_ERR_ARG with a message.  The first call on a device resolves the
- * arrays' device addresses (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  All calls share the arrays: each call clears
- * the status block and rewrites the stage buffer, and calls that overlap on
- * the GPU (other streams or host threads) race.  The call waits for the
- * stream to read the status; info (nullable) is filled as by rhd_step, with
- * t = dt.  Messages: rhd_last_error(NULL). */
+ * arrays' device addresses (cudaGetSymbolAddress), a set-up to be done
+ * before any stream capture begins; the addresses are kept for the life of
+ * the process, so do not call this entry point again on a device after a
+ * cudaDeviceReset of it.  All calls share the arrays: each call clears the
+ * status block and rewrites the stage buffer, and calls that overlap on the
+ * GPU (other streams or host threads) race.  Every call copies the status
+ * block to the host and synchronises its stream before returning; info
+ * (nullable) is filled as by rhd_step, with t = dt.  Messages:
+ * rhd_last_error(NULL). */
 rhd_status rhd_step_noalloc(const rhd_params* p, const double* state_in,
                             double* state_out, double dt, void* stream,
                             rhd_step_info* info);

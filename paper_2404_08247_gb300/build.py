@@ -5,6 +5,11 @@ Each ``csrc/*.cu`` is compiled separately (in parallel) with
 ``paper_2404_08247_gb300/librhd.so`` (CUDA runtime linked statically, so the
 library loads next to any PyTorch build).  Rebuilds only when a source or
 header is newer than the library.
+
+``build(bounds_check=True)`` builds ``librhd_bounds.so`` from the same
+sources with ``-DRHD_BOUNDS_CHECK``: the stage kernels check every global and
+shared-memory index they use and report one outside its array as the status
+RHD_ERR_BOUNDS instead of accessing it (``rhd.load(path)`` selects it).
 """
 from __future__ import annotations
 
@@ -20,6 +25,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librhd.so")
+BOUNDS_BUILD_DIR = os.path.join(PKG, "_build_bounds")
+BOUNDS_LIB = os.path.join(PKG, "librhd_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -43,23 +50,29 @@ def _inputs():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link librhd.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          bounds_check: bool = False) -> str:
+    """Compile and link librhd.so (librhd_bounds.so with bounds_check);
+    returns its path."""
+    lib = BOUNDS_LIB if bounds_check else LIB
+    build_dir = BOUNDS_BUILD_DIR if bounds_check else BUILD_DIR
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if bounds_check:
+        extra = extra + ["-DRHD_BOUNDS_CHECK"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -72,13 +85,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for obj, log in results:
             if log.strip():
                 print(os.path.basename(obj), log)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

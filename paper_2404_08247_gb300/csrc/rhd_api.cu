@@ -77,6 +77,14 @@ struct rhd_ctx {
   // factors of the low face; allocated by the first rhd_step_slabs
   double* halo = nullptr;
   double* hyd_halo = nullptr;  // the same for the primitives (2 x 5 x HALO_PLANES planes)
+  // a slab stepped stage by stage by its own process (rhd_slab_stage): 0 idle,
+  // 1 after stage 1, 2 after stage 2, 3 status read; the step's dt; whether
+  // the neighbours' material plane (top face) and TAU factors (bottom face)
+  // are set for the current rho and kappa
+  int slab_phase = 0;
+  double slab_dt = 0.0;
+  bool slab_mat_above = false;
+  bool slab_eps_below = false;
 };
 
 // a context whose grid is a z-slab of a decomposed grid
@@ -442,6 +450,7 @@ rhd_status rhd_use_private_stream(rhd_ctx* c) {
 static rhd_status check_copy_args(rhd_ctx* c, int field, const void* ptr, int64_t count) {
   if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
   if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (c->slab_phase != 0) return fail(c, RHD_ERR_STATE, "a slab step is in progress");
   if (field < 0 || field >= RHD_NFIELDS) return fail(c, RHD_ERR_ARG, "bad field %d", field);
   if (!ptr) return fail(c, RHD_ERR_ARG, "buffer is NULL");
   if (count != (int64_t)c->ncell)
@@ -450,7 +459,10 @@ static rhd_status check_copy_args(rhd_ctx* c, int field, const void* ptr, int64_
 }
 
 static rhd_status copy_in(rhd_ctx* c, int field, const double* src, int on_dev) {
-  if (field == RHD_F_RHO || field == RHD_F_KAPPA) c->eps_dirty = true;
+  if (field == RHD_F_RHO || field == RHD_F_KAPPA) {
+    c->eps_dirty = true;
+    c->slab_mat_above = c->slab_eps_below = false;  // the neighbours' planes are stale
+  }
   CUDA_TRY(c, cudaMemcpyAsync(field_ptr(c, field), src, sizeof(double) * c->ncell,
                               on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                               c->stream));
@@ -1039,6 +1051,7 @@ static rhd_status hydro_run(rhd_ctx* c, int nsteps, double dt, rhd_step_info* in
     const DevStatus& st = *c->h_status;
     int ok = batch;
     c->eps_dirty = true;  // rho has changed
+    c->slab_mat_above = c->slab_eps_below = false;
     if (st.fail_key != ~0ull) {
       code = (rhd_status)(st.fail_key & 0xffull);
       ok = st.fail_step;
@@ -1210,6 +1223,8 @@ static rhd_status check_slabs(rhd_ctx* const* slabs, int nslab) {
     if (c->device != c0->device || c->stream != c0->stream)
       return fail(c0, RHD_ERR_ARG, "slab %d: slabs share one device and one stream", s);
     if (c->pending) return fail(c0, RHD_ERR_STATE, "slab %d: a step batch is pending", s);
+    if (c->slab_phase != 0)
+      return fail(c0, RHD_ERR_STATE, "slab %d: a stage-by-stage step is in progress", s);
     if (c->fields_set != kAllFields)
       return fail(c0, RHD_ERR_STATE, "slab %d: not every field has been set", s);
     if (s < last && (c->p.bc[2][1] != RHD_BC_HALO || slabs[s + 1]->p.bc[2][0] != RHD_BC_HALO))
@@ -1557,5 +1572,255 @@ double rhd_time(const rhd_ctx* c) { return c ? c->t : 0.0; }
 const char* rhd_last_error(const rhd_ctx* c) { return c ? c->err : g_err; }
 
 void rhd_destroy(rhd_ctx* c) { release(c); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// A z-slab stepped by its own process (the decomposition across processes or
+// GPUs, Sec. 3.2: a stage needs the neighbours' ghost planes only).  The
+// caller moves the planes between slabs (NCCL, MPI, a file ...); the library
+// packs the planes a neighbour needs, stores the planes it receives and runs
+// each stage on them, with the same kernels and halo reads as
+// rhd_step_slabs, so that the slabs stay bit-identical to the whole grid.
+
+// halo buffer of a slab: [2 sides][4 fields][HALO_PLANES][n0 n1], then the
+// kappa and rho planes of the slab above and the TAU factors of the low face
+static rhd_status slab_halo(rhd_ctx* c) {
+  if (c->halo) return RHD_OK;
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  cudaError_t e = cudaMalloc(&c->halo, sizeof(double) * kHaloSlots * P);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->halo = nullptr;
+    return fail(c, RHD_ERR_CUDA, "halo buffer: %s", cudaGetErrorString(e));
+  }
+  return RHD_OK;
+}
+
+static int slab_depth(const rhd_ctx* c) {
+  return c->p.reconstruction == RHD_RECON_PLM ? 2 : 3;
+}
+
+extern "C" {
+
+int64_t rhd_slab_plane_doubles(const rhd_ctx* c, int what) {
+  if (!c || c->p.ndim != 3) return -1;
+  const int64_t P = (int64_t)c->g.n[0] * c->g.n[1];
+  switch (what) {
+    case RHD_SLAB_BOUNDARY_LOW:
+    case RHD_SLAB_BOUNDARY_HIGH:
+    case RHD_SLAB_GHOSTS_LOW:
+    case RHD_SLAB_GHOSTS_HIGH: return 4 * slab_depth(c) * P;
+    case RHD_SLAB_MATERIAL_LOW:
+    case RHD_SLAB_MATERIAL_ABOVE: return 2 * P;
+    case RHD_SLAB_EPS_HIGH:
+    case RHD_SLAB_EPS_BELOW: return P;
+    default: return -1;
+  }
+}
+
+static rhd_status slab_check(rhd_ctx* c, int what, const void* buf, int64_t count) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (!has_halo(c)) return fail(c, RHD_ERR_ARG, "the context has no HALO face");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (!buf) return fail(c, RHD_ERR_ARG, "buffer is NULL");
+  const int64_t want = rhd_slab_plane_doubles(c, what);
+  if (want < 0) return fail(c, RHD_ERR_ARG, "bad plane kind %d", what);
+  if (count != want)
+    return fail(c, RHD_ERR_ARG, "count %lld != %lld doubles", (long long)count, (long long)want);
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  return slab_halo(c);
+}
+
+rhd_status rhd_slab_planes_get(rhd_ctx* c, int what, int stage, double* dst, int64_t count,
+                               int dst_on_device) {
+  rhd_status s = slab_check(c, what, dst, count);
+  if (s != RHD_OK) return s;
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (what == RHD_SLAB_BOUNDARY_LOW || what == RHD_SLAB_BOUNDARY_HIGH) {
+    // stage 1 reads y(n), stage 2 y(n+1/2)
+    if (stage == 1 && c->slab_phase != 0)
+      return fail(c, RHD_ERR_STATE, "stage-1 planes: the slab is within a step");
+    if (stage == 2 && c->slab_phase != 1)
+      return fail(c, RHD_ERR_STATE, "stage-2 planes: stage 1 has not run");
+    if (stage != 1 && stage != 2) return fail(c, RHD_ERR_ARG, "stage must be 1 or 2");
+    const double* src = stage == 1 ? c->ybuf[c->cur] : c->yhalf;
+    const int depth = slab_depth(c);
+    const size_t z0 = what == RHD_SLAB_BOUNDARY_LOW ? 0 : (size_t)c->g.n[2] - depth;
+    static const int kSlots[4] = {Y_ERAD, Y_FX, Y_FY, Y_FZ};
+    for (int q = 0; q < 4; ++q)
+      CUDA_TRY(c, cudaMemcpyAsync(dst + (size_t)q * depth * P,
+                                  src + (size_t)kSlots[q] * c->ncell + z0 * P,
+                                  sizeof(double) * depth * P, kind, c->stream));
+  } else if (what == RHD_SLAB_MATERIAL_LOW) {
+    CUDA_TRY(c, cudaMemcpyAsync(dst, c->kappa, sizeof(double) * P, kind, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(dst + P, c->rho, sizeof(double) * P, kind, c->stream));
+  } else if (what == RHD_SLAB_EPS_HIGH) {
+    if (c->p.hll_mode != RHD_HLL_TAU) return fail(c, RHD_ERR_ARG, "TAU factors: HLL mode NONE");
+    const bool top = c->p.bc[2][1] == RHD_BC_HALO;
+    if (top && !c->slab_mat_above)
+      return fail(c, RHD_ERR_STATE, "TAU factors: the material plane of the slab above is "
+                  "not set");
+    if (c->eps_dirty) {
+      double* hk = c->halo + (size_t)8 * HALO_PLANES * P;
+      CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps,
+                                 c->stream, top ? hk : nullptr, top ? hk + P : nullptr));
+      c->launches += 1;
+      c->eps_dirty = false;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(dst, c->eps[2] + (size_t)(c->g.n[2] - 1) * P,
+                                sizeof(double) * P, kind, c->stream));
+  } else {
+    return fail(c, RHD_ERR_ARG, "plane kind %d is set, not read", what);
+  }
+  if (!dst_on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RHD_OK;
+}
+
+rhd_status rhd_slab_planes_set(rhd_ctx* c, int what, const double* src, int64_t count,
+                               int src_on_device) {
+  rhd_status s = slab_check(c, what, src, count);
+  if (s != RHD_OK) return s;
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  double* hk = c->halo + (size_t)8 * HALO_PLANES * P;
+  if (what == RHD_SLAB_GHOSTS_LOW || what == RHD_SLAB_GHOSTS_HIGH) {
+    const int side = what == RHD_SLAB_GHOSTS_LOW ? 0 : 1;
+    if (c->p.bc[2][side] != RHD_BC_HALO)
+      return fail(c, RHD_ERR_ARG, "ghost planes for a face that is not HALO");
+    const int depth = slab_depth(c);
+    // planes in z order: below, z = -depth..-1; above, z = n2..n2+depth-1
+    const size_t i0 = side == 0 ? HALO_PLANES - depth : 0;
+    double* h = c->halo + (size_t)side * 4 * HALO_PLANES * P;
+    for (int q = 0; q < 4; ++q)
+      CUDA_TRY(c, cudaMemcpyAsync(h + ((size_t)q * HALO_PLANES + i0) * P,
+                                  src + (size_t)q * depth * P, sizeof(double) * depth * P, kind,
+                                  c->stream));
+  } else if (what == RHD_SLAB_MATERIAL_ABOVE) {
+    if (c->p.bc[2][1] != RHD_BC_HALO) return fail(c, RHD_ERR_ARG, "the top face is not HALO");
+    CUDA_TRY(c, cudaMemcpyAsync(hk, src, sizeof(double) * 2 * P, kind, c->stream));
+    c->slab_mat_above = true;
+    c->eps_dirty = true;
+  } else if (what == RHD_SLAB_EPS_BELOW) {
+    if (c->p.bc[2][0] != RHD_BC_HALO) return fail(c, RHD_ERR_ARG, "the low face is not HALO");
+    CUDA_TRY(c, cudaMemcpyAsync(hk + 2 * P, src, sizeof(double) * P, kind, c->stream));
+    c->slab_eps_below = true;
+  } else {
+    return fail(c, RHD_ERR_ARG, "plane kind %d is read, not set", what);
+  }
+  if (!src_on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RHD_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+rhd_status rhd_slab_stage(rhd_ctx* c, int stage, double dt) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (!has_halo(c)) return fail(c, RHD_ERR_ARG, "the context has no HALO face");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (stage != 1 && stage != 2) return fail(c, RHD_ERR_ARG, "stage must be 1 or 2");
+  if (stage == 1 && c->slab_phase != 0)
+    return fail(c, RHD_ERR_STATE, "stage 1: the previous step has not been committed");
+  if (stage == 2 && c->slab_phase != 1) return fail(c, RHD_ERR_STATE, "stage 2 before stage 1");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  rhd_status s = slab_halo(c);
+  if (s != RHD_OK) return s;
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  if (stage == 1) {
+    if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
+    if (!std::isfinite(dt)) return fail(c, RHD_ERR_ARG, "dt is not finite");
+    if (c->p.hll_mode == RHD_HLL_TAU) {
+      const bool top = c->p.bc[2][1] == RHD_BC_HALO, low = c->p.bc[2][0] == RHD_BC_HALO;
+      if ((top && !c->slab_mat_above) || (low && !c->slab_eps_below))
+        return fail(c, RHD_ERR_STATE, "TAU factors: the neighbours' material and factor "
+                    "planes are not set (RHD_SLAB_MATERIAL_ABOVE, RHD_SLAB_EPS_BELOW)");
+      if (c->eps_dirty) {
+        double* hk = c->halo + (size_t)8 * HALO_PLANES * P;
+        CUDA_TRY(c, launch_tau_eps(c->g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps,
+                                   c->stream, top ? hk : nullptr, top ? hk + P : nullptr));
+        c->launches += 1;
+        c->eps_dirty = false;
+      }
+    }
+    CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+    c->launches += 1;
+    c->slab_dt = dt;
+  }
+  StageArgs a;
+  a.cell_base = 0;
+  for (int d = 0; d < 3; ++d) a.eps[d] = c->eps[d];
+  a.g = c->g;
+  a.ph = c->ph;
+  a.dt = c->slab_dt;
+  a.step = 0;
+  a.rho = c->rho;
+  a.kappa = c->kappa;
+  a.st = c->d_status;
+  a.halo[0] = c->halo;
+  a.halo[1] = c->halo + (size_t)4 * HALO_PLANES * P;
+  a.eps_zlo = c->halo + (size_t)8 * HALO_PLANES * P + 2 * P;
+  const int N = c->ncell;
+  if (stage == 1) {
+    slots_of<const double*>(a.yt, c->ybuf[c->cur], N);
+    slots_of<const double*>(a.yn, c->ybuf[c->cur], N);
+    slots_of<double*>(a.yo, c->yhalf, N);
+  } else {
+    slots_of<const double*>(a.yt, c->yhalf, N);
+    slots_of<const double*>(a.yn, c->ybuf[c->cur], N);
+    slots_of<double*>(a.yo, c->ybuf[c->cur ^ 1], N);
+  }
+  CUDA_TRY(c, launch_stage(stage, c->p.precision, a, c->stream));
+  c->launches += 1;
+  c->slab_phase = stage;
+  return RHD_OK;
+}
+
+rhd_status rhd_slab_status(rhd_ctx* c, rhd_step_info* info) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->slab_phase != 2) return fail(c, RHD_ERR_STATE, "no slab step has run both stages");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const DevStatus& st = *c->h_status;
+  rhd_status code = RHD_OK;
+  int64_t cell = -1;
+  if (st.fail_key != ~0ull) {
+    code = (rhd_status)(st.fail_key & 0xffull);
+    cell = (int64_t)(st.fail_key >> 8);
+  }
+  if (info) {
+    clear_info(info, c->t);
+    info->status = code;
+    info->steps_done = code == RHD_OK ? 1 : 0;
+    info->fail_cell = cell;
+    info->fail_step = code == RHD_OK ? -1 : 0;
+    info->fail_stage = code == RHD_OK ? 0 : st.fail_stage;
+    info->max_newton = st.max_newton;
+    info->max_outer = st.max_outer;
+    info->sum_newton = (int64_t)st.sum_newton;
+    info->n_solves = (int64_t)st.n_solves;
+    info->sum_outer = (int64_t)st.sum_outer;
+    info->dt = c->slab_dt;
+  }
+  c->slab_phase = 3;
+  return code;
+}
+
+rhd_status rhd_slab_commit(rhd_ctx* c, int commit) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (c->slab_phase != 3) return fail(c, RHD_ERR_STATE, "the slab step's status was not read");
+  if (commit) {
+    c->cur ^= 1;
+    c->t += c->slab_dt;
+  }
+  c->slab_phase = 0;
+  return RHD_OK;
+}
 
 }  // extern "C"

@@ -31,6 +31,30 @@ struct DevStatus {
   unsigned long long sum_outer;
 };
 
+// Index checks of the bounds-checked build (-DRHD_BOUNDS_CHECK).  chk_index
+// returns whether 0 <= i < n; an index outside records RHD_ERR_BOUNDS in the
+// status block, with the index in place of the cell (its low 56 bits), and
+// the caller skips the access (a load gives 0).  Nothing traps: the context
+// stays usable and the step reports the status.  The default build compiles
+// the plain accesses.
+#ifdef RHD_BOUNDS_CHECK
+__device__ __forceinline__ bool chk_index(DevStatus* st, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicMin(&st->fail_key, (((unsigned long long)i & 0x00ffffffffffffffull) << 8) | 8ull);
+  return false;
+}
+#define RHD_LDG(st, p, i, n) (chk_index((st), (i), (n)) ? __ldg((p) + (i)) : 0.0)
+#define RHD_LD(st, p, i, n) (chk_index((st), (i), (n)) ? (p)[i] : 0.0)
+#define RHD_ST(st, p, i, n, v)                  \
+  do {                                          \
+    if (chk_index((st), (i), (n))) (p)[i] = (v); \
+  } while (0)
+#else
+#define RHD_LDG(st, p, i, n) __ldg((p) + (i))
+#define RHD_LD(st, p, i, n) ((p)[i])
+#define RHD_ST(st, p, i, n, v) ((p)[i] = (v))
+#endif
+
 struct Geometry {
   int ndim;
   int n[3];

@@ -12,6 +12,7 @@
 // shares them: a call clears the status block before use and overwrites the
 // whole stage buffer, but two calls that overlap on the GPU (different
 // streams, or different host threads) race on both.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -45,7 +46,8 @@ rhd_status noalloc_fail(rhd_status s, const char* msg) {
 // Device addresses of the file-scope arrays for the current device.  In host
 // code the array names are host-side stand-ins, not device addresses, so the
 // kernels are given what cudaGetSymbolAddress returns.  Resolved once per
-// device, on the first call made with that device current.
+// device, on the first call made with that device current, and kept for the
+// life of the process: a cudaDeviceReset of that device invalidates them.
 rhd_status resolve_symbols(int dev, DeviceSymbols*& out) {
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(RHD_ERR_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_symbols_mutex);
@@ -100,7 +102,8 @@ extern "C" rhd_status rhd_step_noalloc(const rhd_params* p, const double* state_
   if (a < b + bytes && b < a + bytes)
     return noalloc_fail(RHD_ERR_ARG, "state_in and state_out overlap");
   if (!(dt > 0.0)) dt = rhd_default_dt(p);
-  if (!(dt > 0.0) || dt != dt) return noalloc_fail(RHD_ERR_ARG, "dt is not positive");
+  if (!std::isfinite(dt)) return noalloc_fail(RHD_ERR_ARG, "dt is not finite");
+  if (!(dt > 0.0)) return noalloc_fail(RHD_ERR_ARG, "dt is not positive");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -132,7 +132,9 @@ __device__ __forceinline__ const double* halo_plane(const StageArgs& A, int side
 
 // optical depth of the face from the flux-mean opacity chi_0F
 __device__ __forceinline__ double eps_direct(const StageArgs& A, int ia, int ib, int d) {
-  double tau = 0.5 * (A.kappa[ia] * A.rho[ia] + A.kappa[ib] * A.rho[ib]) * A.g.dx[d];
+  const long long n = A.g.ncell;
+  double tau = 0.5 * (RHD_LD(A.st, A.kappa, ia, n) * RHD_LD(A.st, A.rho, ia, n) +
+                      RHD_LD(A.st, A.kappa, ib, n) * RHD_LD(A.st, A.rho, ib, n)) * A.g.dx[d];
   return tau_factor(tau * A.ph.kappa_F_ratio);
 }
 
@@ -144,7 +146,8 @@ __device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, in
   int c[3] = {cx, cy, cz};
   if (c[d] < 0) {
     // the low face of a slab: the factor its neighbour below computed
-    if (g.bc[d][0] == RHD_BC_HALO) return __ldg(A.eps_zlo + c[0] + g.n[0] * c[1]);
+    if (g.bc[d][0] == RHD_BC_HALO)
+      return RHD_LDG(A.st, A.eps_zlo, c[0] + g.n[0] * c[1], (long long)g.n[0] * g.n[1]);
     if (g.bc[d][0] != RHD_BC_PERIODIC) {
       c[d] = 0;  // reflecting wall: the ghost mirrors cell 0
       int i0 = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
@@ -153,7 +156,7 @@ __device__ __forceinline__ double face_eps(const StageArgs& A, int d, int cx, in
     c[d] = g.n[d] - 1;  // periodic: the same face as the top one
   }
   int il = c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
-  if (A.eps[d]) return __ldg(A.eps[d] + il);
+  if (A.eps[d]) return RHD_LDG(A.st, A.eps[d], il, g.ncell);
   bool flip;
   int xb = fold(c[d] + 1, g.n[d], g.bc[d][0], g.bc[d][1], flip);
   return eps_direct(A, il, il + (xb - c[d]) * g.stride[d], d);
@@ -208,17 +211,19 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
     const double wic = A.ph.inv_c;
     double E, Fx, Fy, Fz;
     if (hs >= 0) {
-      const int pidx = xf + g.n[0] * yf;
-      E = __ldg(hp + pidx);
-      Fx = __dmul_rn(__ldg(hp + hq + pidx), wic);
-      Fy = __dmul_rn(__ldg(hp + 2 * hq + pidx), wic);
-      Fz = __dmul_rn(__ldg(hp + 3 * hq + pidx), wic);
+      // index into the side's halo buffer [4 fields][HALO_PLANES][n0 n1]
+      const long long hi = (hp - A.halo[hs]) + xf + (long long)g.n[0] * yf;
+      const double* hb = A.halo[hs];
+      E = RHD_LDG(A.st, hb, hi, 4 * (long long)hq);
+      Fx = __dmul_rn(RHD_LDG(A.st, hb, hi + hq, 4 * (long long)hq), wic);
+      Fy = __dmul_rn(RHD_LDG(A.st, hb, hi + 2 * hq, 4 * (long long)hq), wic);
+      Fz = __dmul_rn(RHD_LDG(A.st, hb, hi + 3 * hq, 4 * (long long)hq), wic);
     } else {
       int idx = xf + g.n[0] * (yf + g.n[1] * zf);
-      E = __ldg(A.yt[Y_ERAD] + idx);
-      Fx = __dmul_rn(__ldg(A.yt[Y_FX] + idx), wic);
-      Fy = __dmul_rn(__ldg(A.yt[Y_FY] + idx), wic);
-      Fz = __dmul_rn(__ldg(A.yt[Y_FZ] + idx), wic);
+      E = RHD_LDG(A.st, A.yt[Y_ERAD], idx, g.ncell);
+      Fx = __dmul_rn(RHD_LDG(A.st, A.yt[Y_FX], idx, g.ncell), wic);
+      Fy = __dmul_rn(RHD_LDG(A.st, A.yt[Y_FY], idx, g.ncell), wic);
+      Fz = __dmul_rn(RHD_LDG(A.st, A.yt[Y_FZ], idx, g.ncell), wic);
     }
     Fx = fx ? -Fx : Fx;
     Fy = fy ? -Fy : Fy;
@@ -258,9 +263,18 @@ __device__ __forceinline__ void load_plane(const StageArgs& A, R* ring, int slot
   }
 }
 
+#ifdef RHD_BOUNDS_CHECK
+// the status block of the block's launch, for the checks of ring reads
+static __shared__ DevStatus* s_chk_status;
+#define RHD_RING_OK(c, n) chk_index(s_chk_status, (c), (n))
+#else
+#define RHD_RING_OK(c, n) true
+#endif
+
 template <class T, typename R>
 __device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
   using S = SmemT<T, R>;
+  if (!RHD_RING_OK(c, S::PS)) c = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) u[q] = pl[q * S::PS + c];
 }
@@ -269,6 +283,7 @@ __device__ __forceinline__ void cell_of(const R* pl, int c, R u[4]) {
 template <class T>
 __device__ __forceinline__ void cell_hl(const float* pl, int c, float hi[4], float lo[4]) {
   using S = SmemT<T, float>;
+  if (!RHD_RING_OK(c, S::PS)) c = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     hi[q] = pl[q * S::PS + c];
@@ -364,18 +379,19 @@ __device__ __forceinline__ void column_cell(const StageArgs& A, int cx, int cy, 
   const int hs = halo_side(g, zg);
   double w[4];
   if (hs >= 0) {
-    const double* hp = halo_plane(A, hs, zg) + cx + g.n[0] * cy;
-    const size_t hq = (size_t)HALO_PLANES * g.n[0] * g.n[1];
-    w[0] = __ldg(hp);
-    w[1] = __dmul_rn(__ldg(hp + hq), inv_c);
-    w[2] = __dmul_rn(__ldg(hp + 2 * hq), inv_c);
-    w[3] = __dmul_rn(__ldg(hp + 3 * hq), inv_c);
+    const double* hb = A.halo[hs];
+    const long long hi = (halo_plane(A, hs, zg) - hb) + cx + (long long)g.n[0] * cy;
+    const long long hq = (long long)HALO_PLANES * g.n[0] * g.n[1];
+    w[0] = RHD_LDG(A.st, hb, hi, 4 * hq);
+    w[1] = __dmul_rn(RHD_LDG(A.st, hb, hi + hq, 4 * hq), inv_c);
+    w[2] = __dmul_rn(RHD_LDG(A.st, hb, hi + 2 * hq, 4 * hq), inv_c);
+    w[3] = __dmul_rn(RHD_LDG(A.st, hb, hi + 3 * hq, 4 * hq), inv_c);
   } else {
     const int idx = cx + g.n[0] * (cy + g.n[1] * zf);
-    w[0] = __ldg(A.yt[Y_ERAD] + idx);
-    w[1] = __dmul_rn(__ldg(A.yt[Y_FX] + idx), inv_c);
-    w[2] = __dmul_rn(__ldg(A.yt[Y_FY] + idx), inv_c);
-    const double Fz = __dmul_rn(__ldg(A.yt[Y_FZ] + idx), inv_c);
+    w[0] = RHD_LDG(A.st, A.yt[Y_ERAD], idx, g.ncell);
+    w[1] = __dmul_rn(RHD_LDG(A.st, A.yt[Y_FX], idx, g.ncell), inv_c);
+    w[2] = __dmul_rn(RHD_LDG(A.st, A.yt[Y_FY], idx, g.ncell), inv_c);
+    const double Fz = __dmul_rn(RHD_LDG(A.st, A.yt[Y_FZ], idx, g.ncell), inv_c);
     w[3] = fz ? -Fz : Fz;
   }
   const int side = GEN ? inflow_side(g, 2, zg) : -1;
@@ -426,6 +442,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 
   const Geometry& g = A.g;
   const Physics& ph = A.ph;
+#ifdef RHD_BOUNDS_CHECK
+  if (threadIdx.x == 0) s_chk_status = A.st;
+  __syncthreads();
+#endif
   const R chat = (R)ph.chat;
   const double chat6 = ph.chat * (1.0 / 6.0);
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -691,9 +711,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       double y[8];
       if (STAGE == 0) {
         // transport only: s(y) of eq. (yrsla) for E and the physical flux F
-        A.rate[0][idx] = rate[0];
+        RHD_ST(A.st, A.rate[0], idx, g.ncell, rate[0]);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) A.rate[1 + j][idx] = ph.c * rate[1 + j];
+        for (int j = 0; j < 3; ++j) RHD_ST(A.st, A.rate[1 + j], idx, g.ncell, ph.c * rate[1 + j]);
         if (bad) {
           atomicMin(&A.st->fail_key, ((unsigned long long)(A.cell_base + idx) << 8) | RHD_ERR_NONPHYSICAL);
           A.st->fail_step = A.step;
@@ -701,19 +721,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         }
       } else if (STAGE == 1) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) y[q] = A.yt[q][idx];
+        for (int q = 0; q < 8; ++q) y[q] = RHD_LD(A.st, A.yt[q], idx, g.ncell);
         y[Y_ERAD] += A.dt * rate[0];
 #pragma unroll
         for (int j = 0; j < 3; ++j) y[Y_FX + j] += A.dt * ph.c * rate[1 + j];
       } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) y[q] = 0.5 * (A.yn[q][idx] + A.yt[q][idx]);
+        for (int q = 0; q < 8; ++q)
+          y[q] = 0.5 * (RHD_LD(A.st, A.yn[q], idx, g.ncell) + RHD_LD(A.st, A.yt[q], idx, g.ncell));
         y[Y_ERAD] += 0.5 * A.dt * rate[0];
 #pragma unroll
         for (int j = 0; j < 3; ++j) y[Y_FX + j] += 0.5 * A.dt * ph.c * rate[1 + j];
       }
-      const double rho = A.rho[idx];
-      const double chi = A.kappa[idx] * rho;
+      const double rho = RHD_LD(A.st, A.rho, idx, g.ncell);
+      const double chi = RHD_LD(A.st, A.kappa, idx, g.ncell) * rho;
       int nn = 0, no = 0;
       int code = RHD_OK;
       // RK2-SSP (Sec. 4.2): no exchange in stage 1, the full dt f(y(n+1)) in
@@ -730,7 +751,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
             code = local_solve<MIXED, GEN>(ph, tdt, rho, chi, y, nn, no);
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) A.yo[q][idx] = y[q];
+        for (int q = 0; q < 8; ++q) RHD_ST(A.st, A.yo[q], idx, g.ncell, y[q]);
       }
       if (code != RHD_OK) {
         atomicMin(&A.st->fail_key, ((unsigned long long)(A.cell_base + idx) << 8) | (unsigned)code);

@@ -18,8 +18,12 @@ import numpy as np
 
 from . import build as _build
 
+# plane kinds of rhd_slab_planes_get / rhd_slab_planes_set
+(RHD_SLAB_BOUNDARY_LOW, RHD_SLAB_BOUNDARY_HIGH, RHD_SLAB_GHOSTS_LOW, RHD_SLAB_GHOSTS_HIGH,
+ RHD_SLAB_MATERIAL_LOW, RHD_SLAB_MATERIAL_ABOVE, RHD_SLAB_EPS_HIGH,
+ RHD_SLAB_EPS_BELOW) = range(8)
 RHD_OK, RHD_ERR_ARG, RHD_ERR_CUDA, RHD_ERR_NEWTON, RHD_ERR_OUTER, \
-    RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE = range(8)
+    RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE, RHD_ERR_BOUNDS = range(9)
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "newton", 4: "outer",
                 5: "nonphysical", 6: "timeout", 7: "state"}
 RHD_BC_PERIODIC, RHD_BC_REFLECT, RHD_BC_INFLOW, RHD_BC_HALO = 0, 1, 2, 3
@@ -124,6 +128,13 @@ SIGNATURES = {
     "rhd_profile": (ctypes.c_int, [_V, ctypes.c_int]),
     "rhd_profile_read": (ctypes.c_int, [_V, ctypes.POINTER(_I64), _D]),
     "rhd_launch_count": (_I64, [_V]),
+    "rhd_slab_plane_doubles": (_I64, [_V, ctypes.c_int]),
+    "rhd_slab_planes_get": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, _V, _I64,
+                                           ctypes.c_int]),
+    "rhd_slab_planes_set": (ctypes.c_int, [_V, ctypes.c_int, _V, _I64, ctypes.c_int]),
+    "rhd_slab_stage": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
+    "rhd_slab_status": (ctypes.c_int, [_V, ctypes.POINTER(rhd_step_info)]),
+    "rhd_slab_commit": (ctypes.c_int, [_V, ctypes.c_int]),
     "rhd_time": (ctypes.c_double, [_V]),
     "rhd_last_error": (ctypes.c_char_p, [_V]),
     "rhd_destroy": (None, [_V]),
@@ -344,8 +355,10 @@ class RHDContext:
                                       self.ncell, dev), self.h)
 
     def get_state(self, out=None):
+        """The state (10 fields) into `out`, or into a new array that starts as
+        NaN, so that a cell the library failed to write cannot pass as data."""
         if out is None:
-            out = np.empty(self.shape, dtype=np.float64)
+            out = np.full(self.shape, np.nan)
         ptr, dev = _ptr(out)
         _check(self.lib.rhd_state_get_all(self.h, ctypes.c_void_p(ptr),
                                           RHD_NFIELDS * self.ncell, dev), self.h)
@@ -353,7 +366,7 @@ class RHDContext:
 
     def get_field(self, field: int, out=None):
         if out is None:
-            out = np.empty(self.shape[1:], dtype=np.float64)
+            out = np.full(self.shape[1:], np.nan)
         ptr, dev = _ptr(out)
         _check(self.lib.rhd_state_get(self.h, field, ctypes.c_void_p(ptr),
                                       self.ncell, dev), self.h)
@@ -362,7 +375,7 @@ class RHDContext:
     def get_stage_field(self, field: int, out=None):
         """One evolved field of y(n+1/2) of the last step."""
         if out is None:
-            out = np.empty(self.shape[1:], dtype=np.float64)
+            out = np.full(self.shape[1:], np.nan)
         ptr, dev = _ptr(out)
         _check(self.lib.rhd_stage_get(self.h, field, ctypes.c_void_p(ptr), self.ncell, dev),
                self.h)
@@ -376,6 +389,39 @@ class RHDContext:
         d = info.as_dict()
         d["status"] = st
         return d
+
+    # ---- one z-slab stepped stage by stage by its own process
+    def slab_plane_doubles(self, what: int) -> int:
+        return int(self.lib.rhd_slab_plane_doubles(self.h, int(what)))
+
+    def slab_planes_get(self, what: int, stage: int, out):
+        """rhd_slab_planes_get into `out` (numpy array or torch tensor of
+        slab_plane_doubles(what) doubles)."""
+        ptr, dev = _ptr(out)
+        _check(self.lib.rhd_slab_planes_get(self.h, int(what), int(stage), ctypes.c_void_p(ptr),
+                                            int(out.size if isinstance(out, np.ndarray)
+                                                else out.numel()), dev), self.h)
+        return out
+
+    def slab_planes_set(self, what: int, src):
+        ptr, dev = _ptr(src)
+        _check(self.lib.rhd_slab_planes_set(self.h, int(what), ctypes.c_void_p(ptr),
+                                            int(src.size if isinstance(src, np.ndarray)
+                                                else src.numel()), dev), self.h)
+
+    def slab_stage(self, stage: int, dt: float = 0.0):
+        _check(self.lib.rhd_slab_stage(self.h, int(stage), float(dt)), self.h)
+
+    def slab_status(self) -> dict:
+        """rhd_slab_status: the slab's own status (not raised) and counts."""
+        info = rhd_step_info()
+        st = self.lib.rhd_slab_status(self.h, ctypes.byref(info))
+        d = info.as_dict()
+        d["status"] = st
+        return d
+
+    def slab_commit(self, commit: bool):
+        _check(self.lib.rhd_slab_commit(self.h, int(bool(commit))), self.h)
 
     def step_async(self, nsteps: int = 1, dt: float = 0.0):
         _check(self.lib.rhd_step_async(self.h, int(nsteps), float(dt)), self.h)
@@ -413,7 +459,7 @@ class RHDContext:
     def transport(self, out=None):
         """Rates (dE/dt, dFx/dt, dFy/dt, dFz/dt) of s(y), shape (4, nz, ny, nx)."""
         if out is None:
-            out = np.empty((4,) + self.shape[1:], dtype=np.float64)
+            out = np.full((4,) + self.shape[1:], np.nan)
         ptr, dev = _ptr(out)
         _check(self.lib.rhd_transport(self.h, ctypes.c_void_p(ptr), 4 * self.ncell, dev),
                self.h)
@@ -585,7 +631,7 @@ class RHDBatch:
 
     def get_state(self, prob: int, out=None):
         if out is None:
-            out = np.empty(self.shapes[prob], dtype=np.float64)
+            out = np.full(self.shapes[prob], np.nan)
         ptr, dev = _ptr(out)
         self._check(self.lib.rhd_batch_state_get(self.h, prob, ctypes.c_void_p(ptr),
                                                  RHD_NFIELDS * self.cells(prob), dev))

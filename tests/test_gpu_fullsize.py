@@ -34,7 +34,7 @@ def one_step(prob, U, precision="fp64"):
     with rhd.RHDContext(prob, precision, stream=torch.cuda.current_stream()) as ctx:
         ctx.set_state(Ud)
         info = ctx.step(1)
-        out = torch.empty_like(Ud)
+        out = torch.full_like(Ud, float("nan"))
         ctx.get_state(out)
     torch.cuda.synchronize()
     return out.cpu().numpy(), info["dt"]
@@ -96,7 +96,7 @@ def big(box):
         t0 = ctx.totals()
         info = ctx.step(1)
         t1 = ctx.totals()
-        out = torch.empty_like(Ud)
+        out = torch.full_like(Ud, float("nan"))
         ctx.get_state(out)
         dt = info["dt"]
     torch.cuda.synchronize()
@@ -160,7 +160,7 @@ def big_hydro(box):
         t0 = ctx.totals()
         info = ctx.hydro_step(1, dt)
         t1 = ctx.totals()
-        out = torch.empty_like(Ud)
+        out = torch.full_like(Ud, float("nan"))
         ctx.get_state(out)
     torch.cuda.synchronize()
     return prob, U, out.cpu().numpy(), dt, t0, t1, info

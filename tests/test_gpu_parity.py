@@ -155,7 +155,7 @@ def test_device_tensors_and_torch_stream(R):
         with R.RHDContext(prob, stream=torch.cuda.current_stream()) as ctx:
             ctx.set_state(Ud)
             ctx.step(3)
-            out = torch.empty_like(Ud)
+            out = torch.full_like(Ud, float("nan"))
             ctx.get_state(out)
     torch.cuda.synchronize()
     Uh, _ = run_gpu(R, prob, U, 3)

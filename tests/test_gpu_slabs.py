@@ -293,3 +293,136 @@ def test_hydro_failure_on_slabs_leaves_every_slab(R):
         assert info[k] == iw[k], k
     assert info["fail_stage"] in (3, 4) and np.array_equal(Us, U)
     assert all(t == 0.0 for t in times)
+
+
+# ---- slabs stepped stage by stage (rhd_slab_*: the per-process form)
+
+def stage_by_stage(R, prob, U, cuts, nsteps, dt, precision):
+    """The slabs of cuts advanced through the per-slab calls that a process
+    holding one slab makes, with the planes carried between the contexts
+    here (what decomp.py does between ranks): material and face factors once,
+    then per stage every slab's boundary planes into its neighbours' ghost
+    planes, the stage on every slab, the statuses combined, the commit."""
+    stream = torch.cuda.current_stream()
+    probs = R.slab_problems(prob, cuts)
+    ctxs = [R.RHDContext(q, precision, stream=stream) for q in probs]
+    n = len(ctxs)
+    halo = [(q["bc"][2][0] == "halo", q["bc"][2][1] == "halo") for q in probs]
+
+    def get(c, what, stage=1):
+        buf = torch.empty(c.slab_plane_doubles(what), dtype=torch.float64, device="cuda")
+        return c.slab_planes_get(what, stage, buf)
+
+    try:
+        for c, z0, z1 in zip(ctxs, cuts, cuts[1:]):
+            c.set_state(np.ascontiguousarray(U[:, z0:z1]))
+        if prob.get("hll_mode", "tau") == "tau":
+            for s in range(n):
+                if halo[s][1]:
+                    ctxs[s].slab_planes_set(R.RHD_SLAB_MATERIAL_ABOVE,
+                                            get(ctxs[(s + 1) % n], R.RHD_SLAB_MATERIAL_LOW))
+            for s in range(n):
+                if halo[s][0]:
+                    ctxs[s].slab_planes_set(R.RHD_SLAB_EPS_BELOW,
+                                            get(ctxs[(s - 1) % n], R.RHD_SLAB_EPS_HIGH))
+        done, status = 0, R.RHD_OK
+        for _ in range(nsteps):
+            for stage in (1, 2):
+                low = [get(c, R.RHD_SLAB_BOUNDARY_LOW, stage) if h[0] or h[1] else None
+                       for c, h in zip(ctxs, halo)]
+                high = [get(c, R.RHD_SLAB_BOUNDARY_HIGH, stage) if h[0] or h[1] else None
+                        for c, h in zip(ctxs, halo)]
+                for s in range(n):
+                    if halo[s][0]:
+                        ctxs[s].slab_planes_set(R.RHD_SLAB_GHOSTS_LOW, high[(s - 1) % n])
+                    if halo[s][1]:
+                        ctxs[s].slab_planes_set(R.RHD_SLAB_GHOSTS_HIGH, low[(s + 1) % n])
+                for c in ctxs:
+                    c.slab_stage(stage, dt)
+            status = max(c.slab_status()["status"] for c in ctxs)
+            for c in ctxs:
+                c.slab_commit(status == R.RHD_OK)
+            if status != R.RHD_OK:
+                break
+            done += 1
+        Us = np.concatenate([c.get_state() for c in ctxs], axis=1)
+    finally:
+        for c in ctxs:
+            c.close()
+    return Us, done, status
+
+
+STAGE_CASES = [
+    ((37, 23, 19), [0, 9, 19], dict(hll_mode="tau"), "fp64", 4),
+    ((24, 20, 18), [0, 5, 11, 18], dict(hll_mode="tau", walls=True), "mixed", 3),
+    ((20, 17, 16), [0, 3, 9, 16], dict(hll_mode="none", reconstruction="ppm"), "fp64", 3),
+    ((20, 17, 16), [0, 16], dict(hll_mode="tau"), "fp64", 2),
+]
+
+
+@pytest.mark.parametrize("ci", range(len(STAGE_CASES)), ids=[str(c[1]) for c in STAGE_CASES])
+def test_stage_by_stage_slabs_step_like_the_whole_grid(R, ci):
+    shape, cuts, opts, precision, nsteps = STAGE_CASES[ci]
+    prob, U = case_problem(shape, opts)
+    dt = R.rhd_default_dt(R.params_from_problem(prob))
+    Uw, iw = whole(R, prob, U, nsteps, dt, precision)
+    assert iw["status"] == R.RHD_OK
+    Us, done, status = stage_by_stage(R, prob, U, cuts, nsteps, dt, precision)
+    assert status == R.RHD_OK and done == nsteps
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), (STAGE_CASES[ci], f)
+
+
+def test_stage_by_stage_failure_is_applied_on_no_slab(R):
+    """A step far beyond the transport's CFL bound fails on some slab: no
+    slab commits it, every slab keeps its state."""
+    prob, U, _ = I.turbulent_box_3d(shape=(24, 20, 18), hll_mode="none")
+    dt = 60.0 * R.rhd_default_dt(R.params_from_problem(prob))
+    Us, done, status = stage_by_stage(R, prob, U, [0, 6, 12, 18], 2, dt, "fp64")
+    assert status != R.RHD_OK and done == 0
+    assert np.array_equal(Us, U)
+
+
+def test_stage_calls_out_of_order_are_refused(R):
+    prob, U, _ = I.turbulent_box_3d(shape=(12, 10, 9))
+    q = R.slab_problems(prob, [0, 9])[0]
+    with R.RHDContext(q) as c:
+        c.set_state(U)
+        with pytest.raises(R.RHDError):
+            c.slab_stage(2)  # stage 2 before stage 1
+        with pytest.raises(R.RHDError):
+            c.slab_stage(1)  # TAU factors: the neighbours' planes are not set
+        with R.RHDContext(prob) as plain:
+            plain.set_state(U)
+            with pytest.raises(R.RHDError):
+                plain.slab_stage(1)  # not a slab
+
+
+def test_decomp_step_on_one_rank(R):
+    """decomp.step through a one-rank process group: the whole periodic box as
+    one slab, its ghost planes its own opposite boundary planes."""
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_2404_08247_gb300 import decomp
+    prob, U, _ = I.turbulent_box_3d(shape=(20, 16, 14))
+    Uw, _ = whole(R, prob, U, 3, 0.0, "fp64")
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        q = R.slab_problems(prob, [0, prob["n"][2]])[0]
+        with R.RHDContext(q, stream=torch.cuda.current_stream()) as c:
+            c.set_state(U)
+            slab = decomp.CtxSlab(c, "cuda")
+            decomp.exchange_material(slab, dist)
+            res = decomp.step(slab, dist, 3)
+            assert res == {"steps_done": 3, "status": R.RHD_OK}
+            Us = c.get_state()
+    finally:
+        dist.destroy_process_group()
+    assert np.array_equal(Us, Uw)
