@@ -9,8 +9,12 @@
 
 namespace rhd {
 
+#ifndef RHD_STAGE_MINB
+#define RHD_STAGE_MINB 2  // resident blocks per SM (128 registers per thread at 256 threads)
+#endif
 template <int STAGE, int NDIM, typename R, bool GEN, bool PPM>
-__global__ void __launch_bounds__(Tile<NDIM>::NT, 2) stage_kernel(const StageArgs A) {
+__global__ void __launch_bounds__(Tile<NDIM>::NT, NDIM == 3 ? RHD_STAGE_MINB : 2)
+    stage_kernel(const StageArgs A) {
   using T = std::conditional_t<PPM, TilePPM<NDIM>, Tile<NDIM>>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_skip;

@@ -37,8 +37,16 @@ struct DefaultTileOf;
 // 3-D: 8 planes per block.  Longer z-chunks load fewer halo planes, but the
 // per-block cost varies with the local physics (iteration counts), and short
 // chunks balance the SMs better (256^3: 8 planes 2.6 % faster than 32).
+// Build-time shape of the 3-D tile (rows TY of 32 cells, LZ planes per
+// block) and the blocks per SM its stage kernels are compiled for.
+#ifndef RHD_TILE3_TY
+#define RHD_TILE3_TY 8
+#endif
+#ifndef RHD_TILE3_LZ
+#define RHD_TILE3_LZ 8
+#endif
 template <>
-struct DefaultTileOf<3> { using type = TileT<3, 32, 8, 8>; };
+struct DefaultTileOf<3> { using type = TileT<3, 32, RHD_TILE3_TY, RHD_TILE3_LZ>; };
 template <>
 struct DefaultTileOf<2> { using type = TileT<2, 32, 8, 1>; };
 template <>
