@@ -401,14 +401,20 @@ enum {
   RHD_SLAB_MATERIAL_LOW = 4,   /* get: kappa, then rho, of plane 0 */
   RHD_SLAB_MATERIAL_ABOVE = 5, /* set: the MATERIAL_LOW of the slab above */
   RHD_SLAB_EPS_HIGH = 6,       /* get: TAU factors of the top face (needs MATERIAL_ABOVE) */
-  RHD_SLAB_EPS_BELOW = 7       /* set: the EPS_HIGH of the slab below */
+  RHD_SLAB_EPS_BELOW = 7,      /* set: the EPS_HIGH of the slab below */
+  RHD_SLAB_PRIM_BOUNDARY_LOW = 8,   /* get: rho, vx, vy, vz, p of the lowest `depth` planes
+                                       of the hydrodynamic stage (after phase 0 or 2) */
+  RHD_SLAB_PRIM_BOUNDARY_HIGH = 9,  /* get: the same of the highest `depth` planes */
+  RHD_SLAB_PRIM_GHOSTS_LOW = 10,    /* set: the primitive ghost planes below */
+  RHD_SLAB_PRIM_GHOSTS_HIGH = 11    /* set: the primitive ghost planes above */
 };
 
 /* Doubles that a plane kind holds for this slab: 4 depth n0 n1 for the
  * boundary and ghost planes (depth 2 with PLM faces, 3 with PPM), laid out
- * [field E, Fx, Fy, Fz][plane, in z order][n0 n1]; 2 n0 n1 for the material
- * planes; n0 n1 for the TAU factors.  -1 for a bad kind or a grid that is not
- * 3-D. */
+ * [field E, Fx, Fy, Fz][plane, in z order][n0 n1]; 5 depth n0 n1 for the
+ * primitive planes ([rho, vx, vy, vz, p][plane][n0 n1]); 2 n0 n1 for the
+ * material planes; n0 n1 for the TAU factors.  -1 for a bad kind or a grid
+ * that is not 3-D. */
 int64_t rhd_slab_plane_doubles(const rhd_ctx* ctx, int what);
 
 /* Copy planes of kind `what` (a get kind) into dst (count doubles, host or
@@ -437,8 +443,30 @@ rhd_status rhd_slab_stage(rhd_ctx* ctx, int stage, double dt);
 rhd_status rhd_slab_status(rhd_ctx* ctx, rhd_step_info* info);
 
 /* After rhd_slab_status: commit != 0 makes y(n+1) the state and advances the
- * time by dt; 0 keeps y(n) (another slab failed). */
+ * time by dt; 0 keeps y(n) (another slab failed).  After a hydrodynamic step
+ * commit != 0 copies its staged result into the state (one more launch). */
 rhd_status rhd_slab_commit(rhd_ctx* ctx, int commit);
+
+/* The hydrodynamic step of a slab (RK2-SSP with HLLC faces, as
+ * rhd_hydro_step_slabs), phase by phase:
+ *   rhd_slab_hydro_speed on every slab, the largest smax of all slabs gives
+ *     dt = cfl_hydro / smax (the whole grid's CFL step);
+ *   rhd_slab_hydro_phase(0, dt): primitives of the state; exchange the
+ *     PRIM_BOUNDARY planes into the neighbours' PRIM_GHOSTS;
+ *     rhd_slab_hydro_phase(1): face fluxes and stage 1;
+ *   rhd_slab_hydro_phase(2): primitives of stage 1; exchange again;
+ *     rhd_slab_hydro_phase(3): face fluxes and stage 2, staged;
+ *   rhd_slab_status, combine, rhd_slab_commit.
+ * Periodic and reflecting x and y axes only (no inflow faces). */
+
+/* *smax: the slab's largest sum_d (|v_d| + a)/dx_d (+inf if a cell has
+ * rho <= 0 or p <= 0).  Synchronises the stream. */
+rhd_status rhd_slab_hydro_speed(rhd_ctx* ctx, double* smax);
+
+/* Run hydrodynamic phase 0 .. 3 (phase 0 takes dt > 0 and starts the step;
+ * later phases use it) on the slab's stream, reading the primitive ghost
+ * planes set last.  RHD_ERR_STATE out of order. */
+rhd_status rhd_slab_hydro_phase(rhd_ctx* ctx, int phase, double dt);
 
 /* Number of kernels this context has launched since rhd_init. */
 int64_t rhd_launch_count(const rhd_ctx* ctx);

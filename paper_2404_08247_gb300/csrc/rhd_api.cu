@@ -1597,6 +1597,22 @@ static rhd_status slab_halo(rhd_ctx* c) {
   return RHD_OK;
 }
 
+// the hydrodynamic scratch and the primitives' halo buffer of a slab
+// [2 sides][5 fields rho, vx, vy, vz, p][HALO_PLANES][n0 n1]
+static rhd_status slab_hyd_halo(rhd_ctx* c) {
+  rhd_status s = hydro_alloc(c);
+  if (s != RHD_OK) return s;
+  if (c->hyd_halo) return RHD_OK;
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  cudaError_t e = cudaMalloc(&c->hyd_halo, sizeof(double) * 2 * 5 * HALO_PLANES * P);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->hyd_halo = nullptr;
+    return fail(c, RHD_ERR_CUDA, "halo buffer: %s", cudaGetErrorString(e));
+  }
+  return RHD_OK;
+}
+
 static int slab_depth(const rhd_ctx* c) {
   return c->p.reconstruction == RHD_RECON_PLM ? 2 : 3;
 }
@@ -1615,6 +1631,10 @@ int64_t rhd_slab_plane_doubles(const rhd_ctx* c, int what) {
     case RHD_SLAB_MATERIAL_ABOVE: return 2 * P;
     case RHD_SLAB_EPS_HIGH:
     case RHD_SLAB_EPS_BELOW: return P;
+    case RHD_SLAB_PRIM_BOUNDARY_LOW:
+    case RHD_SLAB_PRIM_BOUNDARY_HIGH:
+    case RHD_SLAB_PRIM_GHOSTS_LOW:
+    case RHD_SLAB_PRIM_GHOSTS_HIGH: return 5 * slab_depth(c) * P;
     default: return -1;
   }
 }
@@ -1629,6 +1649,7 @@ static rhd_status slab_check(rhd_ctx* c, int what, const void* buf, int64_t coun
   if (count != want)
     return fail(c, RHD_ERR_ARG, "count %lld != %lld doubles", (long long)count, (long long)want);
   CUDA_TRY(c, cudaSetDevice(c->device));
+  if (what >= RHD_SLAB_PRIM_BOUNDARY_LOW) return slab_hyd_halo(c);
   return slab_halo(c);
 }
 
@@ -1671,6 +1692,16 @@ rhd_status rhd_slab_planes_get(rhd_ctx* c, int what, int stage, double* dst, int
     }
     CUDA_TRY(c, cudaMemcpyAsync(dst, c->eps[2] + (size_t)(c->g.n[2] - 1) * P,
                                 sizeof(double) * P, kind, c->stream));
+  } else if (what == RHD_SLAB_PRIM_BOUNDARY_LOW || what == RHD_SLAB_PRIM_BOUNDARY_HIGH) {
+    // the primitives of the current hydrodynamic stage (after phase 0 or 2)
+    if (c->slab_phase != 10 && c->slab_phase != 12)
+      return fail(c, RHD_ERR_STATE, "primitive planes: run hydrodynamic phase 0 or 2 first");
+    const int depth = slab_depth(c);
+    const size_t z0 = what == RHD_SLAB_PRIM_BOUNDARY_LOW ? 0 : (size_t)c->g.n[2] - depth;
+    for (int q = 0; q < 5; ++q)
+      CUDA_TRY(c, cudaMemcpyAsync(dst + (size_t)q * depth * P,
+                                  c->hyd_w + (size_t)q * c->ncell + z0 * P,
+                                  sizeof(double) * depth * P, kind, c->stream));
   } else {
     return fail(c, RHD_ERR_ARG, "plane kind %d is set, not read", what);
   }
@@ -1706,6 +1737,17 @@ rhd_status rhd_slab_planes_set(rhd_ctx* c, int what, const double* src, int64_t 
     if (c->p.bc[2][0] != RHD_BC_HALO) return fail(c, RHD_ERR_ARG, "the low face is not HALO");
     CUDA_TRY(c, cudaMemcpyAsync(hk + 2 * P, src, sizeof(double) * P, kind, c->stream));
     c->slab_eps_below = true;
+  } else if (what == RHD_SLAB_PRIM_GHOSTS_LOW || what == RHD_SLAB_PRIM_GHOSTS_HIGH) {
+    const int side = what == RHD_SLAB_PRIM_GHOSTS_LOW ? 0 : 1;
+    if (c->p.bc[2][side] != RHD_BC_HALO)
+      return fail(c, RHD_ERR_ARG, "ghost planes for a face that is not HALO");
+    const int depth = slab_depth(c);
+    const size_t i0 = side == 0 ? HALO_PLANES - depth : 0;
+    double* h = c->hyd_halo + (size_t)side * 5 * HALO_PLANES * P;
+    for (int q = 0; q < 5; ++q)
+      CUDA_TRY(c, cudaMemcpyAsync(h + ((size_t)q * HALO_PLANES + i0) * P,
+                                  src + (size_t)q * depth * P, sizeof(double) * depth * P, kind,
+                                  c->stream));
   } else {
     return fail(c, RHD_ERR_ARG, "plane kind %d is read, not set", what);
   }
@@ -1782,7 +1824,8 @@ rhd_status rhd_slab_stage(rhd_ctx* c, int stage, double dt) {
 
 rhd_status rhd_slab_status(rhd_ctx* c, rhd_step_info* info) {
   if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
-  if (c->slab_phase != 2) return fail(c, RHD_ERR_STATE, "no slab step has run both stages");
+  if (c->slab_phase != 2 && c->slab_phase != 13)
+    return fail(c, RHD_ERR_STATE, "no slab step has run all its stages");
   CUDA_TRY(c, cudaSetDevice(c->device));
   CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DevStatus),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -1808,18 +1851,95 @@ rhd_status rhd_slab_status(rhd_ctx* c, rhd_step_info* info) {
     info->sum_outer = (int64_t)st.sum_outer;
     info->dt = c->slab_dt;
   }
-  c->slab_phase = 3;
+  c->slab_phase = c->slab_phase == 2 ? 3 : 14;
   return code;
 }
 
 rhd_status rhd_slab_commit(rhd_ctx* c, int commit) {
   if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
-  if (c->slab_phase != 3) return fail(c, RHD_ERR_STATE, "the slab step's status was not read");
+  if (c->slab_phase != 3 && c->slab_phase != 14)
+    return fail(c, RHD_ERR_STATE, "the slab step's status was not read");
+  if (c->slab_phase == 14) {
+    // hydrodynamic step: phase 4 copies the staged result into the state
+    c->slab_phase = 0;
+    if (!commit) return RHD_OK;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    HydroBufs b = hydro_bufs(c);
+    CUDA_TRY(c, launch_hydro_phase(4, c->g, c->p.gamma, c->p.reconstruction, c->slab_dt, b,
+                                   c->d_status, 0, c->stream));
+    c->launches += 1;
+    c->t += c->slab_dt;
+    c->eps_dirty = true;  // rho has changed
+    c->slab_mat_above = c->slab_eps_below = false;
+    return RHD_OK;
+  }
   if (commit) {
     c->cur ^= 1;
     c->t += c->slab_dt;
   }
   c->slab_phase = 0;
+  return RHD_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+rhd_status rhd_slab_hydro_speed(rhd_ctx* c, double* smax) {
+  if (!c || !smax) return fail(c, RHD_ERR_ARG, "ctx or smax is NULL");
+  if (!has_halo(c)) return fail(c, RHD_ERR_ARG, "the context has no HALO face");
+  if (c->pending || c->slab_phase != 0)
+    return fail(c, RHD_ERR_STATE, "a step is in progress");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  rhd_status s = slab_hyd_halo(c);
+  if (s != RHD_OK) return s;
+  HydroBufs b = hydro_bufs(c);
+  CUDA_TRY(c, launch_hydro_speed(c->g, c->p.gamma, b, c->stream));
+  c->launches += 1;
+  unsigned long long bits = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&bits, c->hyd_bits, sizeof(bits), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  memcpy(smax, &bits, sizeof(*smax));
+  return RHD_OK;
+}
+
+rhd_status rhd_slab_hydro_phase(rhd_ctx* c, int phase, double dt) {
+  if (!c) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+  if (!has_halo(c)) return fail(c, RHD_ERR_ARG, "the context has no HALO face");
+  if (c->pending) return fail(c, RHD_ERR_STATE, "a step batch is pending");
+  if (c->fields_set != kAllFields)
+    return fail(c, RHD_ERR_STATE, "not every field has been set (mask 0x%x)", c->fields_set);
+  if (phase < 0 || phase > 3) return fail(c, RHD_ERR_ARG, "phase must be 0 .. 3");
+  if ((phase == 0 && c->slab_phase != 0) || (phase > 0 && c->slab_phase != 9 + phase))
+    return fail(c, RHD_ERR_STATE, "hydrodynamic phase %d out of order", phase);
+  for (int d = 0; d < 2; ++d)
+    if (c->p.bc[d][0] == RHD_BC_INFLOW || c->p.bc[d][1] == RHD_BC_INFLOW)
+      return fail(c, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
+  if (c->p.bc[2][0] == RHD_BC_INFLOW || c->p.bc[2][1] == RHD_BC_INFLOW)
+    return fail(c, RHD_ERR_ARG, "the hydrodynamic step takes periodic and reflecting axes");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  rhd_status s = slab_hyd_halo(c);
+  if (s != RHD_OK) return s;
+  if (phase == 0) {
+    if (!(dt > 0.0) || !std::isfinite(dt))
+      return fail(c, RHD_ERR_ARG, "dt must be positive and finite (rhd_slab_hydro_speed "
+                  "gives the CFL bound of the slab)");
+    CUDA_TRY(c, launch_status_reset(c->d_status, c->stream));
+    c->launches += 1;
+    c->slab_dt = dt;
+  }
+  const size_t P = (size_t)c->g.n[0] * c->g.n[1];
+  HydroBufs b = hydro_bufs(c);
+  b.halo[0] = c->hyd_halo;
+  b.halo[1] = c->hyd_halo + (size_t)5 * HALO_PLANES * P;
+  b.cell_base = 0;
+  CUDA_TRY(c, launch_hydro_phase(phase, c->g, c->p.gamma, c->p.reconstruction, c->slab_dt, b,
+                                 c->d_status, 0, c->stream));
+  c->launches += phase == 1 || phase == 3 ? 1 + c->p.ndim : 1;
+  c->slab_phase = 10 + phase;
   return RHD_OK;
 }
 

@@ -57,6 +57,20 @@ class CtxSlab:
     def commit(self, ok: bool):
         self.ctx.slab_commit(ok)
 
+    # the hydrodynamic step and the split (Sec. 3.1)
+    def hydro_speed(self) -> float:
+        return self.ctx.slab_hydro_speed()
+
+    def hydro_phase(self, phase: int, dt: float):
+        self.ctx.slab_hydro_phase(phase, dt)
+
+    @property
+    def cfl_hydro(self) -> float:
+        return float(self.ctx.prob.get("cfl_hydro", 0.3))
+
+    def radiation_dt(self) -> float:
+        return R.rhd_default_dt(R.params_from_problem(self.ctx.prob))
+
 
 def neighbours(rank: int, world: int, low: bool, high: bool):
     """Ranks of the slabs below and above (None where the face is not HALO);
@@ -141,3 +155,73 @@ def step(slab, dist, nsteps: int = 1, dt: float = 0.0, group=None) -> dict:
         if worst != R.RHD_OK:
             return {"steps_done": k, "status": worst}
     return {"steps_done": nsteps, "status": R.RHD_OK}
+
+
+def _reduce(dist, x, op, dev, group):
+    """x reduced over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op, group=group)
+    return float(t.item())
+
+
+def _status_device(slab, dist, group):
+    if dist is not None and dist.get_backend(group) == "nccl":
+        return getattr(slab, "device", "cpu")
+    return "cpu"
+
+
+def hydro_step(slab, dist, nsteps: int = 1, dt: float = 0.0, group=None) -> dict:
+    """nsteps hydrodynamic steps (RK2-SSP, HLLC faces) of the decomposed grid:
+    the primitives' ghost planes exchanged before each stage's face fluxes;
+    dt <= 0: before each step the whole grid's CFL step, cfl_hydro over the
+    largest signal-speed bound of any slab.  A step that failed on any slab
+    is committed on none.  Returns {"steps_done", "status", "dt"}."""
+    dev = _status_device(slab, dist, group)
+    h = dt
+    for k in range(nsteps):
+        if not (dt > 0.0):
+            smax = _reduce(dist, slab.hydro_speed(), dist.ReduceOp.MAX if dist else None,
+                           dev, group)
+            if not (smax > 0.0) or smax == float("inf") or smax != smax:
+                return {"steps_done": k, "status": R.RHD_ERR_NONPHYSICAL, "dt": h}
+            h = slab.cfl_hydro / smax
+        slab.hydro_phase(0, h)
+        exchange(slab, dist, R.RHD_SLAB_PRIM_BOUNDARY_HIGH, R.RHD_SLAB_PRIM_BOUNDARY_LOW,
+                 R.RHD_SLAB_PRIM_GHOSTS_LOW, R.RHD_SLAB_PRIM_GHOSTS_HIGH, 1, group)
+        slab.hydro_phase(1, h)
+        slab.hydro_phase(2, h)
+        exchange(slab, dist, R.RHD_SLAB_PRIM_BOUNDARY_HIGH, R.RHD_SLAB_PRIM_BOUNDARY_LOW,
+                 R.RHD_SLAB_PRIM_GHOSTS_LOW, R.RHD_SLAB_PRIM_GHOSTS_HIGH, 1, group)
+        slab.hydro_phase(3, h)
+        worst = slab.status()
+        if dist is not None:
+            worst = int(_reduce(dist, worst, dist.ReduceOp.MAX, dev, group))
+        slab.commit(worst == R.RHD_OK)
+        if worst != R.RHD_OK:
+            return {"steps_done": k, "status": worst, "dt": h}
+    return {"steps_done": nsteps, "status": R.RHD_OK, "dt": h}
+
+
+def split_step(slab, dist, nsteps: int = 1, dt_h: float = 0.0, group=None) -> dict:
+    """nsteps operator-split steps (Sec. 3.1): one hydrodynamic step of dt_h
+    (<= 0: the CFL step), then ceil(dt_h / dt_rad) radiation steps of
+    dt_h / nsub (dt_rad the radiation step of rhd_default_dt), the material
+    planes exchanged again after the hydrodynamic step has moved rho.
+    Returns {"steps_done", "status", "substeps"}."""
+    import math
+    subs = []
+    for k in range(nsteps):
+        r = hydro_step(slab, dist, 1, dt_h, group)
+        if r["status"] != R.RHD_OK:
+            return {"steps_done": k, "status": r["status"], "substeps": subs}
+        h = r["dt"]
+        nsub = max(1, math.ceil(h / slab.radiation_dt() - 1e-12))
+        exchange_material(slab, dist, group)
+        r = step(slab, dist, nsub, h / nsub, group)
+        subs.append(nsub)
+        if r["status"] != R.RHD_OK:
+            return {"steps_done": k, "status": r["status"], "substeps": subs}
+    return {"steps_done": nsteps, "status": R.RHD_OK, "substeps": subs}

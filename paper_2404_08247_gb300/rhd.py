@@ -21,7 +21,8 @@ from . import build as _build
 # plane kinds of rhd_slab_planes_get / rhd_slab_planes_set
 (RHD_SLAB_BOUNDARY_LOW, RHD_SLAB_BOUNDARY_HIGH, RHD_SLAB_GHOSTS_LOW, RHD_SLAB_GHOSTS_HIGH,
  RHD_SLAB_MATERIAL_LOW, RHD_SLAB_MATERIAL_ABOVE, RHD_SLAB_EPS_HIGH,
- RHD_SLAB_EPS_BELOW) = range(8)
+ RHD_SLAB_EPS_BELOW, RHD_SLAB_PRIM_BOUNDARY_LOW, RHD_SLAB_PRIM_BOUNDARY_HIGH,
+ RHD_SLAB_PRIM_GHOSTS_LOW, RHD_SLAB_PRIM_GHOSTS_HIGH) = range(12)
 RHD_OK, RHD_ERR_ARG, RHD_ERR_CUDA, RHD_ERR_NEWTON, RHD_ERR_OUTER, \
     RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE, RHD_ERR_BOUNDS = range(9)
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "newton", 4: "outer",
@@ -135,6 +136,8 @@ SIGNATURES = {
     "rhd_slab_stage": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "rhd_slab_status": (ctypes.c_int, [_V, ctypes.POINTER(rhd_step_info)]),
     "rhd_slab_commit": (ctypes.c_int, [_V, ctypes.c_int]),
+    "rhd_slab_hydro_speed": (ctypes.c_int, [_V, _D]),
+    "rhd_slab_hydro_phase": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "rhd_time": (ctypes.c_double, [_V]),
     "rhd_last_error": (ctypes.c_char_p, [_V]),
     "rhd_destroy": (None, [_V]),
@@ -422,6 +425,14 @@ class RHDContext:
 
     def slab_commit(self, commit: bool):
         _check(self.lib.rhd_slab_commit(self.h, int(bool(commit))), self.h)
+
+    def slab_hydro_speed(self) -> float:
+        smax = ctypes.c_double(0.0)
+        _check(self.lib.rhd_slab_hydro_speed(self.h, ctypes.byref(smax)), self.h)
+        return smax.value
+
+    def slab_hydro_phase(self, phase: int, dt: float = 0.0):
+        _check(self.lib.rhd_slab_hydro_phase(self.h, int(phase), float(dt)), self.h)
 
     def step_async(self, nsteps: int = 1, dt: float = 0.0):
         _check(self.lib.rhd_step_async(self.h, int(nsteps), float(dt)), self.h)

@@ -192,3 +192,100 @@ def test_one_periodic_slab_exchanges_with_itself():
     top planes and its high ghosts its bottom planes (a copy, no transfer)."""
     res = run(1, True, 2)
     np.testing.assert_array_equal(res[0][0], whole_grid(2, True))
+
+
+# ---- the hydrodynamic step's schedule (five primitive fields, the CFL step)
+
+CFL_H = 0.3
+
+
+class FakeHydro(FakeSlab):
+    """The five primitive fields (here the state itself) of planes z0..z1,
+    stepped by the z-stencil in the RK2-SSP phases of the hydrodynamic
+    step; the signal-speed bound is the largest |u| of the slab."""
+
+    def __init__(self, z0, z1, low, high):
+        super().__init__(z0, z1, low, high)
+        self.u = hydro_state()[:, z0:z1].copy()
+
+    def buffer(self, what):
+        n = SHAPE[2] * SHAPE[3]
+        return torch.empty(5 * DEPTH * n, dtype=torch.float64)
+
+    def planes_get(self, what, stage):
+        out = self.w[:, :DEPTH] if what == R.RHD_SLAB_PRIM_BOUNDARY_LOW else self.w[:, -DEPTH:]
+        return torch.from_numpy(np.ascontiguousarray(out).reshape(-1).copy())
+
+    def planes_set(self, what, buf):
+        a = buf.numpy().copy().reshape(5, DEPTH, SHAPE[2], SHAPE[3])
+        if what == R.RHD_SLAB_PRIM_GHOSTS_LOW:
+            self.glo = a
+        else:
+            self.ghi = a
+
+    def hydro_speed(self):
+        return float(np.abs(self.u).max())
+
+    cfl_hydro = CFL_H
+
+    def hydro_phase(self, phase, dt):
+        if phase in (0, 2):
+            self.w = self.u if phase == 0 else self.u1
+            self.glo = self.ghi = None
+            return
+        L = stencil(extend(self.w, self.glo if self.low else None,
+                           self.ghi if self.high else None))
+        if phase == 1:
+            self.u1 = self.u + dt * L
+        else:
+            self.staged = 0.5 * (self.u + self.u1 + dt * L)
+
+    def status(self):
+        return R.RHD_OK
+
+    def commit(self, ok):
+        if ok:
+            self.u = self.staged
+
+
+def hydro_state():
+    return np.random.default_rng(5).standard_normal((5,) + SHAPE[1:])
+
+
+def whole_hydro(nsteps, periodic):
+    u = hydro_state()
+    for _ in range(nsteps):
+        h = CFL_H / np.abs(u).max()
+        ext = lambda v: extend(v, v[:, -DEPTH:] if periodic else None,  # noqa: E731
+                               v[:, :DEPTH] if periodic else None)
+        u1 = u + h * stencil(ext(u))
+        u = 0.5 * (u + u1 + h * stencil(ext(u1)))
+    return u
+
+
+def _hydro_worker(rank, world, port, periodic, nsteps, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    cuts = np.linspace(0, SHAPE[1], world + 1).astype(int)
+    slab = FakeHydro(cuts[rank], cuts[rank + 1], periodic or rank > 0,
+                     periodic or rank < world - 1)
+    res = decomp.hydro_step(slab, dist, nsteps)
+    out[rank] = (slab.u, res)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,periodic", [(2, True), (3, False)])
+def test_decomposed_hydro_step_equals_whole_grid(world, periodic):
+    """The primitives' ghost planes before both face phases, and the CFL step
+    of the whole grid (the largest bound of any rank) on every rank."""
+    nsteps = 3
+    port = _free_port()
+    manager = mp.Manager()
+    out = manager.dict()
+    mp.spawn(_hydro_worker, args=(world, port, periodic, nsteps, out), nprocs=world,
+             join=True)
+    u = np.concatenate([out[r][0] for r in range(world)], axis=1)
+    np.testing.assert_array_equal(u, whole_hydro(nsteps, periodic))
+    assert all(out[r][1]["steps_done"] == nsteps for r in range(world))

@@ -426,3 +426,100 @@ def test_decomp_step_on_one_rank(R):
     finally:
         dist.destroy_process_group()
     assert np.array_equal(Us, Uw)
+
+
+def hydro_stage_by_stage(R, prob, U, cuts, nsteps, precision="fp64"):
+    """The hydrodynamic step of the slabs through the per-slab calls: the
+    CFL step from the largest bound of any slab, then per phase pair the
+    primitives' boundary planes into the neighbours' ghost planes."""
+    stream = torch.cuda.current_stream()
+    probs = R.slab_problems(prob, cuts)
+    ctxs = [R.RHDContext(q, precision, stream=stream) for q in probs]
+    n = len(ctxs)
+    halo = [(q["bc"][2][0] == "halo", q["bc"][2][1] == "halo") for q in probs]
+
+    def get(c, what):
+        buf = torch.empty(c.slab_plane_doubles(what), dtype=torch.float64, device="cuda")
+        return c.slab_planes_get(what, 1, buf)
+
+    def swap():
+        low = [get(c, R.RHD_SLAB_PRIM_BOUNDARY_LOW) for c in ctxs]
+        high = [get(c, R.RHD_SLAB_PRIM_BOUNDARY_HIGH) for c in ctxs]
+        for s in range(n):
+            if halo[s][0]:
+                ctxs[s].slab_planes_set(R.RHD_SLAB_PRIM_GHOSTS_LOW, high[(s - 1) % n])
+            if halo[s][1]:
+                ctxs[s].slab_planes_set(R.RHD_SLAB_PRIM_GHOSTS_HIGH, low[(s + 1) % n])
+
+    try:
+        for c, z0, z1 in zip(ctxs, cuts, cuts[1:]):
+            c.set_state(np.ascontiguousarray(U[:, z0:z1]))
+        for _ in range(nsteps):
+            smax = max(c.slab_hydro_speed() for c in ctxs)
+            h = prob.get("cfl_hydro", 0.3) / smax
+            for c in ctxs:
+                c.slab_hydro_phase(0, h)
+            swap()
+            for c in ctxs:
+                c.slab_hydro_phase(1, h)
+            for c in ctxs:
+                c.slab_hydro_phase(2, h)
+            swap()
+            for c in ctxs:
+                c.slab_hydro_phase(3, h)
+            status = max(c.slab_status()["status"] for c in ctxs)
+            for c in ctxs:
+                c.slab_commit(status == R.RHD_OK)
+            assert status == R.RHD_OK
+        Us = np.concatenate([c.get_state() for c in ctxs], axis=1)
+    finally:
+        for c in ctxs:
+            c.close()
+    return Us
+
+
+@pytest.mark.parametrize("recon", ["plm", "ppm"])
+def test_stage_by_stage_hydro_slabs_step_like_the_whole_grid(R, recon):
+    prob, U = case_problem((20, 17, 16), dict(hll_mode="tau", reconstruction=recon))
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        for _ in range(3):
+            ctx.hydro_step(1)
+        Uw = ctx.get_state()
+    Us = hydro_stage_by_stage(R, prob, U, [0, 5, 11, 16], 3)
+    for f in range(I.NFIELD):
+        assert np.array_equal(Us[f], Uw[f]), (recon, f)
+
+
+def test_decomp_split_step_on_one_rank(R):
+    """decomp.split_step through a one-rank process group (the whole periodic
+    box as one slab): the hydrodynamic step, the material planes again, the
+    subcycled radiation steps, bit for bit like rhd_step_split."""
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_2404_08247_gb300 import decomp
+    prob, U, _ = I.turbulent_box_3d(shape=(20, 16, 14))
+    with R.RHDContext(prob) as ctx:
+        ctx.set_state(U)
+        info = ctx.step_split(2)
+        Uw = ctx.get_state()
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        q = R.slab_problems(prob, [0, prob["n"][2]])[0]
+        with R.RHDContext(q, stream=torch.cuda.current_stream()) as c:
+            c.set_state(U)
+            slab = decomp.CtxSlab(c, "cuda")
+            decomp.exchange_material(slab, dist)
+            res = decomp.split_step(slab, dist, 2)
+            assert res["status"] == R.RHD_OK and res["steps_done"] == 2
+            Us = c.get_state()
+    finally:
+        dist.destroy_process_group()
+    assert np.array_equal(Us, Uw), info
