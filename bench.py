@@ -95,6 +95,8 @@ def parse(argv=None):
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the 512-problem batched workload (for profiling); "
                          "prints its own JSON line")
+    ap.add_argument("--batched-steps", type=int, default=500,
+                    help="steps of the batched workload (its configuration: 500)")
     ap.add_argument("--no-graph", action="store_true",
                     help="batched workload: enqueue the launches instead of replaying a "
                          "CUDA graph (for profilers that do not see graph nodes)")
@@ -446,27 +448,28 @@ def run_batched(args, rhd, torch, rank, ws, dist, barrier, roof=None):
         for i, (_, U) in enumerate(problems):
             b.set_state(i, U)
         cells = b.cells()
-        b.step(args.steps)  # graph capture + warm-up
+        nsteps = args.batched_steps
+        b.step(nsteps)  # graph capture + warm-up
         barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        info = b.step(args.steps)
+        info = b.step(nsteps)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
     views = None
     if roof is not None:
         rec = roof["counts"]["batched"] if roof["counts"] else None
-        views = pipe_views(step_record(rec), cells, ms / args.steps, roof["peaks"],
+        views = pipe_views(step_record(rec), cells, ms / nsteps, roof["peaks"],
                            roof["hbm"], ALG_BYTES[0] + ALG_BYTES[1])
         views["note"] = ("one whole step (both stage launches) of the pooled cells; "
                          "flops per cell from ncu counts of the batch kernel's graph "
                          "nodes on this workload (profiles/kernel_counts.json)")
-    return {"value": whole_job_rate(cells, args.steps, ws, ms * 1e-3), "unit": UNIT,
+    return {"value": whole_job_rate(cells, nsteps, ws, ms * 1e-3), "unit": UNIT,
             "roofline": views,
-            "ms_per_step": ms / args.steps, "steps": args.steps, "problems": len(probs),
+            "ms_per_step": ms / nsteps, "steps": nsteps, "problems": len(probs),
             "cells": int(cells), "precision": "mixed",
             "n_1d": sum(1 for p in probs if p["ndim"] == 1),
             "tile2d": b.TILES[tuned["tile2d"]], "blocks_per_sm": tuned["blocks_per_sm"],

@@ -329,3 +329,32 @@ def test_colella_sekora_keeps_the_pulse_density_dip(oracle_mod):
         oracle_mod.hydro_step(prob, U, nh, t_end / nh)
         loss[rec] = np.max(np.abs(np.roll(U[I.F_RHO, 0, 0], -128) - rho) / rho)
     assert loss["ppm"] > 2e-2 and loss["ppm_cs"] < 1e-4, loss
+
+
+def test_sod_ppm_rounding_floor(oracle_mod):
+    """Conditioning of Sod's tube with PPM faces (100 cells, 134 steps), the
+    basis of the GPU parity bound of that case: half-ulp noise added to rho,
+    m and E_gas after every step moves the oracle's own end state by more
+    than 1e-10 (the constraint's switches at the shock and contact feed
+    rounding back), and by less than the bound the GPU test applies (1e-9);
+    with PLM faces the same noise stays below 1e-13."""
+    from parity import field_errors
+    O = oracle_mod
+    spread = {}
+    for rec in ("plm", "ppm"):
+        prob, U = I.riemann_problem_1d(100, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1),
+                                       reconstruction=rec)
+        A = U.copy()
+        O.hydro_step(prob, A, 134, 0.2 / 134)
+        worst = 0.0
+        for seed in (1, 2):
+            rng = np.random.default_rng(seed)
+            B = U.copy()
+            for _ in range(134):
+                O.hydro_step(prob, B, 1, 0.2 / 134)
+                for f in (I.F_RHO, I.F_MX, I.F_EGAS):
+                    B[f] *= 1.0 + 1.1e-16 * rng.choice([-1.0, 1.0], B.shape[1:])
+            worst = max(worst, max(field_errors(B, A).values()))
+        spread[rec] = worst
+    assert 1e-10 < spread["ppm"] <= 1e-9, spread
+    assert spread["plm"] < 1e-13, spread
