@@ -241,6 +241,35 @@ rhd_status rhd_step_async(rhd_ctx* ctx, int nsteps, double dt);
 /* Wait for the pending rhd_step_async batch and report it like rhd_step. */
 rhd_status rhd_sync(rhd_ctx* ctx, rhd_step_info* info);
 
+/* Step a state held in host memory: copy src in, advance nsteps >= 1 IMEX
+ * PD-ARS steps of size dt (eq. imex1, imex2; dt <= 0: rhd_default_dt), and
+ * copy the result to dst.  src and dst are host arrays of RHD_NFIELDS*ncell
+ * doubles, field-major as in rhd_state_set_all, owned by the caller; dst
+ * receives all ten fields (rho and kappa unchanged, and not copied back when
+ * dst is src) and may be src itself, but must not otherwise overlap it.  The
+ * copies run in up to 16 chunks of tile rows along the slowest grid axis (z
+ * in 3-D) on the context's own two copy streams (even and odd fields) and
+ * overlap the stage kernels, which run on its own compute streams of falling
+ * priority, one per launch group: the
+ * first step's stage 1 starts on the first chunks as soon as they and their
+ * neighbours are in, and the last step's stage 2 ends on small groups of
+ * chunks, each copied out as it finishes; the steps between run on the whole
+ * grid.  With pinned (page-locked) buffers the
+ * copies overlap the compute; pageable buffers give the same results without
+ * the overlap.  Ordered after earlier work on the context's stream, which
+ * waits for all of it; synchronises before returning; not for stream
+ * capture.  The result equals rhd_state_set_all + rhd_step + rhd_state_get_all
+ * bit for bit.  The input is validated as by rhd_state_set_all, after the
+ * fact: a non-finite or out-of-range value returns RHD_ERR_ARG, leaves dst
+ * unspecified and the context without a state (set it again).  On a failed
+ * step info (nullable) reports it as rhd_step does, the context holds the
+ * last completed step, and the evolved fields of dst are unspecified.  Any
+ * other error (RHD_ERR_CUDA, RHD_ERR_STATE) also leaves the context without a
+ * state.  Refused while a batch is pending, during a slab step and on a
+ * context with a HALO face. */
+rhd_status rhd_step_host(rhd_ctx* ctx, const double* src, double* dst, int64_t count,
+                         int nsteps, double dt, rhd_step_info* info);
+
 /* Transport operator of the current state, s(y) of eq. (yrsla): the rates
  * dE/dt and dF/dt (physical flux) of the explicit stage (Sec. 3.3 face states
  * and HLL fluxes), without the local source terms.  rates: 4*ncell doubles,

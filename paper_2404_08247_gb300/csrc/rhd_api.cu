@@ -85,6 +85,11 @@ struct rhd_ctx {
   double slab_dt = 0.0;
   bool slab_mat_above = false;
   bool slab_eps_below = false;
+  // rhd_step_host: its two copy streams and four compute streams (priority
+  // falling from the first), and its events (timing disabled), created by
+  // the first call
+  cudaStream_t hs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> hev;
 };
 
 // a context whose grid is a z-slab of a decomposed grid
@@ -337,6 +342,9 @@ static void release(rhd_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->pool) cudaEventDestroy(e);
+  for (auto e : c->hev) cudaEventDestroy(e);
+  for (auto h : c->hs)
+    if (h) cudaStreamDestroy(h);
   cudaFree(c->ybuf[0]);
   cudaFree(c->ybuf[1]);
   cudaFree(c->yhalf);
@@ -673,6 +681,291 @@ rhd_status rhd_step(rhd_ctx* c, int nsteps, double dt, rhd_step_info* info) {
     return s;
   }
   return rhd_sync(c, info);
+}
+
+// ------------------------------------------------ a step of a host-held state
+// rhd_step_host: the state is copied in and out in chunks of tile rows along
+// the slowest axis, so that the copies overlap the stage kernels.  A stage
+// launch over rows [r0, r1) reads the cells of those rows and their ghost
+// cells, at most 3 deep (the PPM stencil), so with chunks of at least 2 tile
+// rows (>= 8 planes) it needs its own chunks' inputs and its two neighbour
+// chunks' (cyclically: periodic faces wrap); the TAU factors of a chunk's +d
+// faces need its own and the next chunk's rho and kappa.
+
+static rhd_status host_step_fail_info(rhd_ctx* c, rhd_status s, rhd_step_info* info) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->status = s;
+    info->fail_cell = -1;
+    info->fail_step = -1;
+    info->t = c ? c->t : 0.0;
+  }
+  return s;
+}
+
+static StageArgs host_stage_args(rhd_ctx* c, double dt, int step, int stage) {
+  StageArgs A;
+  A.cell_base = 0;
+  for (int d = 0; d < 3; ++d) A.eps[d] = c->eps[d];
+  A.g = c->g;
+  A.ph = c->ph;
+  A.dt = dt;
+  A.rho = c->rho;
+  A.kappa = c->kappa;
+  A.st = c->d_status;
+  A.step = step;
+  const int N = c->ncell;
+  const int in = c->cur ^ (step & 1);  // y(n) of this step
+  if (stage == 1) {
+    slots_of<const double*>(A.yt, c->ybuf[in], N);
+    slots_of<const double*>(A.yn, c->ybuf[in], N);
+    slots_of<double*>(A.yo, c->yhalf, N);
+  } else {
+    slots_of<const double*>(A.yt, c->yhalf, N);
+    slots_of<const double*>(A.yn, c->ybuf[in], N);
+    slots_of<double*>(A.yo, c->ybuf[in ^ 1], N);
+  }
+  return A;
+}
+
+static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, int nsteps,
+                                    double dt) {
+  if (!c->hs[0]) {
+    int least = 0, greatest = 0;  // numerically: greatest priority <= least
+    CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    for (int k = 0; k < 6; ++k) {
+      const int prio = k < 2 ? least : std::min(least, greatest + (k - 2));
+      CUDA_TRY(c, cudaStreamCreateWithPriority(&c->hs[k], cudaStreamNonBlocking, prio));
+    }
+  }
+  const Geometry& g = c->g;
+  const size_t N = (size_t)c->ncell;
+  const int rows = stage_rows(g);
+  const int K = std::max(1, std::min(16, rows / 2));
+  std::vector<int> r0(K + 1);
+  std::vector<size_t> i0(K + 1, 0);
+  for (int k = 0; k <= K; ++k) r0[k] = (int)((long long)k * rows / K);
+  for (int k = 0; k < K; ++k) {
+    size_t n = 0;
+    for (int r = r0[k]; r < r0[k + 1]; ++r) n += (size_t)stage_row_cells(g, r);
+    i0[k + 1] = i0[k] + n;
+  }
+  if (i0[K] != N) return fail(c, RHD_ERR_STATE, "chunks cover %zu of %zu cells", i0[K], N);
+  const int nev = 5 * K + 8;
+  while ((int)c->hev.size() < nev) {
+    cudaEvent_t e = nullptr;
+    CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->hev.push_back(e);
+  }
+  cudaEvent_t* in_ev = c->hev.data();  // chunk k copied in, on copy stream 0 and 1
+  cudaEvent_t* tau_ev = in_ev + 2 * K; // TAU factors of chunk k's +d faces
+  cudaEvent_t* s1 = tau_ev + K;        // stage 1 of launch group q (at most K groups)
+  cudaEvent_t* s2 = s1 + K;            // stage 2 (of the last step) of launch group q
+  cudaEvent_t* ev = s2 + K;            // start, last stage 1, joins of the six streams
+  cudaStream_t cs[2] = {c->hs[0], c->hs[1]};
+  cudaStream_t* ks = c->hs + 2;        // compute stream q: launch group q
+  const int prec = c->p.precision;
+  const bool tau = c->p.hll_mode == RHD_HLL_TAU;
+  auto cyc = [K](int k) { return (k % K + K) % K; };
+
+  CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
+  for (int k = 0; k < 6; ++k) CUDA_TRY(c, cudaStreamWaitEvent(c->hs[k], ev[0], 0));
+  CUDA_TRY(c, launch_status_reset(c->d_status, cs[0]));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), cs[0]));
+  c->launches += 1;
+  if (tau) {
+    c->eps_dirty = false;
+    c->slab_mat_above = c->slab_eps_below = false;
+  }
+
+  // copies in, in the order 0, K-1, 1, ..., K-2 (chunk 0 needs K-1 and 1),
+  // even fields on copy stream 0 and odd ones on copy stream 1 (two copy
+  // engines; a field's copies in and out share a stream, so dst may be src).
+  // Only copies go on the copy streams: a kernel there would wait for SMs the
+  // stage kernels hold, and every later copy behind it.
+  std::vector<int> order(1, 0);
+  if (K > 1) order.push_back(K - 1);
+  for (int k = 1; k < K - 1; ++k) order.push_back(k);
+  for (int x : order) {
+    const size_t n = i0[x + 1] - i0[x];
+    for (int f = 0; f < RHD_NFIELDS; ++f)
+      CUDA_TRY(c, cudaMemcpyAsync(field_ptr(c, f) + i0[x], src + f * N + i0[x],
+                                  sizeof(double) * n, cudaMemcpyHostToDevice, cs[f & 1]));
+    for (int h = 0; h < 2; ++h) CUDA_TRY(c, cudaEventRecord(in_ev[2 * x + h], cs[h]));
+  }
+
+  // Stage launches over groups of chunks [a, b): few launches, small ones
+  // where they start or end the pipeline.  Group q runs on compute stream q,
+  // whose priority falls with q: launched together, the groups' blocks are
+  // dispatched in group order, each group's last wave shared with the next
+  // group's first blocks.  Stage 1: chunk 0 as soon as chunks K-1, 0, 1 are in, chunks
+  // 1 .. K/4 - 1 (enough work to cover the remaining copies in), then the
+  // rest.  The last stage 2: groups of decreasing size, each copied out as it
+  // finishes while the next ones compute: chunks 1 .. K-4, K-3 .. K-2, K-1,
+  // and 0 last.  A stage-1 group reads the inputs of chunks a-1 .. b and the
+  // TAU factors of chunks a-1 .. b-1 (launched on the stream of the first
+  // group that needs them); a stage-2 group the stage-1 outputs of a-1 .. b.
+  std::vector<std::pair<int, int>> g1, g2;
+  if (K >= 3) {
+    const int q1 = std::max(2, K / 4);
+    g1 = {{0, 1}, {1, q1}, {q1, K}};
+    if (K >= 5)
+      g2 = {{1, K - 3}, {K - 3, K - 1}, {K - 1, K}, {0, 1}};
+    else
+      g2 = {{1, K - 1}, {K - 1, K}, {0, 1}};
+  } else if (K == 2) {
+    g1 = {{0, 1}, {1, 2}};
+    g2 = {{1, 2}, {0, 1}};
+  } else {
+    g1 = {{0, 1}};
+    g2 = {{0, 1}};
+  }
+  const StageArgs A1 = host_stage_args(c, dt, 0, 1);
+  std::vector<int> grp1(K, -1);          // the stage-1 group of each chunk
+  std::vector<int> tau_on(K, -1);        // the stream index that made chunk k's TAU factors
+  for (int q = 0; q < (int)g1.size(); ++q) {
+    const int a = g1[q].first, b = g1[q].second;
+    const int si = q;
+    cudaStream_t st = ks[si];
+    std::vector<char> waited(K, 0);
+    for (int k = a - 1; k <= b; ++k) {
+      if (waited[cyc(k)]) continue;
+      for (int h = 0; h < 2; ++h)
+        CUDA_TRY(c, cudaStreamWaitEvent(st, in_ev[2 * cyc(k) + h], 0));
+      waited[cyc(k)] = 1;
+    }
+    if (tau) {
+      for (int k = a - 1; k < b; ++k) {
+        const int j = cyc(k);
+        if (tau_on[j] < 0) {
+          CUDA_TRY(c, launch_tau_eps(g, c->rho, c->kappa, c->ph.kappa_F_ratio, c->eps, st,
+                                     nullptr, nullptr, (long long)i0[j], (long long)i0[j + 1]));
+          CUDA_TRY(c, cudaEventRecord(tau_ev[j], st));
+          tau_on[j] = si;
+          c->launches += 1;
+        } else if (tau_on[j] != si) {
+          CUDA_TRY(c, cudaStreamWaitEvent(st, tau_ev[j], 0));
+        }
+      }
+    }
+    CUDA_TRY(c, launch_stage(1, prec, A1, st, r0[a], r0[b]));
+    CUDA_TRY(c, cudaEventRecord(s1[q], st));
+    for (int k = a; k < b; ++k) grp1[k] = q;
+    c->launches += 1;
+  }
+  // the input check (as rhd_state_set_all), read after the step: whole
+  // fields on the stream of the last stage-1 group, whose wait covers every
+  // chunk's copy
+  const int nq1 = (int)g1.size();
+  for (int f = 0; f < RHD_NFIELDS; ++f)
+    CUDA_TRY(c, launch_check_field(f, field_ptr(c, f), c->ncell, c->d_flag, ks[nq1 - 1]));
+  c->launches += RHD_NFIELDS;
+
+  // the steps between: whole-grid launches on the first compute stream
+  const StageArgs A2 = host_stage_args(c, dt, nsteps - 1, 2);
+  if (nsteps > 1) {
+    for (int q = 0; q < (int)g1.size(); ++q) CUDA_TRY(c, cudaStreamWaitEvent(ks[0], s1[q], 0));
+    CUDA_TRY(c, launch_stage(2, prec, host_stage_args(c, dt, 0, 2), ks[0]));
+    for (int s = 1; s < nsteps; ++s) {
+      CUDA_TRY(c, launch_stage(1, prec, host_stage_args(c, dt, s, 1), ks[0]));
+      if (s < nsteps - 1) CUDA_TRY(c, launch_stage(2, prec, host_stage_args(c, dt, s, 2), ks[0]));
+    }
+    c->launches += 2 * (nsteps - 1);
+    CUDA_TRY(c, cudaEventRecord(ev[1], ks[0]));
+    for (int q = 1; q < 4; ++q) CUDA_TRY(c, cudaStreamWaitEvent(ks[q], ev[1], 0));
+  }
+  for (int q = 0; q < (int)g2.size(); ++q) {
+    const int a = g2[q].first, b = g2[q].second;
+    cudaStream_t st = ks[q];
+    if (nsteps == 1) {
+      std::vector<char> seen(g1.size(), 0);
+      for (int k = a - 1; k <= b; ++k) {
+        const int gq = grp1[(k + K) % K];
+        if (!seen[gq]) CUDA_TRY(c, cudaStreamWaitEvent(st, s1[gq], 0));
+        seen[gq] = 1;
+      }
+    }
+    CUDA_TRY(c, launch_stage(2, prec, A2, st, r0[a], r0[b]));
+    CUDA_TRY(c, cudaEventRecord(s2[q], st));
+    c->launches += 1;
+  }
+  // copies out: rho and kappa (unchanged; not copied back in place) first,
+  // then each group's evolved fields after its stage 2, on the stream that
+  // copied the field in
+  if (dst != src)
+    for (int f : {RHD_F_RHO, RHD_F_KAPPA})
+      CUDA_TRY(c, cudaMemcpyAsync(dst + f * N, field_ptr(c, f), sizeof(double) * N,
+                                  cudaMemcpyDeviceToHost, cs[f & 1]));
+  const double* out = c->ybuf[c->cur ^ (nsteps & 1)];
+  for (int q = 0; q < (int)g2.size(); ++q) {
+    for (int h = 0; h < 2; ++h) CUDA_TRY(c, cudaStreamWaitEvent(cs[h], s2[q], 0));
+    const size_t lo = i0[g2[q].first], n = i0[g2[q].second] - lo;
+    for (int f = 0; f < RHD_NFIELDS; ++f) {
+      const int slot = slot_of(f);
+      if (slot < 0) continue;
+      CUDA_TRY(c, cudaMemcpyAsync(dst + f * N + lo, out + (size_t)slot * N + lo,
+                                  sizeof(double) * n, cudaMemcpyDeviceToHost, cs[f & 1]));
+    }
+  }
+  for (int k = 0; k < 6; ++k) {
+    CUDA_TRY(c, cudaEventRecord(ev[2 + k], c->hs[k]));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, ev[2 + k], 0));
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+  return RHD_OK;
+}
+
+rhd_status rhd_step_host(rhd_ctx* c, const double* src, double* dst, int64_t count,
+                         int nsteps, double dt, rhd_step_info* info) {
+  if (!c) return host_step_fail_info(c, fail(nullptr, RHD_ERR_ARG, "ctx is NULL"), info);
+  rhd_status s = RHD_OK;
+  if (c->pending)
+    s = fail(c, RHD_ERR_STATE, "a step batch is pending");
+  else if (c->slab_phase != 0)
+    s = fail(c, RHD_ERR_STATE, "a slab step is in progress");
+  else if (has_halo(c))
+    s = fail(c, RHD_ERR_STATE, "%s", kHaloOnly);
+  else if (!src || !dst)
+    s = fail(c, RHD_ERR_ARG, "buffer is NULL");
+  else if (count != (int64_t)RHD_NFIELDS * c->ncell)
+    s = fail(c, RHD_ERR_ARG, "count must be RHD_NFIELDS * ncell");
+  else if (nsteps < 1)
+    s = fail(c, RHD_ERR_ARG, "nsteps < 1");
+  if (s == RHD_OK) {
+    if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
+    if (!std::isfinite(dt)) s = fail(c, RHD_ERR_ARG, "dt is not finite");
+  }
+  if (s != RHD_OK) return host_step_fail_info(c, s, info);
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess)
+    return host_step_fail_info(
+        c, fail(c, RHD_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e)), info);
+  const int cur0 = c->cur;
+  const double t0 = c->t;
+  *c->h_flag = 0;
+  s = host_step_enqueue(c, src, dst, nsteps, dt);
+  if (s != RHD_OK) {
+    cudaStreamSynchronize(c->stream);
+    for (auto h : c->hs)
+      if (h) cudaStreamSynchronize(h);
+    c->fields_set = 0;  // the copies in may have stopped part way
+    return host_step_fail_info(c, s, info);
+  }
+  c->pending = true;
+  c->pending_n = nsteps;
+  c->pending_dt = dt;
+  c->pending_cur0 = cur0;
+  s = rhd_sync(c, info);  // waits for the copies out too
+  if (*c->h_flag) {
+    c->fields_set = 0;
+    c->cur = cur0;
+    c->t = t0;
+    return host_step_fail_info(
+        c, fail(c, RHD_ERR_ARG, "state holds a non-finite or out-of-range value"), info);
+  }
+  c->fields_set = kAllFields;
+  return s;
 }
 
 rhd_status rhd_transport(rhd_ctx* c, double* rates, int64_t count, int dst_on_device) {

@@ -106,6 +106,9 @@ struct StageArgs {
   // factors of the low slab face (n0 n1)
   const double* halo[2] = {nullptr, nullptr};
   const double* eps_zlo = nullptr;
+  // tile rows skipped along the slowest axis (z in 3-D, y in 2-D, x in 1-D):
+  // a launch over the rows [blk_off, blk_off + grid extent) of that axis
+  int blk_off = 0;
 };
 
 // ghost planes a HALO face holds (the widest face stencil: PPM's 3)
@@ -946,17 +949,25 @@ __device__ int local_solve_nongrey(const Physics& ph, double tdt, double rho, do
 
 // ------------------------------------------------------------ launchers
 // (host side, defined in the .cu files)
-cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s);
-cudaError_t launch_stage_ppm(int stage, int precision, const StageArgs& A, cudaStream_t s);
+// b0, b1: the tile rows [b0, b1) of the slowest axis (b1 < 0: to the end)
+cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s,
+                         int b0 = 0, int b1 = -1);
+cudaError_t launch_stage_ppm(int stage, int precision, const StageArgs& A, cudaStream_t s,
+                             int b0 = 0, int b1 = -1);
+// tile rows of a grid along its slowest axis, and the cells of one row
+int stage_rows(const Geometry& g);
+long long stage_row_cells(const Geometry& g, int row);
 cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s);
 cudaError_t launch_totals(const Geometry& g, const Physics& ph, const double* y,
                           double* partials, int npart, double* out4, cudaStream_t s);
 int totals_partials_needed();
-// halo_kappa, halo_rho: plane 0 of the slab above a HALO top face (else null)
+// halo_kappa, halo_rho: plane 0 of the slab above a HALO top face (else null);
+// i0, i1: the cells [i0, i1) whose +d faces are computed (i1 < 0: to the end)
 cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
                            double tau_scale, double* const eps[3], cudaStream_t s,
                            const double* halo_kappa = nullptr,
-                           const double* halo_rho = nullptr);
+                           const double* halo_rho = nullptr, long long i0 = 0,
+                           long long i1 = -1);
 cudaError_t launch_check_field(int field, const double* x, int n, int* flag,
                                cudaStream_t s);
 // message returned by rhd_last_error(NULL) on this thread

@@ -6,6 +6,8 @@
 // The stage-2 explicit state is eq. (imex2) with dt f(y(n+1/2)) replaced by
 // y(n+1/2) - y*, which eq. (imex1) makes exact.  One block per tile; the tile
 // body is stage_tile (rhd_tile.cuh), the kernel stage_kernel (rhd_stage.cuh).
+#include <algorithm>
+
 #include "rhd_stage.cuh"
 
 namespace rhd {
@@ -33,9 +35,9 @@ cudaError_t launch_status_reset(DevStatus* st, cudaStream_t s) {
 __global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
                                const double* __restrict__ kappa, double tau_scale, double* e0,
                                double* e1, double* e2, const double* __restrict__ hk,
-                               const double* __restrict__ hr) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.ncell) return;
+                               const double* __restrict__ hr, int i0, int i1) {
+  int idx = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= i1) return;
   int c[3];
   c[0] = idx % g.n[0];
   int r = idx / g.n[0];
@@ -62,11 +64,14 @@ __global__ void tau_eps_kernel(const Geometry g, const double* __restrict__ rho,
 
 cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* kappa,
                            double tau_scale, double* const eps[3], cudaStream_t s,
-                           const double* halo_kappa, const double* halo_rho) {
+                           const double* halo_kappa, const double* halo_rho, long long i0,
+                           long long i1) {
   if (g.bc[2][1] == RHD_BC_HALO && (!halo_kappa || !halo_rho)) return cudaErrorInvalidValue;
-  int blocks = (g.ncell + 255) / 256;
+  if (i1 < 0 || i1 > g.ncell) i1 = g.ncell;
+  if (i0 < 0 || i0 >= i1) return cudaErrorInvalidValue;
+  int blocks = (int)((i1 - i0 + 255) / 256);
   tau_eps_kernel<<<blocks, 256, 0, s>>>(g, rho, kappa, tau_scale, eps[0], eps[1], eps[2],
-                                        halo_kappa, halo_rho);
+                                        halo_kappa, halo_rho, (int)i0, (int)i1);
   return cudaGetLastError();
 }
 
@@ -74,19 +79,42 @@ cudaError_t launch_tau_eps(const Geometry& g, const double* rho, const double* k
 // temperature-dependent or non-grey opacity or an inflow face select the
 // general ones; PPM faces the PPM unit's (general physics, wider halo).
 template <int STAGE>
-static cudaError_t launch_stage_t(int precision, const StageArgs& A, cudaStream_t s) {
-  if (A.ph.reconstruction != RHD_RECON_PLM) return launch_stage_ppm(STAGE, precision, A, s);
+static cudaError_t launch_stage_t(int precision, const StageArgs& A, cudaStream_t s, int b0,
+                                  int b1) {
+  if (A.ph.reconstruction != RHD_RECON_PLM)
+    return launch_stage_ppm(STAGE, precision, A, s, b0, b1);
   const bool gen = needs_general(A.g, A.ph);
   if (precision == RHD_PREC_MIXED)
-    return gen ? launch_prec<STAGE, float, true, false>(A, s)
-               : launch_prec<STAGE, float, false, false>(A, s);
-  return gen ? launch_prec<STAGE, double, true, false>(A, s)
-             : launch_prec<STAGE, double, false, false>(A, s);
+    return gen ? launch_prec<STAGE, float, true, false>(A, s, b0, b1)
+               : launch_prec<STAGE, float, false, false>(A, s, b0, b1);
+  return gen ? launch_prec<STAGE, double, true, false>(A, s, b0, b1)
+             : launch_prec<STAGE, double, false, false>(A, s, b0, b1);
 }
 
-cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s) {
-  if (stage == 0) return launch_stage_t<0>(precision, A, s);
-  return stage == 1 ? launch_stage_t<1>(precision, A, s) : launch_stage_t<2>(precision, A, s);
+cudaError_t launch_stage(int stage, int precision, const StageArgs& A, cudaStream_t s, int b0,
+                         int b1) {
+  if (stage == 0) return launch_stage_t<0>(precision, A, s, b0, b1);
+  return stage == 1 ? launch_stage_t<1>(precision, A, s, b0, b1)
+                    : launch_stage_t<2>(precision, A, s, b0, b1);
+}
+
+// Tile rows along the slowest axis, and the cells one row covers (PLM and
+// PPM tiles have the same shape).
+int stage_rows(const Geometry& g) {
+  switch (g.ndim) {
+    case 1: return (g.n[0] + Tile<1>::TX - 1) / Tile<1>::TX;
+    case 2: return (g.n[1] + Tile<2>::TY - 1) / Tile<2>::TY;
+    default: return (g.n[2] + Tile<3>::LZ - 1) / Tile<3>::LZ;
+  }
+}
+
+long long stage_row_cells(const Geometry& g, int row) {
+  const int ax = g.ndim - 1;
+  const int w = g.ndim == 1 ? Tile<1>::TX : g.ndim == 2 ? Tile<2>::TY : Tile<3>::LZ;
+  long long plane = 1;
+  for (int d = 0; d < ax; ++d) plane *= g.n[d];
+  const int lo = row * w, hi = std::min(g.n[ax], lo + w);
+  return hi > lo ? plane * (hi - lo) : 0;
 }
 
 }  // namespace rhd

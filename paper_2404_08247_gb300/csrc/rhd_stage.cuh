@@ -22,13 +22,16 @@ __global__ void __launch_bounds__(Tile<NDIM>::NT, NDIM == 3 ? RHD_STAGE_MINB : 2
   __syncthreads();
   if (s_skip) return;  // a previous launch of this batch failed
   TileStats ts;
-  stage_tile<STAGE, T, R, GEN>(A, blockIdx.x * T::TX, blockIdx.y * T::TY,
-                               blockIdx.z * T::LZ, smem_raw, ts);
+  const int bx = blockIdx.x + (NDIM == 1 ? A.blk_off : 0);
+  const int by = blockIdx.y + (NDIM == 2 ? A.blk_off : 0);
+  const int bz = blockIdx.z + (NDIM == 3 ? A.blk_off : 0);
+  stage_tile<STAGE, T, R, GEN>(A, bx * T::TX, by * T::TY, bz * T::LZ, smem_raw, ts);
   flush_stats<T::NT>(A.st, ts);
 }
 
+// The tile rows [b0, b1) of the slowest axis (b1 < 0: all of them).
 template <int STAGE, int NDIM, typename R, bool GEN, bool PPM>
-static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s) {
+static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s, int b0, int b1) {
   using T = std::conditional_t<PPM, TilePPM<NDIM>, Tile<NDIM>>;
   using S = SmemT<T, R>;
   // opt in to more than 48 KiB of dynamic shared memory (idempotent)
@@ -36,18 +39,26 @@ static cudaError_t launch_nd(const StageArgs& A, cudaStream_t s) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)S::BYTES);
   if (e != cudaSuccess) return e;
-  dim3 grid((A.g.n[0] + T::TX - 1) / T::TX, (A.g.n[1] + T::TY - 1) / T::TY,
-            (A.g.n[2] + T::LZ - 1) / T::LZ);
-  stage_kernel<STAGE, NDIM, R, GEN, PPM><<<grid, T::TX * T::TY, S::BYTES, s>>>(A);
+  unsigned nb[3] = {(unsigned)((A.g.n[0] + T::TX - 1) / T::TX),
+                    (unsigned)((A.g.n[1] + T::TY - 1) / T::TY),
+                    (unsigned)((A.g.n[2] + T::LZ - 1) / T::LZ)};
+  const int rows = (int)nb[NDIM - 1];
+  if (b1 < 0 || b1 > rows) b1 = rows;
+  if (b0 < 0 || b0 >= b1) return cudaErrorInvalidValue;
+  nb[NDIM - 1] = (unsigned)(b1 - b0);
+  StageArgs a = A;
+  a.blk_off = b0;
+  stage_kernel<STAGE, NDIM, R, GEN, PPM><<<dim3(nb[0], nb[1], nb[2]), T::TX * T::TY, S::BYTES,
+                                           s>>>(a);
   return cudaGetLastError();
 }
 
 template <int STAGE, typename R, bool GEN, bool PPM>
-static cudaError_t launch_prec(const StageArgs& A, cudaStream_t s) {
+static cudaError_t launch_prec(const StageArgs& A, cudaStream_t s, int b0, int b1) {
   switch (A.g.ndim) {
-    case 1: return launch_nd<STAGE, 1, R, GEN, PPM>(A, s);
-    case 2: return launch_nd<STAGE, 2, R, GEN, PPM>(A, s);
-    default: return launch_nd<STAGE, 3, R, GEN, PPM>(A, s);
+    case 1: return launch_nd<STAGE, 1, R, GEN, PPM>(A, s, b0, b1);
+    case 2: return launch_nd<STAGE, 2, R, GEN, PPM>(A, s, b0, b1);
+    default: return launch_nd<STAGE, 3, R, GEN, PPM>(A, s, b0, b1);
   }
 }
 

@@ -6,14 +6,17 @@
 namespace rhd {
 
 template <int STAGE>
-static cudaError_t launch_ppm_t(int precision, const StageArgs& A, cudaStream_t s) {
-  if (precision == RHD_PREC_MIXED) return launch_prec<STAGE, float, true, true>(A, s);
-  return launch_prec<STAGE, double, true, true>(A, s);
+static cudaError_t launch_ppm_t(int precision, const StageArgs& A, cudaStream_t s, int b0,
+                                int b1) {
+  if (precision == RHD_PREC_MIXED) return launch_prec<STAGE, float, true, true>(A, s, b0, b1);
+  return launch_prec<STAGE, double, true, true>(A, s, b0, b1);
 }
 
-cudaError_t launch_stage_ppm(int stage, int precision, const StageArgs& A, cudaStream_t s) {
-  if (stage == 0) return launch_ppm_t<0>(precision, A, s);
-  return stage == 1 ? launch_ppm_t<1>(precision, A, s) : launch_ppm_t<2>(precision, A, s);
+cudaError_t launch_stage_ppm(int stage, int precision, const StageArgs& A, cudaStream_t s,
+                             int b0, int b1) {
+  if (stage == 0) return launch_ppm_t<0>(precision, A, s, b0, b1);
+  return stage == 1 ? launch_ppm_t<1>(precision, A, s, b0, b1)
+                    : launch_ppm_t<2>(precision, A, s, b0, b1);
 }
 
 }  // namespace rhd

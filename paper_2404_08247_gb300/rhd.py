@@ -124,6 +124,8 @@ SIGNATURES = {
                                 ctypes.POINTER(rhd_step_info)]),
     "rhd_step_async": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_double]),
     "rhd_sync": (ctypes.c_int, [_V, ctypes.POINTER(rhd_step_info)]),
+    "rhd_step_host": (ctypes.c_int, [_V, _V, _V, _I64, ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(rhd_step_info)]),
     "rhd_transport": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
     "rhd_totals": (ctypes.c_int, [_V, _D]),
     "rhd_profile": (ctypes.c_int, [_V, ctypes.c_int]),
@@ -391,6 +393,29 @@ class RHDContext:
             _check(st, self.h)
         d = info.as_dict()
         d["status"] = st
+        return d
+
+    def step_host(self, src, dst=None, nsteps: int = 1, dt: float = 0.0,
+                  raise_on_error=True) -> dict:
+        """rhd_step_host: step the host state `src` (10 fields, numpy array or
+        CPU tensor; pinned memory lets the copies overlap the kernels) and write
+        the result to `dst` (default: a new array that starts as NaN; may be
+        src).  Returns the step info with "out" = dst."""
+        if dst is None:
+            dst = np.full(self.shape, np.nan)
+        ps, ds = _ptr(src)
+        pd, dd = _ptr(dst)
+        if ds or dd:
+            raise ValueError("step_host takes host buffers")
+        info = rhd_step_info()
+        st = self.lib.rhd_step_host(self.h, ctypes.c_void_p(ps), ctypes.c_void_p(pd),
+                                    RHD_NFIELDS * self.ncell, int(nsteps), float(dt),
+                                    ctypes.byref(info))
+        if raise_on_error:
+            _check(st, self.h)
+        d = info.as_dict()
+        d["status"] = st
+        d["out"] = dst
         return d
 
     # ---- one z-slab stepped stage by stage by its own process
