@@ -175,6 +175,18 @@ def pipe_views(rec, n_cells, ms_per_launch, peaks, hbm_peak, alg_bytes):
     f64 = rec["fp64_flop"] * n_cells / sec / 1e12
     v["fp64"] = {"achieved": f64, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                  "frac": f64 / peaks["fp64_tflops"], "flop_per_cell": rec["fp64_flop"]}
+    if rec.get("fp64_warp_inst") and rec.get("fp64_thread_arith_inst"):
+        # frac = (FP64 pipe busy over the launch) x (active lanes x arithmetic
+        # share of the FP64-pipe instructions) x (flops per arithmetic
+        # instruction / 2): the last two from the counts, the first implied
+        lane_arith = rec["fp64_thread_arith_inst"] / (32.0 * rec["fp64_warp_inst"])
+        fma_mix = rec["fp64_flop"] / (2.0 * rec["fp64_thread_arith_inst"])
+        v["fp64"]["decomposition"] = {
+            "lane_arith_share": lane_arith, "fma_mix": fma_mix,
+            "fp64_pipe_busy_implied": v["fp64"]["frac"] / (lane_arith * fma_mix),
+            "note": "frac = pipe busy x lane_arith_share x fma_mix; an add or multiply "
+                    "fills an FMA slot with one flop, so fma_mix bounds frac even at full "
+                    "lanes and a fully busy pipe"}
     if rec.get("fp32_flop", 0.0) > 1.0:
         f32 = rec["fp32_flop"] * n_cells / sec / 1e12
         v["fp32"] = {"achieved": f32, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
