@@ -85,10 +85,10 @@ struct rhd_ctx {
   double slab_dt = 0.0;
   bool slab_mat_above = false;
   bool slab_eps_below = false;
-  // rhd_step_host: its two copy streams and four compute streams (priority
+  // rhd_step_host: its two copy streams and six compute streams (priority
   // falling from the first), and its events (timing disabled), created by
   // the first call
-  cudaStream_t hs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t hs[8] = {};
   std::vector<cudaEvent_t> hev;
 };
 
@@ -733,7 +733,7 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
   if (!c->hs[0]) {
     int least = 0, greatest = 0;  // numerically: greatest priority <= least
     CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 8; ++k) {
       const int prio = k < 2 ? least : std::min(least, greatest + (k - 2));
       CUDA_TRY(c, cudaStreamCreateWithPriority(&c->hs[k], cudaStreamNonBlocking, prio));
     }
@@ -751,7 +751,7 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
     i0[k + 1] = i0[k] + n;
   }
   if (i0[K] != N) return fail(c, RHD_ERR_STATE, "chunks cover %zu of %zu cells", i0[K], N);
-  const int nev = 5 * K + 8;
+  const int nev = 5 * K + 10;
   while ((int)c->hev.size() < nev) {
     cudaEvent_t e = nullptr;
     CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -769,7 +769,7 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
   auto cyc = [K](int k) { return (k % K + K) % K; };
 
   CUDA_TRY(c, cudaEventRecord(ev[0], c->stream));
-  for (int k = 0; k < 6; ++k) CUDA_TRY(c, cudaStreamWaitEvent(c->hs[k], ev[0], 0));
+  for (int k = 0; k < 8; ++k) CUDA_TRY(c, cudaStreamWaitEvent(c->hs[k], ev[0], 0));
   CUDA_TRY(c, launch_status_reset(c->d_status, cs[0]));
   CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), cs[0]));
   c->launches += 1;
@@ -800,18 +800,24 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
   // dispatched in group order, each group's last wave shared with the next
   // group's first blocks.  Stage 1: chunk 0 as soon as chunks K-1, 0, 1 are in, chunks
   // 1 .. K/4 - 1 (enough work to cover the remaining copies in), then the
-  // rest.  The last stage 2: groups of decreasing size, each copied out as it
-  // finishes while the next ones compute: chunks 1 .. K-4, K-3 .. K-2, K-1,
-  // and 0 last.  A stage-1 group reads the inputs of chunks a-1 .. b and the
+  // rest.  The last stage 2: groups each copied out as it finishes while the
+  // next ones compute, none larger than a quarter of the grid (so that a slow
+  // copy out keeps pace): chunks 1 .. K-4 in up to three groups, then
+  // K-3 .. K-2, K-1, and 0 last.  A stage-1 group reads the inputs of chunks a-1 .. b and the
   // TAU factors of chunks a-1 .. b-1 (launched on the stream of the first
   // group that needs them); a stage-2 group the stage-1 outputs of a-1 .. b.
   std::vector<std::pair<int, int>> g1, g2;
   if (K >= 3) {
     const int q1 = std::max(2, K / 4);
     g1 = {{0, 1}, {1, q1}, {q1, K}};
-    if (K >= 5)
-      g2 = {{1, K - 3}, {K - 3, K - 1}, {K - 1, K}, {0, 1}};
-    else
+    if (K >= 5) {
+      const int nb = std::min(3, K - 4);  // groups of the body 1 .. K-4
+      for (int j = 0; j < nb; ++j)
+        g2.push_back({1 + j * (K - 4) / nb, 1 + (j + 1) * (K - 4) / nb});
+      g2.push_back({K - 3, K - 1});
+      g2.push_back({K - 1, K});
+      g2.push_back({0, 1});
+    } else
       g2 = {{1, K - 1}, {K - 1, K}, {0, 1}};
   } else if (K == 2) {
     g1 = {{0, 1}, {1, 2}};
@@ -872,7 +878,7 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
     }
     c->launches += 2 * (nsteps - 1);
     CUDA_TRY(c, cudaEventRecord(ev[1], ks[0]));
-    for (int q = 1; q < 4; ++q) CUDA_TRY(c, cudaStreamWaitEvent(ks[q], ev[1], 0));
+    for (int q = 1; q < 6; ++q) CUDA_TRY(c, cudaStreamWaitEvent(ks[q], ev[1], 0));
   }
   for (int q = 0; q < (int)g2.size(); ++q) {
     const int a = g2[q].first, b = g2[q].second;
@@ -907,7 +913,7 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
                                   sizeof(double) * n, cudaMemcpyDeviceToHost, cs[f & 1]));
     }
   }
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 8; ++k) {
     CUDA_TRY(c, cudaEventRecord(ev[2 + k], c->hs[k]));
     CUDA_TRY(c, cudaStreamWaitEvent(c->stream, ev[2 + k], 0));
   }
