@@ -45,6 +45,9 @@ struct rhd_ctx {
   double* kappa = nullptr;
   double* eps[3] = {nullptr, nullptr, nullptr};  // TAU-mode face factors
   bool eps_dirty = true;
+  // each cell's solve cost in stage 1 and stage 2 of the last step (2 ncell
+  // bytes): the order of the next step's solves
+  unsigned char* cost = nullptr;
   DevStatus* d_status = nullptr;
   DevStatus* h_status = nullptr;
   double* d_partials = nullptr;
@@ -351,6 +354,7 @@ static void release(rhd_ctx* c) {
   cudaFree(c->rho);
   cudaFree(c->kappa);
   for (int d = 0; d < 3; ++d) cudaFree(c->eps[d]);
+  cudaFree(c->cost);
   cudaFree(c->d_status);
   cudaFree(c->d_partials);
   cudaFree(c->d_tot);
@@ -417,6 +421,8 @@ rhd_status rhd_init(const rhd_params* p, rhd_ctx** out) {
   if (p->hll_mode == RHD_HLL_TAU)
     for (int d = 0; d < p->ndim && e == cudaSuccess; ++d)
       e = cudaMalloc(&c->eps[d], sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&c->cost, 2 * N);
+  if (e == cudaSuccess) e = cudaMemset(c->cost, 0, 2 * N);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(DevStatus));
   if (e == cudaSuccess)
     e = cudaMalloc(&c->d_partials, sizeof(double) * totals_partials_needed());
@@ -614,9 +620,11 @@ rhd_status rhd_step_async(rhd_ctx* c, int nsteps, double dt) {
     slots_of<const double*>(A.yt, c->ybuf[cur], N);
     slots_of<const double*>(A.yn, c->ybuf[cur], N);
     slots_of<double*>(A.yo, c->yhalf, N);
+    A.cost = c->cost;
     CUDA_TRY(c, launch_recorded(c, 0, 1, A));
     slots_of<const double*>(A.yt, c->yhalf, N);
     slots_of<double*>(A.yo, c->ybuf[cur ^ 1], N);
+    A.cost = c->cost + N;
     CUDA_TRY(c, launch_recorded(c, 1, 2, A));
     c->launches += 2;
     cur ^= 1;
@@ -725,6 +733,7 @@ static StageArgs host_stage_args(rhd_ctx* c, double dt, int step, int stage) {
     slots_of<const double*>(A.yn, c->ybuf[in], N);
     slots_of<double*>(A.yo, c->ybuf[in ^ 1], N);
   }
+  A.cost = c->cost + (stage == 1 ? 0 : N);
   return A;
 }
 
@@ -1625,6 +1634,7 @@ static rhd_status slab_radiation(rhd_ctx* const* slabs, int nslab, int nsteps, d
       slots_of<const double*>(a.yt, c->ybuf[cur[s]], c->ncell);
       slots_of<const double*>(a.yn, c->ybuf[cur[s]], c->ncell);
       slots_of<double*>(a.yo, c->yhalf, c->ncell);
+      a.cost = c->cost;
       CUDA_TRY(c0, launch_stage(1, c->p.precision, a, st));
     }
     for (int s = 0; s < nslab; ++s) src[s] = slabs[s]->yhalf;
@@ -1636,6 +1646,7 @@ static rhd_status slab_radiation(rhd_ctx* const* slabs, int nslab, int nsteps, d
       StageArgs& a = A[s];
       slots_of<const double*>(a.yt, c->yhalf, c->ncell);
       slots_of<double*>(a.yo, c->ybuf[cur[s] ^ 1], c->ncell);
+      a.cost = c->cost + c->ncell;
       CUDA_TRY(c0, launch_stage(2, c->p.precision, a, st));
       c->launches += 2;
       cur[s] ^= 1;
@@ -2115,6 +2126,7 @@ rhd_status rhd_slab_stage(rhd_ctx* c, int stage, double dt) {
     slots_of<const double*>(a.yn, c->ybuf[c->cur], N);
     slots_of<double*>(a.yo, c->ybuf[c->cur ^ 1], N);
   }
+  a.cost = c->cost + (stage == 1 ? 0 : N);
   CUDA_TRY(c, launch_stage(stage, c->p.precision, a, c->stream));
   c->launches += 1;
   c->slab_phase = stage;

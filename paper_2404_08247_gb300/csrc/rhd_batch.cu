@@ -48,6 +48,7 @@ struct BatchArgs {
   const double* eps1;
   DevStatus* st;
   int step;
+  unsigned char* cost;  // this stage's per-cell solve costs (pooled), or null
 };
 
 using Tile1 = TileT<1, 256, 1, 1>;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
     A.eps[0] = B.eps0 ? B.eps0 + off : nullptr;
     A.eps[1] = B.eps1 ? B.eps1 + off : nullptr;
     A.eps[2] = nullptr;
+    A.cost = B.cost ? B.cost + off : nullptr;
 #pragma unroll
     for (int q = 0; q < 4; ++q) A.rate[q] = nullptr;
     if (w.kind == 0)
@@ -191,6 +193,7 @@ struct rhd_batch {
   double* rho = nullptr;
   double* kappa = nullptr;
   double* eps[2] = {nullptr, nullptr};
+  unsigned char* cost = nullptr;  // solve costs of stage 1 and 2 (2 ntot bytes)
   ProblemDesc* d_desc = nullptr;
   WorkItem* d_items = nullptr;
   int nitems = 0;
@@ -252,6 +255,7 @@ static void batch_release(rhd_batch* b) {
   cudaFree(b->yhalf);
   cudaFree(b->rho);
   cudaFree(b->kappa);
+  cudaFree(b->cost);
   cudaFree(b->eps[0]);
   cudaFree(b->eps[1]);
   cudaFree(b->d_desc);
@@ -339,6 +343,8 @@ rhd_status rhd_batch_init(const rhd_params* probs, int nprob, rhd_batch** out) {
   if (e == cudaSuccess) e = cudaMalloc(&b->yhalf, sizeof(double) * NY * N);
   if (e == cudaSuccess) e = cudaMalloc(&b->rho, sizeof(double) * N);
   if (e == cudaSuccess) e = cudaMalloc(&b->kappa, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&b->cost, 2 * N);
+  if (e == cudaSuccess) e = cudaMemset(b->cost, 0, 2 * N);
   if (any_tau) {
     if (e == cudaSuccess) e = cudaMalloc(&b->eps[0], sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMalloc(&b->eps[1], sizeof(double) * N);
@@ -490,11 +496,13 @@ static cudaError_t enqueue_steps(rhd_batch* b, int nsteps, int cur0, cudaStream_
     B.yt = b->ybuf[cur];
     B.yn = b->ybuf[cur];
     B.yo = b->yhalf;
+    B.cost = b->cost;
     e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
     if (e == cudaSuccess)
       e = launch_batch(1, b->precision, b->general, b->ppm, b->tile2d, B, grid, cs);
     B.yt = b->yhalf;
     B.yo = b->ybuf[cur ^ 1];
+    B.cost = b->cost + b->ntot;
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), cs);
     if (e == cudaSuccess)
       e = launch_batch(2, b->precision, b->general, b->ppm, b->tile2d, B, grid, cs);

@@ -87,7 +87,17 @@ struct SmemT {
   static constexpr int FXI = ISO ? T::TY * (T::TX + 1) : 0;
   static constexpr int FYI = ISO && T::NDIM >= 2 ? (T::TY + 1) * T::TX : 0;
   static constexpr size_t ISO_OFF = sizeof(R) * (RING + FX + FY + CZ);
-  static constexpr size_t BYTES = ISO_OFF + sizeof(double) * (FXI + FYI);
+  // local solves in cost order (stages 1 and 2, where the launch supplies
+  // the predicted costs): per slot the explicit state, rho and chi (10
+  // doubles, slot-minor), then the solve flag / status, Newton and outer
+  // counts, and the per-warp counts of each cost bucket.  Not with the 3-D
+  // PPM tile, whose two blocks per SM leave no room.
+  static constexpr bool SORT = !(T::PPM && T::NDIM == 3);
+  static constexpr int NB = 32;  // cost buckets
+  static constexpr size_t SORT_OFF = ISO_OFF + sizeof(double) * (FXI + FYI);
+  static constexpr size_t SORT_BYTES =
+      SORT ? sizeof(double) * 10 * T::NT + sizeof(int) * (3 * T::NT + (T::NT / 32) * NB) : 0;
+  static constexpr size_t BYTES = SORT_OFF + SORT_BYTES;
 };
 
 // Coordinate x >= -3 folded onto [0, n) by the boundary condition (padding
@@ -422,6 +432,131 @@ __device__ __forceinline__ void column_cell(const StageArgs& A, int cx, int cy, 
 }
 
 // Per-thread iteration statistics of the cells a thread has solved.
+// ------------------------------------------------ local solves in cost order
+// Shared arrays of the sorted solves (SmemT::SORT): 10 doubles per slot
+// (y[0..7], rho, chi), then per slot the solve flag / status, the Newton and
+// the outer counts, then the per-warp counts of each cost bucket.
+template <class T, typename R>
+struct SortSmem {
+  double* v;
+  int* flag;
+  int* nn;
+  int* no;
+  int* tab;
+  __device__ __forceinline__ explicit SortSmem(unsigned char* smem) {
+    using S = SmemT<T, R>;
+    v = reinterpret_cast<double*>(smem + S::SORT_OFF);
+    flag = reinterpret_cast<int*>(v + 10 * T::NT);
+    nn = flag + T::NT;
+    no = nn + T::NT;
+    tab = no + T::NT;
+  }
+};
+
+// Slot of this thread's cell in the block's cost order: a stable counting
+// sort on the cost bucket (the previous step's cost - 8, within [0, 31]:
+// costs run from about 6 to 50, a Newton update counting 1 and an outer pass
+// 4; cells without a solve in bucket 0).  Sorted rank r goes to warp r / 32 in the first half of
+// the warps and to the mirrored warp in the second (ranks 128..255 of 256 to
+// warps 7..4), so that each of the SM's schedulers (warp w runs on scheduler
+// w mod 4) holds one cheaper and one dearer warp of the block.  The bucket
+// counts must be zero on entry; every thread of the block calls this.
+template <class T, typename R>
+__device__ __forceinline__ int sort_slot(unsigned char* smem, const StageArgs& A, bool need,
+                                         int idx, int ncell) {
+  using S = SmemT<T, R>;
+  constexpr int NT = T::NT, NW = NT / 32, NB = S::NB;
+  static_assert(NB == 32 && NT % 32 == 0 && (NW % 2 == 0), "one lane per bucket, warp pairs");
+  SortSmem<T, R> q(smem);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int key = 0;
+  if (need) key = max(0, min(NB - 1, (int)RHD_LD(A.st, A.cost, idx, ncell) - 8));
+  const unsigned m = __match_any_sync(full, key);
+  const int wrank = __popc(m & ((1u << lane) - 1u));
+  if (wrank == 0) RHD_ST(A.st, q.tab, warp * NB + key, NW * NB, __popc(m));
+  __syncthreads();
+  if (warp == 0) {  // lane b: the start of bucket b in each warp
+    int tot = 0;
+    for (int w = 0; w < NW; ++w) tot += q.tab[w * NB + lane];
+    int base = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, base, o);
+      if (lane >= o) base += v;
+    }
+    base -= tot;
+    for (int w = 0; w < NW; ++w) {
+      const int c = q.tab[w * NB + lane];
+      q.tab[w * NB + lane] = base;
+      base += c;
+    }
+  }
+  __syncthreads();
+  const int r = (int)RHD_LD(A.st, q.tab, warp * NB + key, NW * NB) + wrank;
+  const int gw = r >> 5;
+  const int tw = gw < NW / 2 ? gw : (3 * NW / 2 - 1) - gw;
+  return tw * 32 + (r & 31);
+}
+
+// this thread's cell into its sorted slot
+template <class T, typename R>
+__device__ __forceinline__ void stage_slot_put(unsigned char* smem, const StageArgs& A, int slot,
+                                               const double y[8], double rho, double chi,
+                                               bool need) {
+  constexpr int NT = T::NT;
+  SortSmem<T, R> q(smem);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) RHD_ST(A.st, q.v, j * NT + slot, 10 * NT, y[j]);
+  RHD_ST(A.st, q.v, 8 * NT + slot, 10 * NT, rho);
+  RHD_ST(A.st, q.v, 9 * NT + slot, 10 * NT, chi);
+  RHD_ST(A.st, q.flag, slot, NT, need ? 1 : 0);
+}
+
+// the cell of slot (this thread's solve); clears the bucket counts for the
+// next plane (all threads have read them before the barrier that precedes
+// this call); returns whether the cell needs a solve
+template <class T, typename R>
+__device__ __forceinline__ bool stage_slot_get(unsigned char* smem, const StageArgs& A, int slot,
+                                               double y[8], double& rho, double& chi) {
+  using S = SmemT<T, R>;
+  constexpr int NT = T::NT, NTAB = (NT / 32) * S::NB;
+  SortSmem<T, R> q(smem);
+  for (int i = threadIdx.x; i < NTAB; i += NT) q.tab[i] = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) y[j] = RHD_LD(A.st, q.v, j * NT + slot, 10 * NT);
+  rho = RHD_LD(A.st, q.v, 8 * NT + slot, 10 * NT);
+  chi = RHD_LD(A.st, q.v, 9 * NT + slot, 10 * NT);
+  return RHD_LD(A.st, q.flag, slot, NT) != 0;
+}
+
+// the solved cell of slot back into its slot
+template <class T, typename R>
+__device__ __forceinline__ void stage_slot_result(unsigned char* smem, const StageArgs& A,
+                                                  int slot, const double y[8], int code, int nn,
+                                                  int no) {
+  constexpr int NT = T::NT;
+  SortSmem<T, R> q(smem);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) RHD_ST(A.st, q.v, j * NT + slot, 10 * NT, y[j]);
+  RHD_ST(A.st, q.flag, slot, NT, code);
+  RHD_ST(A.st, q.nn, slot, NT, nn);
+  RHD_ST(A.st, q.no, slot, NT, no);
+}
+
+// this thread's own cell, solved, from its sorted slot
+template <class T, typename R>
+__device__ __forceinline__ void stage_slot_take(unsigned char* smem, const StageArgs& A, int slot,
+                                                double y[8], int& code, int& nn, int& no) {
+  constexpr int NT = T::NT;
+  SortSmem<T, R> q(smem);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) y[j] = RHD_LD(A.st, q.v, j * NT + slot, 10 * NT);
+  code = (int)RHD_LD(A.st, q.flag, slot, NT);
+  nn = (int)RHD_LD(A.st, q.nn, slot, NT);
+  no = (int)RHD_LD(A.st, q.no, slot, NT);
+}
+
 struct TileStats {
   int nn_max = 0, no_max = 0;
   unsigned long long nn_sum = 0, no_sum = 0, cnt = 0;
@@ -454,6 +589,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   if (threadIdx.x == 0) s_chk_status = A.st;
   __syncthreads();
 #endif
+  if constexpr (STAGE != 0 && S::SORT) {
+    if (A.cost != nullptr) {  // the sorted solves' bucket counts start at zero
+      SortSmem<T, R> q(smem_raw);
+      for (int i = threadIdx.x; i < (NT / 32) * S::NB; i += NT) q.tab[i] = 0;
+      __syncthreads();
+    }
+  }
   const R chat = (R)ph.chat;
   const double chat6 = ph.chat * (1.0 / 6.0);
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -682,8 +824,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
     }
     __syncthreads();
 
+    // this thread's cell: its explicit state y* (stages 1, 2), rho, chi
+    double y[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double rho = 0.0, chi = 0.0;
+    int idx = 0;
+    int nn = 0, no = 0;
+    int code = RHD_OK;
+    bool need = false;  // a local solve to run for it
+    // RK2-SSP (Sec. 4.2): no exchange in stage 1, the full dt f(y(n+1)) in
+    // stage 2; IMEX PD-ARS: theta = 1, then theta = 1/2
+    const bool rk2 = GEN && ph.scheme == RHD_SCHEME_RK2_SSP;
     if (col) {
-      const int idx = ix + g.n[0] * (iy + g.n[1] * k);
+      idx = ix + g.n[0] * (iy + g.n[1] * k);
       double rate[4];
       const int fl = tx + ty * (TX + 1);
       // flux differences in double: the difference of two floats is exact in
@@ -716,7 +868,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       bad = bad || !isfinite(rate[0]) || !isfinite(rate[1]) || !isfinite(rate[2]) ||
             !isfinite(rate[3]);
 
-      double y[8];
       if (STAGE == 0) {
         // transport only: s(y) of eq. (yrsla) for E and the physical flux F
         RHD_ST(A.st, A.rate[0], idx, g.ncell, rate[0]);
@@ -741,25 +892,59 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 #pragma unroll
         for (int j = 0; j < 3; ++j) y[Y_FX + j] += 0.5 * A.dt * ph.c * rate[1 + j];
       }
-      const double rho = RHD_LD(A.st, A.rho, idx, g.ncell);
-      const double chi = RHD_LD(A.st, A.kappa, idx, g.ncell) * rho;
-      int nn = 0, no = 0;
-      int code = RHD_OK;
-      // RK2-SSP (Sec. 4.2): no exchange in stage 1, the full dt f(y(n+1)) in
-      // stage 2; IMEX PD-ARS: theta = 1, then theta = 1/2
-      const bool rk2 = GEN && ph.scheme == RHD_SCHEME_RK2_SSP;
+      rho = RHD_LD(A.st, A.rho, idx, g.ncell);
+      chi = RHD_LD(A.st, A.kappa, idx, g.ncell) * rho;
       if (STAGE != 0) {
         if (bad)
           code = RHD_ERR_NONPHYSICAL;
-        else if (!(rk2 && STAGE == 1)) {
-          const double tdt = (STAGE == 1 || rk2) ? A.dt : 0.5 * A.dt;
-          if (GEN && (ph.kappa_P_ratio != 1.0 || ph.kappa_F_ratio != 1.0))
-            code = local_solve_nongrey<MIXED>(ph, tdt, rho, chi, y, nn, no);
-          else
-            code = local_solve<MIXED, GEN>(ph, tdt, rho, chi, y, nn, no);
+        else
+          need = !(rk2 && STAGE == 1);
+      }
+    }
+    if constexpr (STAGE != 0) {
+      const double tdt = (STAGE == 1 || rk2) ? A.dt : 0.5 * A.dt;
+      // with predicted costs the block's solves run in cost order: each
+      // thread solves the cell of its sorted slot, so that a warp's lanes
+      // take similar numbers of iterations; a cell's arithmetic does not
+      // depend on the lane that runs it, so the results are the same bits
+      bool sorted = false;
+      if constexpr (S::SORT) sorted = A.cost != nullptr && !(rk2 && STAGE == 1);
+      int myslot = threadIdx.x;
+      bool run = need;
+      if constexpr (S::SORT) {
+        if (sorted) {
+          myslot = sort_slot<T, R>(smem_raw, A, need, idx, g.ncell);
+          stage_slot_put<T, R>(smem_raw, A, myslot, y, rho, chi, need);
+          __syncthreads();
+          run = stage_slot_get<T, R>(smem_raw, A, threadIdx.x, y, rho, chi);
         }
+      }
+      int scode = RHD_OK, snn = 0, sno = 0;
+      if (run) {
+        if (GEN && (ph.kappa_P_ratio != 1.0 || ph.kappa_F_ratio != 1.0))
+          scode = local_solve_nongrey<MIXED>(ph, tdt, rho, chi, y, snn, sno);
+        else
+          scode = local_solve<MIXED, GEN>(ph, tdt, rho, chi, y, snn, sno);
+      }
+      if constexpr (S::SORT) {
+        if (sorted) {
+          if (run) stage_slot_result<T, R>(smem_raw, A, threadIdx.x, y, scode, snn, sno);
+          __syncthreads();
+          if (need) stage_slot_take<T, R>(smem_raw, A, myslot, y, scode, snn, sno);
+        }
+      }
+      if (need) {
+        code = scode;
+        nn = snn;
+        no = sno;
+      }
+    }
+    if (col) {
+      if (STAGE != 0) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) RHD_ST(A.st, A.yo[q], idx, g.ncell, y[q]);
+        if (A.cost != nullptr && need)
+          RHD_ST(A.st, A.cost, idx, g.ncell, (unsigned char)min(255, nn + 4 * no));
       }
       if (code != RHD_OK) {
         atomicMin(&A.st->fail_key, ((unsigned long long)(A.cell_base + idx) << 8) | (unsigned)code);
