@@ -109,9 +109,9 @@ struct StageArgs {
   // tile rows skipped along the slowest axis (z in 3-D, y in 2-D, x in 1-D):
   // a launch over the rows [blk_off, blk_off + grid extent) of that axis
   int blk_off = 0;
-  // stages 1 and 2: each cell's solve cost (Newton updates + 4 x outer passes,
-  // at most 255) in this stage of the previous step, read to order the local
-  // solves of a plane by cost and rewritten; null: solves in cell order
+  // stages 1 and 2: each cell's solve cost (outer passes and Newton updates,
+  // packed in a byte) in this stage of the previous step, read to order the
+  // local solves of a plane by cost and rewritten; null: solves in cell order
   unsigned char* cost = nullptr;
 };
 

@@ -453,10 +453,23 @@ struct SortSmem {
   }
 };
 
+// Solve cost of a cell as kept between steps: its outer passes (1..8) in the
+// top 3 bits, its Newton updates (0..31) in the low 5; 0 before the first.
+__device__ __forceinline__ unsigned char cost_byte(int nn, int no) {
+  return (unsigned char)((min(max(no, 1), 8) - 1) << 5 | min(nn, 31));
+}
+
+// Cost bucket of a kept cost: nn + 4 no - 8, within [0, 31] (the work of a
+// Newton update counting 1 and of an outer pass about 4).
+__device__ __forceinline__ int cost_key(int b) {
+  if (b == 0) return 0;
+  const int no = (b >> 5) + 1, nn = b & 31;
+  return max(0, min(31, nn + 4 * no - 8));
+}
+
 // Slot of this thread's cell in the block's cost order: a stable counting
-// sort on the cost bucket (the previous step's cost - 8, within [0, 31]:
-// costs run from about 6 to 50, a Newton update counting 1 and an outer pass
-// 4; cells without a solve in bucket 0).  Sorted rank r goes to warp r / 32 in the first half of
+// sort on the cost bucket of the previous step's cost (cells without a solve
+// in bucket 0).  Sorted rank r goes to warp r / 32 in the first half of
 // the warps and to the mirrored warp in the second (ranks 128..255 of 256 to
 // warps 7..4), so that each of the SM's schedulers (warp w runs on scheduler
 // w mod 4) holds one cheaper and one dearer warp of the block.  The bucket
@@ -471,7 +484,7 @@ __device__ __forceinline__ int sort_slot(unsigned char* smem, const StageArgs& A
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int key = 0;
-  if (need) key = max(0, min(NB - 1, (int)RHD_LD(A.st, A.cost, idx, ncell) - 8));
+  if (need) key = cost_key((int)RHD_LD(A.st, A.cost, idx, ncell));
   const unsigned m = __match_any_sync(full, key);
   const int wrank = __popc(m & ((1u << lane) - 1u));
   if (wrank == 0) RHD_ST(A.st, q.tab, warp * NB + key, NW * NB, __popc(m));
@@ -944,7 +957,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
 #pragma unroll
         for (int q = 0; q < 8; ++q) RHD_ST(A.st, A.yo[q], idx, g.ncell, y[q]);
         if (A.cost != nullptr && need)
-          RHD_ST(A.st, A.cost, idx, g.ncell, (unsigned char)min(255, nn + 4 * no));
+          RHD_ST(A.st, A.cost, idx, g.ncell, cost_byte(nn, no));
       }
       if (code != RHD_OK) {
         atomicMin(&A.st->fail_key, ((unsigned long long)(A.cell_base + idx) << 8) | (unsigned)code);
