@@ -878,6 +878,7 @@ def run_ours(args):
              "peak_source": "measured on this GPU: " + fma_peaks["method"],
              "peak_nominal": FP64_PEAK_TFLOPS,
              "hbm_view": hbm_view,
+             "decomposition": views["fp64"].get("decomposition"),
              "note": "FP64-pipe bound: the fraction of the FP64 flop peak also loses "
                      "the lanes idle in the per-cell iterations and the FP64-pipe "
                      "slots of adds and multiplies (1 flop) against FMAs (2)"},
