@@ -88,16 +88,21 @@ struct SmemT {
   static constexpr int FYI = ISO && T::NDIM >= 2 ? (T::TY + 1) * T::TX : 0;
   static constexpr size_t ISO_OFF = sizeof(R) * (RING + FX + FY + CZ);
   // local solves in cost order (stages 1 and 2, where the launch supplies
-  // the predicted costs): per slot the explicit state, rho and chi (10
-  // doubles, slot-minor), then the solve flag / status, Newton and outer
-  // counts, and the per-warp counts of each cost bucket.  Not with the 3-D
-  // PPM tile, whose two blocks per SM leave no room.
-  static constexpr bool SORT = !(T::PPM && T::NDIM == 3);
+  // the predicted costs): per slot the explicit state (8 doubles,
+  // slot-minor), then per slot the solve flag and source thread / the
+  // status, the Newton and outer counts, and the per-warp counts of each cost
+  // bucket.  The FP64 3-D PPM tile, whose two blocks per SM leave no room for
+  // more, stages the states in its face-flux arrays, which hold nothing
+  // between a plane's flux differences and the next plane's faces.
   static constexpr int NB = 32;  // cost buckets
-  static constexpr size_t SORT_OFF = ISO_OFF + sizeof(double) * (FXI + FYI);
-  static constexpr size_t SORT_BYTES =
-      SORT ? sizeof(double) * 10 * T::NT + sizeof(int) * (3 * T::NT + (T::NT / 32) * NB) : 0;
-  static constexpr size_t BYTES = SORT_OFF + SORT_BYTES;
+  static constexpr bool SORT_ALIAS = T::PPM && T::NDIM == 3 && sizeof(R) == sizeof(double);
+  static_assert(!SORT_ALIAS || sizeof(R) * (FX + FY) >= sizeof(double) * 8 * T::NT,
+                "the face-flux arrays hold the staged states");
+  static constexpr size_t SORT_Y_OFF =
+      SORT_ALIAS ? sizeof(R) * RING : ISO_OFF + sizeof(double) * (FXI + FYI);
+  static constexpr size_t SORT_I_OFF = ISO_OFF + sizeof(double) * (FXI + FYI) +
+                                       (SORT_ALIAS ? 0 : sizeof(double) * 8 * T::NT);
+  static constexpr size_t BYTES = SORT_I_OFF + sizeof(int) * (3 * T::NT + (T::NT / 32) * NB);
 };
 
 // Coordinate x >= -3 folded onto [0, n) by the boundary condition (padding
@@ -433,9 +438,10 @@ __device__ __forceinline__ void column_cell(const StageArgs& A, int cx, int cy, 
 
 // Per-thread iteration statistics of the cells a thread has solved.
 // ------------------------------------------------ local solves in cost order
-// Shared arrays of the sorted solves (SmemT::SORT): 10 doubles per slot
-// (y[0..7], rho, chi), then per slot the solve flag / status, the Newton and
-// the outer counts, then the per-warp counts of each cost bucket.
+// Shared arrays of the sorted solves: 8 doubles per slot (the explicit state
+// y*), then per slot the solve flag and source thread (in) / the status
+// (out), the Newton and the outer counts, then the per-warp counts of each
+// cost bucket.
 template <class T, typename R>
 struct SortSmem {
   double* v;
@@ -445,8 +451,8 @@ struct SortSmem {
   int* tab;
   __device__ __forceinline__ explicit SortSmem(unsigned char* smem) {
     using S = SmemT<T, R>;
-    v = reinterpret_cast<double*>(smem + S::SORT_OFF);
-    flag = reinterpret_cast<int*>(v + 10 * T::NT);
+    v = reinterpret_cast<double*>(smem + S::SORT_Y_OFF);
+    flag = reinterpret_cast<int*>(smem + S::SORT_I_OFF);
     nn = flag + T::NT;
     no = nn + T::NT;
     tab = no + T::NT;
@@ -512,35 +518,34 @@ __device__ __forceinline__ int sort_slot(unsigned char* smem, const StageArgs& A
   return tw * 32 + (r & 31);
 }
 
-// this thread's cell into its sorted slot
+// this thread's cell (its explicit state; whether it needs a solve) into its
+// sorted slot
 template <class T, typename R>
 __device__ __forceinline__ void stage_slot_put(unsigned char* smem, const StageArgs& A, int slot,
-                                               const double y[8], double rho, double chi,
-                                               bool need) {
+                                               const double y[8], bool need) {
   constexpr int NT = T::NT;
   SortSmem<T, R> q(smem);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) RHD_ST(A.st, q.v, j * NT + slot, 10 * NT, y[j]);
-  RHD_ST(A.st, q.v, 8 * NT + slot, 10 * NT, rho);
-  RHD_ST(A.st, q.v, 9 * NT + slot, 10 * NT, chi);
-  RHD_ST(A.st, q.flag, slot, NT, need ? 1 : 0);
+  for (int j = 0; j < 8; ++j) RHD_ST(A.st, q.v, j * NT + slot, 8 * NT, y[j]);
+  RHD_ST(A.st, q.flag, slot, NT, need ? (int)(threadIdx.x << 1) | 1 : 0);
 }
 
-// the cell of slot (this thread's solve); clears the bucket counts for the
-// next plane (all threads have read them before the barrier that precedes
-// this call); returns whether the cell needs a solve
+// the cell of slot (this thread's solve): its state, and through src the
+// thread that owns it; clears the bucket counts for the next plane (all
+// threads have read them before the barrier that precedes this call);
+// returns whether the cell needs a solve
 template <class T, typename R>
 __device__ __forceinline__ bool stage_slot_get(unsigned char* smem, const StageArgs& A, int slot,
-                                               double y[8], double& rho, double& chi) {
+                                               double y[8], int& src) {
   using S = SmemT<T, R>;
   constexpr int NT = T::NT, NTAB = (NT / 32) * S::NB;
   SortSmem<T, R> q(smem);
   for (int i = threadIdx.x; i < NTAB; i += NT) q.tab[i] = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) y[j] = RHD_LD(A.st, q.v, j * NT + slot, 10 * NT);
-  rho = RHD_LD(A.st, q.v, 8 * NT + slot, 10 * NT);
-  chi = RHD_LD(A.st, q.v, 9 * NT + slot, 10 * NT);
-  return RHD_LD(A.st, q.flag, slot, NT) != 0;
+  for (int j = 0; j < 8; ++j) y[j] = RHD_LD(A.st, q.v, j * NT + slot, 8 * NT);
+  const int f = (int)RHD_LD(A.st, q.flag, slot, NT);
+  src = f >> 1;
+  return (f & 1) != 0;
 }
 
 // the solved cell of slot back into its slot
@@ -551,7 +556,7 @@ __device__ __forceinline__ void stage_slot_result(unsigned char* smem, const Sta
   constexpr int NT = T::NT;
   SortSmem<T, R> q(smem);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) RHD_ST(A.st, q.v, j * NT + slot, 10 * NT, y[j]);
+  for (int j = 0; j < 8; ++j) RHD_ST(A.st, q.v, j * NT + slot, 8 * NT, y[j]);
   RHD_ST(A.st, q.flag, slot, NT, code);
   RHD_ST(A.st, q.nn, slot, NT, nn);
   RHD_ST(A.st, q.no, slot, NT, no);
@@ -564,7 +569,7 @@ __device__ __forceinline__ void stage_slot_take(unsigned char* smem, const Stage
   constexpr int NT = T::NT;
   SortSmem<T, R> q(smem);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) y[j] = RHD_LD(A.st, q.v, j * NT + slot, 10 * NT);
+  for (int j = 0; j < 8; ++j) y[j] = RHD_LD(A.st, q.v, j * NT + slot, 8 * NT);
   code = (int)RHD_LD(A.st, q.flag, slot, NT);
   nn = (int)RHD_LD(A.st, q.nn, slot, NT);
   no = (int)RHD_LD(A.st, q.no, slot, NT);
@@ -602,7 +607,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
   if (threadIdx.x == 0) s_chk_status = A.st;
   __syncthreads();
 #endif
-  if constexpr (STAGE != 0 && S::SORT) {
+  if constexpr (STAGE != 0) {
     if (A.cost != nullptr) {  // the sorted solves' bucket counts start at zero
       SortSmem<T, R> q(smem_raw);
       for (int i = threadIdx.x; i < (NT / 32) * S::NB; i += NT) q.tab[i] = 0;
@@ -920,16 +925,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
       // thread solves the cell of its sorted slot, so that a warp's lanes
       // take similar numbers of iterations; a cell's arithmetic does not
       // depend on the lane that runs it, so the results are the same bits
-      bool sorted = false;
-      if constexpr (S::SORT) sorted = A.cost != nullptr && !(rk2 && STAGE == 1);
+      const bool sorted = A.cost != nullptr && !(rk2 && STAGE == 1);
       int myslot = threadIdx.x;
       bool run = need;
-      if constexpr (S::SORT) {
-        if (sorted) {
-          myslot = sort_slot<T, R>(smem_raw, A, need, idx, g.ncell);
-          stage_slot_put<T, R>(smem_raw, A, myslot, y, rho, chi, need);
-          __syncthreads();
-          run = stage_slot_get<T, R>(smem_raw, A, threadIdx.x, y, rho, chi);
+      if (sorted) {
+        myslot = sort_slot<T, R>(smem_raw, A, need, idx, g.ncell);
+        stage_slot_put<T, R>(smem_raw, A, myslot, y, need);
+        __syncthreads();
+        int src = 0;
+        run = stage_slot_get<T, R>(smem_raw, A, threadIdx.x, y, src);
+        if (run) {  // rho and chi of the slot's cell, as its own thread took them
+          const int sidx = (x0 + src % TX) + g.n[0] * ((y0 + src / TX) + g.n[1] * k);
+          rho = RHD_LD(A.st, A.rho, sidx, g.ncell);
+          chi = RHD_LD(A.st, A.kappa, sidx, g.ncell) * rho;
         }
       }
       int scode = RHD_OK, snn = 0, sno = 0;
@@ -939,12 +947,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& A, int x0, int y0, i
         else
           scode = local_solve<MIXED, GEN>(ph, tdt, rho, chi, y, snn, sno);
       }
-      if constexpr (S::SORT) {
-        if (sorted) {
-          if (run) stage_slot_result<T, R>(smem_raw, A, threadIdx.x, y, scode, snn, sno);
-          __syncthreads();
-          if (need) stage_slot_take<T, R>(smem_raw, A, myslot, y, scode, snn, sno);
-        }
+      if (sorted) {
+        if (run) stage_slot_result<T, R>(smem_raw, A, threadIdx.x, y, scode, snn, sno);
+        __syncthreads();
+        if (need) stage_slot_take<T, R>(smem_raw, A, myslot, y, scode, snn, sno);
       }
       if (need) {
         code = scode;
