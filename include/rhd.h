@@ -266,7 +266,8 @@ rhd_status rhd_sync(rhd_ctx* ctx, rhd_step_info* info);
  * last completed step, and the evolved fields of dst are unspecified.  Any
  * other error (RHD_ERR_CUDA, RHD_ERR_STATE) also leaves the context without a
  * state.  Refused while a batch is pending, during a slab step and on a
- * context with a HALO face. */
+ * context with a HALO face; a dst that overlaps src without being src
+ * returns RHD_ERR_ARG. */
 rhd_status rhd_step_host(rhd_ctx* ctx, const double* src, double* dst, int64_t count,
                          int nsteps, double dt, rhd_step_info* info);
 

@@ -947,6 +947,8 @@ rhd_status rhd_step_host(rhd_ctx* c, const double* src, double* dst, int64_t cou
     s = fail(c, RHD_ERR_ARG, "count must be RHD_NFIELDS * ncell");
   else if (nsteps < 1)
     s = fail(c, RHD_ERR_ARG, "nsteps < 1");
+  else if (dst != src && dst < src + count && src < dst + count)
+    s = fail(c, RHD_ERR_ARG, "dst overlaps src without being src");
   if (s == RHD_OK) {
     if (!(dt > 0.0)) dt = rhd_default_dt(&c->p);
     if (!std::isfinite(dt)) s = fail(c, RHD_ERR_ARG, "dt is not finite");

@@ -137,6 +137,11 @@ def test_host_step_rejects_bad_input_and_arguments(R):
             ctx.step_host(U.copy(), None, 1, dt=float("inf"))
         with pytest.raises(ValueError):
             ctx.step_host(torch.from_numpy(U.copy()).cuda(), None, 1)
+        # a destination that overlaps the source without being it
+        buf = np.zeros(U.size + 8)
+        buf[: U.size] = U.ravel()
+        st = ctx.step_host(buf[: U.size], buf[8:], 1, raise_on_error=False)["status"]
+        assert st == R.RHD_ERR_ARG
         # a good call afterwards works
         out = ctx.step_host(U.copy(), None, 1)["out"]
     Ur, _ = reference(R, prob, U, 1, "fp64")
