@@ -271,6 +271,18 @@ rhd_status rhd_sync(rhd_ctx* ctx, rhd_step_info* info);
 rhd_status rhd_step_host(rhd_ctx* ctx, const double* src, double* dst, int64_t count,
                          int nsteps, double dt, rhd_step_info* info);
 
+/* Diagnostic, host only (no device work): the plan rhd_step_host follows
+ * for the grid of p.  On return *nchunks = K, the chunks of tile rows along
+ * the slowest axis: chunk k holds the tile rows rows[k] .. rows[k+1] - 1
+ * and the cells cells[k] .. cells[k+1] - 1 (cell order of the state).
+ * groups receives pairs (first chunk, end chunk): ngroups[0] stage-1 launch
+ * groups, then ngroups[1] groups of the last step's stage 2, each copied
+ * out as it finishes.  cells and rows hold cap >= K + 1 entries, groups
+ * cap >= ngroups[0] + ngroups[1] pairs; a smaller cap, a NULL pointer or
+ * invalid params return RHD_ERR_ARG (message: rhd_last_error(NULL)). */
+rhd_status rhd_host_step_plan(const rhd_params* p, int* nchunks, int64_t* cells, int* rows,
+                              int* groups, int ngroups[2], int cap);
+
 /* Transport operator of the current state, s(y) of eq. (yrsla): the rates
  * dE/dt and dF/dt (physical flux) of the explicit stage (Sec. 3.3 face states
  * and HLL fluxes), without the local source terms.  rates: 4*ncell doubles,

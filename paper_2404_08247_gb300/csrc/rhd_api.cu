@@ -737,6 +737,54 @@ static StageArgs host_stage_args(rhd_ctx* c, double dt, int step, int stage) {
   return A;
 }
 
+// The chunks and launch groups of rhd_step_host for a grid: K chunks of
+// tile rows along the slowest axis (at least 2 rows each, at most 16
+// chunks), rows r0[k] .. r0[k+1] and cells i0[k] .. i0[k+1]; the stage-1
+// groups g1 (chunk 0, chunks 1 .. K/4 - 1, the rest) and the last stage-2
+// groups g2 (chunks 1 .. K-4 in up to three, K-3 .. K-2, K-1, then 0).
+struct HostPlan {
+  int K = 0;
+  std::vector<int> r0;
+  std::vector<size_t> i0;
+  std::vector<std::pair<int, int>> g1, g2;
+};
+
+static HostPlan host_step_plan(const Geometry& g) {
+  HostPlan P;
+  const int rows = stage_rows(g);
+  const int K = std::max(1, std::min(16, rows / 2));
+  P.K = K;
+  P.r0.assign(K + 1, 0);
+  P.i0.assign(K + 1, 0);
+  for (int k = 0; k <= K; ++k) P.r0[k] = (int)((long long)k * rows / K);
+  for (int k = 0; k < K; ++k) {
+    size_t n = 0;
+    for (int r = P.r0[k]; r < P.r0[k + 1]; ++r) n += (size_t)stage_row_cells(g, r);
+    P.i0[k + 1] = P.i0[k] + n;
+  }
+  if (K >= 3) {
+    const int q1 = std::max(2, K / 4);
+    P.g1 = {{0, 1}, {1, q1}, {q1, K}};
+    if (K >= 5) {
+      const int nb = std::min(3, K - 4);  // groups of the body 1 .. K-4
+      for (int j = 0; j < nb; ++j)
+        P.g2.push_back({1 + j * (K - 4) / nb, 1 + (j + 1) * (K - 4) / nb});
+      P.g2.push_back({K - 3, K - 1});
+      P.g2.push_back({K - 1, K});
+      P.g2.push_back({0, 1});
+    } else {
+      P.g2 = {{1, K - 1}, {K - 1, K}, {0, 1}};
+    }
+  } else if (K == 2) {
+    P.g1 = {{0, 1}, {1, 2}};
+    P.g2 = {{1, 2}, {0, 1}};
+  } else {
+    P.g1 = {{0, 1}};
+    P.g2 = {{0, 1}};
+  }
+  return P;
+}
+
 static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, int nsteps,
                                     double dt) {
   if (!c->hs[0]) {
@@ -749,16 +797,12 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
   }
   const Geometry& g = c->g;
   const size_t N = (size_t)c->ncell;
-  const int rows = stage_rows(g);
-  const int K = std::max(1, std::min(16, rows / 2));
-  std::vector<int> r0(K + 1);
-  std::vector<size_t> i0(K + 1, 0);
-  for (int k = 0; k <= K; ++k) r0[k] = (int)((long long)k * rows / K);
-  for (int k = 0; k < K; ++k) {
-    size_t n = 0;
-    for (int r = r0[k]; r < r0[k + 1]; ++r) n += (size_t)stage_row_cells(g, r);
-    i0[k + 1] = i0[k] + n;
-  }
+  const HostPlan P = host_step_plan(g);
+  const int K = P.K;
+  const std::vector<int>& r0 = P.r0;
+  const std::vector<size_t>& i0 = P.i0;
+  const std::vector<std::pair<int, int>>& g1 = P.g1;
+  const std::vector<std::pair<int, int>>& g2 = P.g2;
   if (i0[K] != N) return fail(c, RHD_ERR_STATE, "chunks cover %zu of %zu cells", i0[K], N);
   const int nev = 5 * K + 10;
   while ((int)c->hev.size() < nev) {
@@ -815,26 +859,6 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
   // K-3 .. K-2, K-1, and 0 last.  A stage-1 group reads the inputs of chunks a-1 .. b and the
   // TAU factors of chunks a-1 .. b-1 (launched on the stream of the first
   // group that needs them); a stage-2 group the stage-1 outputs of a-1 .. b.
-  std::vector<std::pair<int, int>> g1, g2;
-  if (K >= 3) {
-    const int q1 = std::max(2, K / 4);
-    g1 = {{0, 1}, {1, q1}, {q1, K}};
-    if (K >= 5) {
-      const int nb = std::min(3, K - 4);  // groups of the body 1 .. K-4
-      for (int j = 0; j < nb; ++j)
-        g2.push_back({1 + j * (K - 4) / nb, 1 + (j + 1) * (K - 4) / nb});
-      g2.push_back({K - 3, K - 1});
-      g2.push_back({K - 1, K});
-      g2.push_back({0, 1});
-    } else
-      g2 = {{1, K - 1}, {K - 1, K}, {0, 1}};
-  } else if (K == 2) {
-    g1 = {{0, 1}, {1, 2}};
-    g2 = {{1, 2}, {0, 1}};
-  } else {
-    g1 = {{0, 1}};
-    g2 = {{0, 1}};
-  }
   const StageArgs A1 = host_stage_args(c, dt, 0, 1);
   std::vector<int> grp1(K, -1);          // the stage-1 group of each chunk
   std::vector<int> tau_on(K, -1);        // the stream index that made chunk k's TAU factors
@@ -928,6 +952,33 @@ static rhd_status host_step_enqueue(rhd_ctx* c, const double* src, double* dst, 
   }
   CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
                               c->stream));
+  return RHD_OK;
+}
+
+rhd_status rhd_host_step_plan(const rhd_params* p, int* nchunks, int64_t* cells, int* rows,
+                              int* groups, int ngroups[2], int cap) {
+  char msg[256];
+  if (!p || !nchunks || !cells || !rows || !groups || !ngroups)
+    return fail(nullptr, RHD_ERR_ARG, "a pointer argument is NULL");
+  if (rhd_params_validate(p, msg, sizeof(msg)) != RHD_OK)
+    return fail(nullptr, RHD_ERR_ARG, "invalid params: %s", msg);
+  Geometry g;
+  Physics ph;
+  fill_geometry(p, g, ph);
+  const HostPlan P = host_step_plan(g);
+  const int ng = (int)(P.g1.size() + P.g2.size());
+  if (cap < P.K + 1 || cap < ng)
+    return fail(nullptr, RHD_ERR_ARG, "cap %d < %d", cap, std::max(P.K + 1, ng));
+  *nchunks = P.K;
+  for (int k = 0; k <= P.K; ++k) {
+    cells[k] = (int64_t)P.i0[k];
+    rows[k] = P.r0[k];
+  }
+  int j = 0;
+  for (const auto& q : P.g1) { groups[2 * j] = q.first; groups[2 * j + 1] = q.second; ++j; }
+  for (const auto& q : P.g2) { groups[2 * j] = q.first; groups[2 * j + 1] = q.second; ++j; }
+  ngroups[0] = (int)P.g1.size();
+  ngroups[1] = (int)P.g2.size();
   return RHD_OK;
 }
 

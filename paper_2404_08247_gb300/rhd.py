@@ -126,6 +126,10 @@ SIGNATURES = {
     "rhd_sync": (ctypes.c_int, [_V, ctypes.POINTER(rhd_step_info)]),
     "rhd_step_host": (ctypes.c_int, [_V, _V, _V, _I64, ctypes.c_int, ctypes.c_double,
                                      ctypes.POINTER(rhd_step_info)]),
+    "rhd_host_step_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "rhd_transport": (ctypes.c_int, [_V, _V, _I64, ctypes.c_int]),
     "rhd_totals": (ctypes.c_int, [_V, _D]),
     "rhd_profile": (ctypes.c_int, [_V, ctypes.c_int]),
@@ -275,6 +279,25 @@ def _ptr(x):
     if str(x.dtype) != "torch.float64" or not x.is_contiguous():
         raise ValueError("expected a contiguous float64 tensor")
     return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+def host_step_plan(prob: dict) -> dict:
+    """rhd_host_step_plan for a problem dict: {"cells": K + 1 offsets,
+    "rows": K + 1 tile-row offsets, "stage1": [(a, b)], "stage2": [(a, b)]}.
+    Host only."""
+    p = params_from_problem(prob)
+    cap = 64
+    K = ctypes.c_int()
+    cells = (_I64 * cap)()
+    rows = (ctypes.c_int * cap)()
+    groups = (ctypes.c_int * (2 * cap))()
+    ng = (ctypes.c_int * 2)()
+    _check(load().rhd_host_step_plan(ctypes.byref(p), ctypes.byref(K), cells, rows, groups, ng,
+                                     cap))
+    n = K.value
+    pairs = [(groups[2 * j], groups[2 * j + 1]) for j in range(ng[0] + ng[1])]
+    return {"cells": list(cells[: n + 1]), "rows": list(rows[: n + 1]),
+            "stage1": pairs[: ng[0]], "stage2": pairs[ng[0]:]}
 
 
 def eval_recip(x):

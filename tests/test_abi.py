@@ -219,3 +219,66 @@ def test_slab_problems_split_the_z_axis(rhd):
         rhd.slab_problems(prob, [0, 5])
     with pytest.raises(ValueError):
         rhd.slab_problems(I.base_problem(2, [8, 6], [1 / 8, 1 / 6]), [0, 6])
+
+
+# grids for the host-step plan: every dimension, tile rows that are ragged,
+# a single tile row, fewer rows than two chunks need, and the benchmark box
+PLAN_SHAPES = [(1,), (255,), (256,), (257,), (600,), (4000,), (100000,),
+               (7, 1), (33, 8), (45, 70), (64, 9), (512, 512),
+               (9, 7, 5), (40, 24, 70), (33, 9, 37), (16, 16, 8), (16, 16, 9), (8, 8, 17),
+               (12, 10, 40), (32, 32, 129), (256, 256, 256), (64, 64, 1000)]
+
+
+@pytest.mark.parametrize("n", PLAN_SHAPES, ids=lambda n: "x".join(map(str, n)))
+def test_host_step_plan_partitions_the_grid(rhd, n):
+    """The chunks of rhd_step_host cover the cells once, in order, each a run
+    of whole tile rows along the slowest axis; every chunk spans at least
+    three cells along that axis (the deepest face stencil, PPM's, reaches
+    only its neighbour chunks) unless there is one chunk; the stage-1 and
+    stage-2 launch groups each partition the chunks into contiguous runs,
+    within the compute streams (3 and 6), no stage-2 group above a quarter
+    of the chunks (rounded up) when there are five or more, and chunk 0
+    first in stage 1 and last in stage 2."""
+    ndim = len(n)
+    prob = I.base_problem(ndim, n, [1.0 / v for v in n])
+    plan = rhd.host_step_plan(prob)
+    cells, rows = plan["cells"], plan["rows"]
+    K = len(cells) - 1
+    ncell = 1
+    for v in n:
+        ncell *= v
+    plane = ncell // n[-1]  # cells per index of the slowest axis
+    tile = {1: 256, 2: 8, 3: 8}[ndim]  # cells of a tile row along that axis
+    assert 1 <= K <= 16
+    assert cells[0] == 0 and cells[-1] == ncell
+    assert all(b > a for a, b in zip(cells, cells[1:]))
+    assert rows[0] == 0 and rows[-1] == -(-n[-1] // tile)
+    for k in range(K):
+        lo, hi = cells[k] // plane, cells[k + 1] // plane
+        assert cells[k] % plane == 0
+        assert lo == rows[k] * tile and hi == min(n[-1], rows[k + 1] * tile)
+        assert K == 1 or hi - lo >= 3
+    for groups, most in ((plan["stage1"], 3), (plan["stage2"], 6)):
+        assert 1 <= len(groups) <= most
+        cover = sorted(c for a, b in groups for c in range(a, b))
+        assert cover == list(range(K))
+        assert all(b > a for a, b in groups)
+    if K >= 2:
+        assert plan["stage2"][-1] == (0, 1) and plan["stage1"][0] == (0, 1)
+    if K >= 5:
+        assert max(b - a for a, b in plan["stage2"]) <= -(-K // 4)
+
+
+def test_host_step_plan_rejects_bad_arguments(rhd):
+    p = rhd.params_from_problem(I.base_problem(3, (64, 64, 64), [1 / 64] * 3))
+    K = ctypes.c_int()
+    cells = (ctypes.c_int64 * 4)()
+    rows = (ctypes.c_int * 4)()
+    groups = (ctypes.c_int * 8)()
+    ng = (ctypes.c_int * 2)()
+    lib = rhd.load()
+    # 64 planes: 8 tile rows, 4 chunks: 5 entries needed
+    assert lib.rhd_host_step_plan(ctypes.byref(p), ctypes.byref(K), cells, rows, groups, ng,
+                                  4) == rhd.RHD_ERR_ARG
+    assert lib.rhd_host_step_plan(None, ctypes.byref(K), cells, rows, groups, ng,
+                                  4) == rhd.RHD_ERR_ARG
