@@ -3,10 +3,10 @@
 For a batch of problems it times every candidate (2-D tile shape x resident
 blocks per SM) on a throwaway copy of the batch (same problems, same initial
 states), with CUDA events around graph replays, and returns the fastest.
-Results are cached in a JSON file keyed by a signature of the workload
-(precision, counts of 1-D and 2-D problems, and their cell totals rounded to
-a power of two), so a workload of the same class reuses the choice without
-timing again.
+Results are cached in a JSON file keyed by a signature of the GPU model and
+the workload (precision, counts of 1-D and 2-D problems, and their cell
+totals rounded to a power of two), so a workload of the same class on the
+same kind of GPU reuses the choice without timing again.
 """
 from __future__ import annotations
 
@@ -20,14 +20,14 @@ CANDIDATES = [(t, b) for t in (0, 1, 2) for b in (1, 2)]
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rhd_gb300_autotune.json")
 
 
-def signature(probs, precision) -> str:
+def signature(probs, precision, device: str = "") -> str:
     n1 = [p["n"][0] for p in probs if p["ndim"] == 1]
     n2 = [p["n"][0] * p["n"][1] for p in probs if p["ndim"] == 2]
 
     def bucket(x):
         return 0 if x <= 0 else int(round(math.log2(x)))
-    return "%s|1d:%d:%d|2d:%d:%d" % (precision, len(n1), bucket(sum(n1)), len(n2),
-                                     bucket(sum(n2)))
+    return "%s%s|1d:%d:%d|2d:%d:%d" % (device + "|" if device else "", precision, len(n1),
+                                       bucket(sum(n1)), len(n2), bucket(sum(n2)))
 
 
 def _load(path):
@@ -52,7 +52,7 @@ def tune(problems, precision="mixed", nsteps=4, cache_path=DEFAULT_CACHE, force=
     {"tile2d", "blocks_per_sm", "timings_ms", "signature", "cached"}."""
     import torch
     probs = [p for p, _ in problems]
-    sig = signature(probs, precision)
+    sig = signature(probs, precision, torch.cuda.get_device_name())
     cache = _load(cache_path) if cache_path else {}
     if not force and sig in cache:
         hit = dict(cache[sig])
