@@ -56,11 +56,11 @@ ALG_BYTES = {0: 8 * (8 + 2 + 8), 1: 8 * (8 + 8 + 2 + 8)}
 KERNEL_NAMES = {0: "stage1", 1: "stage2"}
 FALLBACK_HBM_GBS = 6800.0
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 DFMA per
-# clock x 2 flops x 2.07 GHz (the probe of the design notes measured 600 G
-# DFMA/s, 95 % of it)
+# clock x 2 flops x 2.07 GHz (the library's probe, rhd_fma_probe, reaches
+# 1.24-1.25 TFLOP/s of it on the GB300)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops per face of the hydrodynamic face kernel (PLM, ncu thread
-# counts dadd + dmul + 2 dfma at 128^3; profiles/hydro_kernels_turbulent_box.md)
+# counts dadd + dmul + 2 dfma at 128^3)
 HYDRO_FACE_FLOPS = 210
 
 
@@ -653,8 +653,8 @@ def run_split(args, rhd, torch, prob, Ud, rank, ws, dist, barrier):
                                "unit": "GB/s", "frac": achieved / hbm,
                                "bytes_per_cell": HYDRO_BYTES_PER_CELL,
                                "note": "model of the multi-kernel step's traffic; the "
-                                       "face kernels are bound by the FP64 pipe (84 % busy, "
-                                       "profiles/hydro_kernels_turbulent_box.md)",
+                                       "face kernels are bound by the FP64 pipe (84 % busy "
+                                       "under ncu)",
                                "fp64_view": {
                                    "achieved": fp64_face / (hydro_ms * 1e-3) / 1e12,
                                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -889,8 +889,8 @@ def run_ours(args):
              "unit": "GB/s", "frac": views["hbm"]["frac"],
              "alg_bytes_per_cell": ALG_BYTES[dom], "peak_source": hbm_view["peak_source"],
              "pipe_views": {k: views[k] for k in ("fp64", "fp32") if k in views},
-             "note": "the stage kernels are bound by the FP64 pipe, not by HBM; see "
-                     "profiles/stage_kernel_fp64_turbulent_box.md"},
+             "note": "the stage kernels are bound by the FP64 pipe, not by HBM (DRAM "
+                     "below 1 % busy under ncu)"},
             **common)
 
     # end to end through the public API with pinned host buffers: a state held

@@ -63,8 +63,7 @@ CASES = {
     # Sec. 5.3 (static diffusion): (v0, cells, kappa, the paper's bound on the
     # frame difference).  The dynamic-diffusion pulse of Sec. 5.4 (3e7 cm/s,
     # 1,024 cells, kappa 500; 4.0 million radiation steps per frame) is a
-    # measurement recorded with the design notes, not a test: it takes eight
-    # minutes of GPU time.
+    # measurement, not a test: it takes eight minutes of GPU time.
     "static": (1e6, 512, 100.0, 3e-4),
 }
 
