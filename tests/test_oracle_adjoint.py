@@ -273,7 +273,8 @@ def test_trajectory_gradient_matches_central_differences(oracle_mod):
 @pytest.mark.parametrize("tau_cell", [1e-4, 1e-3, 0.03, 0.049, 0.051, 0.3])
 def test_opacity_gradient_across_the_tau_series_switch(oracle_mod, tau_cell):
     """TAU mode with optical depths on both sides of the switch between the
-    series and the closed form of d eps/d tau (R18): dL/dkappa of one step
+    Taylor series (below tau = 0.05, where the closed form cancels) and the
+    closed form (e^-tau (1 + tau) - 1)/tau^2 of d eps/d tau: dL/dkappa of one step
     equals central differences in kappa, cell by cell."""
     O = oracle_mod
     n = 12

@@ -651,6 +651,36 @@ def test_full_implicit_system_by_generic_root_finder(oracle_mod, theta):
         _check_against_root_finder(O, prob, theta, 0.1, rho, chi, y0)
 
 
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+@pytest.mark.parametrize("delta", [1e-4, 1e-8, 0.0])
+def test_outer_stop_with_cancelling_exchange_terms(oracle_mod, theta, delta):
+    """The outer iteration stops on the change of Q, the part of the exchange
+    that depends on v and F (Sec. 3.3).  With v = (u, u, 0) and F = (f,
+    -f (1 - delta), 0), v.F cancels to a fraction delta of its terms and
+    radiation starts in equilibrium, so Q is far smaller than its terms.
+    The solve must still stop within a few passes (the cap is 32) and on the
+    root of eq. (egupdate)-(fupdate) that a generic root finder gives: a stop
+    taken on rounding noise of the cancelled Q would leave F and m off that
+    root.  (Here |R| is large enough that the paper's own two tests stop
+    too: a copy of the oracle without the test against the terms' magnitude
+    takes the same passes.)"""
+    O = oracle_mod
+    prob = I.base_problem(1, [1], [1.0], c=10.0, chat=10.0, closure="eddington",
+                          a_rad=1e4)
+    rho = 1e6
+    Cv = rho / (prob["gamma"] - 1)
+    T0 = 3.0
+    E0 = prob["a_rad"] * T0 ** 4
+    u, f = 0.05 * prob["c"], 0.3 * prob["c"] * E0
+    v0 = np.array([u, u, 0.0])
+    F0 = np.array([f, -f * (1.0 - delta), 0.0])
+    y0 = [Cv * T0 + 0.5 * rho * (v0 ** 2).sum(), *(rho * v0), E0, *F0]
+    for chi in (0.1, 10.0, 100.0):
+        st, _, _, n_outer = O.local_solve(prob, theta, 0.1, rho, chi, y0)
+        assert st == 0 and n_outer <= 10
+        _check_against_root_finder(O, prob, theta, 0.1, rho, chi, y0)
+
+
 @pytest.mark.parametrize("order", [2, 1])
 @pytest.mark.parametrize("rP,rF", [(0.5, 0.3), (3.0, 1.5), (1.0, 4.0)])
 def test_nongrey_implicit_system_by_generic_root_finder(oracle_mod, order, rP, rF):
