@@ -26,7 +26,7 @@ from . import build as _build
 RHD_OK, RHD_ERR_ARG, RHD_ERR_CUDA, RHD_ERR_NEWTON, RHD_ERR_OUTER, \
     RHD_ERR_NONPHYSICAL, RHD_ERR_TIMEOUT, RHD_ERR_STATE, RHD_ERR_BOUNDS = range(9)
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "cuda", 3: "newton", 4: "outer",
-                5: "nonphysical", 6: "timeout", 7: "state"}
+                5: "nonphysical", 6: "timeout", 7: "state", 8: "bounds"}
 RHD_BC_PERIODIC, RHD_BC_REFLECT, RHD_BC_INFLOW, RHD_BC_HALO = 0, 1, 2, 3
 RHD_SCHEME_IMEX_PDARS, RHD_SCHEME_RK2_SSP = 0, 1
 RHD_CLOSURE_M1, RHD_CLOSURE_EDDINGTON = 0, 1

@@ -42,6 +42,30 @@ def test_library_exports_every_declared_symbol(rhd):
     assert sorted(rhd.SIGNATURES) == declared_functions()
 
 
+def test_binding_constants_match_header_enums():
+    """Every enumerator of the header (status codes, boundary kinds, plane
+    kinds, fields, options) has the same value in the Python binding, and
+    every status code has a name for the binding's errors."""
+    from paper_2404_08247_gb300 import rhd as R
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    seen = 0
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        value = -1
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, expr = item.partition("=")
+            name = name.strip()
+            value = int(expr.strip(), 0) if expr.strip() else value + 1
+            if hasattr(R, name):
+                assert getattr(R, name) == value, name
+                seen += 1
+    assert seen >= 40
+    for code in range(R.RHD_ERR_BOUNDS + 1):
+        assert code in R.STATUS_NAMES
+
+
 def test_struct_layouts_match_header(rhd, tmp_path):
     """sizeof/offsetof of the ABI structs, as the C compiler lays them out,
     equal the ctypes mirrors of the binding."""
