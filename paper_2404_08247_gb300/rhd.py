@@ -269,16 +269,22 @@ def params_from_problem(prob: dict, precision: str | int = "fp64") -> rhd_params
     return p
 
 
-def _ptr(x):
-    """(pointer, on_device) of a numpy array or torch tensor (float64, contiguous)."""
+def _ptr(x, count=None):
+    """(pointer, on_device) of a numpy array or torch tensor (float64,
+    contiguous) that holds at least `count` doubles: the library reads or
+    writes `count` of them, so a smaller buffer is refused here instead of
+    being overrun on the host or the device."""
     if isinstance(x, np.ndarray):
         if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
             raise ValueError("expected a C-contiguous float64 array")
-        return x.ctypes.data, 0
-    # torch tensor
-    if str(x.dtype) != "torch.float64" or not x.is_contiguous():
-        raise ValueError("expected a contiguous float64 tensor")
-    return x.data_ptr(), 1 if x.is_cuda else 0
+        ptr, dev, size = x.ctypes.data, 0, x.size
+    else:  # torch tensor
+        if str(x.dtype) != "torch.float64" or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 tensor")
+        ptr, dev, size = x.data_ptr(), 1 if x.is_cuda else 0, x.numel()
+    if count is not None and size < count:
+        raise ValueError("buffer holds %d doubles, the call needs %d" % (size, count))
+    return ptr, dev
 
 
 def host_step_plan(prob: dict) -> dict:
@@ -373,12 +379,12 @@ class RHDContext:
         _check(self.lib.rhd_set_stream(self.h, ctypes.c_void_p(int(handle))), self.h)
 
     def set_state(self, U):
-        ptr, dev = _ptr(U)
+        ptr, dev = _ptr(U, RHD_NFIELDS * self.ncell)
         _check(self.lib.rhd_state_set_all(self.h, ctypes.c_void_p(ptr),
                                           RHD_NFIELDS * self.ncell, dev), self.h)
 
     def set_field(self, field: int, x):
-        ptr, dev = _ptr(x)
+        ptr, dev = _ptr(x, self.ncell)
         _check(self.lib.rhd_state_set(self.h, field, ctypes.c_void_p(ptr),
                                       self.ncell, dev), self.h)
 
@@ -387,7 +393,7 @@ class RHDContext:
         NaN, so that a cell the library failed to write cannot pass as data."""
         if out is None:
             out = np.full(self.shape, np.nan)
-        ptr, dev = _ptr(out)
+        ptr, dev = _ptr(out, RHD_NFIELDS * self.ncell)
         _check(self.lib.rhd_state_get_all(self.h, ctypes.c_void_p(ptr),
                                           RHD_NFIELDS * self.ncell, dev), self.h)
         return out
@@ -395,7 +401,7 @@ class RHDContext:
     def get_field(self, field: int, out=None):
         if out is None:
             out = np.full(self.shape[1:], np.nan)
-        ptr, dev = _ptr(out)
+        ptr, dev = _ptr(out, self.ncell)
         _check(self.lib.rhd_state_get(self.h, field, ctypes.c_void_p(ptr),
                                       self.ncell, dev), self.h)
         return out
@@ -404,7 +410,7 @@ class RHDContext:
         """One evolved field of y(n+1/2) of the last step."""
         if out is None:
             out = np.full(self.shape[1:], np.nan)
-        ptr, dev = _ptr(out)
+        ptr, dev = _ptr(out, self.ncell)
         _check(self.lib.rhd_stage_get(self.h, field, ctypes.c_void_p(ptr), self.ncell, dev),
                self.h)
         return out
@@ -426,8 +432,8 @@ class RHDContext:
         src).  Returns the step info with "out" = dst."""
         if dst is None:
             dst = np.full(self.shape, np.nan)
-        ps, ds = _ptr(src)
-        pd, dd = _ptr(dst)
+        ps, ds = _ptr(src, RHD_NFIELDS * self.ncell)
+        pd, dd = _ptr(dst, RHD_NFIELDS * self.ncell)
         if ds or dd:
             raise ValueError("step_host takes host buffers")
         info = rhd_step_info()
@@ -519,7 +525,7 @@ class RHDContext:
         """Rates (dE/dt, dFx/dt, dFy/dt, dFz/dt) of s(y), shape (4, nz, ny, nx)."""
         if out is None:
             out = np.full((4,) + self.shape[1:], np.nan)
-        ptr, dev = _ptr(out)
+        ptr, dev = _ptr(out, 4 * self.ncell)
         _check(self.lib.rhd_transport(self.h, ctypes.c_void_p(ptr), 4 * self.ncell, dev),
                self.h)
         return out
@@ -684,14 +690,14 @@ class RHDBatch:
         return int(self.lib.rhd_batch_cells(self.h, prob))
 
     def set_state(self, prob: int, U):
-        ptr, dev = _ptr(U)
+        ptr, dev = _ptr(U, RHD_NFIELDS * self.cells(prob))
         self._check(self.lib.rhd_batch_state_set(self.h, prob, ctypes.c_void_p(ptr),
                                                  RHD_NFIELDS * self.cells(prob), dev))
 
     def get_state(self, prob: int, out=None):
         if out is None:
             out = np.full(self.shapes[prob], np.nan)
-        ptr, dev = _ptr(out)
+        ptr, dev = _ptr(out, RHD_NFIELDS * self.cells(prob))
         self._check(self.lib.rhd_batch_state_get(self.h, prob, ctypes.c_void_p(ptr),
                                                  RHD_NFIELDS * self.cells(prob), dev))
         return out

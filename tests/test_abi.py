@@ -306,3 +306,25 @@ def test_host_step_plan_rejects_bad_arguments(rhd):
                                   4) == rhd.RHD_ERR_ARG
     assert lib.rhd_host_step_plan(None, ctypes.byref(K), cells, rows, groups, ng,
                                   4) == rhd.RHD_ERR_ARG
+
+
+def test_binding_refuses_buffers_smaller_than_the_call_needs():
+    """The binding passes the library a count derived from the grid, so it
+    checks the caller's buffer against it first: a smaller array or tensor
+    is refused before any library call could overrun it."""
+    import numpy as np
+    import torch
+    from paper_2404_08247_gb300 import rhd as R
+    a = np.zeros(12)
+    assert R._ptr(a, 12) == (a.ctypes.data, 0)
+    assert R._ptr(a, 10)[1] == 0
+    with pytest.raises(ValueError, match="holds 12 doubles, the call needs 13"):
+        R._ptr(a, 13)
+    t = torch.zeros(7, dtype=torch.float64)
+    assert R._ptr(t, 7) == (t.data_ptr(), 0)
+    with pytest.raises(ValueError):
+        R._ptr(t, 8)
+    with pytest.raises(ValueError):
+        R._ptr(np.zeros(12, dtype=np.float32), 12)
+    with pytest.raises(ValueError):
+        R._ptr(np.zeros((4, 6))[:, ::2], 12)
